@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the BLINK dirty-image path on GB300.
+
+Workload (the configuration the headline metric is quoted on): a 256-antenna
+station (32640 baselines) in a 38 m disk, 1000 time steps x 32 channels over
+150-180 MHz, 180 x 180 all-sky images, uniform weighting, 20 point sources +
+sigma = 1 noise -- 32000 dirty images per step.
+
+One step = one pass of the whole path over the batch through the C ABI:
+a1-a2 + weight tables (plan build, one host sync), a3-a7 (gridding + FFT
+kernels), plan release.  Inputs are device resident when the timed region
+starts; `e2e` repeats the measurement with host buffers and the host<->device
+copies inside the timed region.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dirty images/s and Gvis/s gridded on 1 GB300, % roofline, error vs FP64 oracle"
+UNIT = "images/s"
+KERNEL = "k_image_small<180>"
+CSRC = os.path.join(ROOT, "paper_2405_13478_gb300", "csrc")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--n-times", type=int, default=1000, help="time steps per rank (1000)")
+    return p.parse_args()
+
+
+def dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None if there is none for the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "k_image_small_180_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("csrc_sha") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_layer"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(ws, seconds: float = 10.0):
+    """The FP64 oracle, as it stands, on all host cores over a bounded sample
+    of the same workload (20 time steps x 32 channels, repeated for ~10 s)."""
+    import numpy as np
+
+    import oracle
+
+    cores = os.cpu_count() or 1
+    n_t = 20
+    vis = ws.vis("cpu", times=range(n_t)).reshape(-1).numpy()
+    layers = ws.layers(times=range(n_t))
+    oracle.image_batch(ws.ant_xyz, layers[:cores], vis, "fft", n_threads=cores)  # warm
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.image_batch(ws.ant_xyz, layers, vis, "fft", n_threads=cores)
+        done += len(layers)
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_t} time steps x 32 channels of the same workload ({len(layers)} "
+                      f"images of 180^2, uniform), repeated {done // len(layers)}x in {el:.1f} s; "
+                      "FP64 C oracle, FFT route, OpenMP over images"}
+
+
+def sampled_error(ctx, ws, d_xyz, vis, images, layers, n=8):
+    """Max |gpu - oracle| / max |oracle| over a few layers of the batch."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    rng = np.random.default_rng(1)
+    pick = sorted(set(rng.integers(0, len(layers), n).tolist()))
+    B = ws.n_baselines
+    sub = [dict(layers[k], vis_offset=i * B) for i, k in enumerate(pick)]
+    v = torch.stack([vis[layers[k]["vis_offset"]:layers[k]["vis_offset"] + B] for k in pick])
+    want, _ = oracle.image_batch(ws.ant_xyz, sub, v.cpu().reshape(-1).numpy(), "fft")
+    worst = 0.0
+    for k, w in zip(pick, want):
+        o = layers[k]["out_offset"]
+        g = images[o:o + 180 * 180].cpu().numpy().reshape(180, 180)
+        worst = max(worst, float(np.abs(g - w).max() / np.abs(w).max()))
+    return worst
+
+
+def run_reference(args):
+    import synth
+
+    rank, world, _ = dist()
+    if rank != 0:
+        return
+    ws = synth.config2(seed=0, n_times=20)
+    import oracle
+
+    cores = os.cpu_count() or 1
+    vis = ws.vis("cpu").reshape(-1).numpy()
+    layers = ws.layers()
+    for _ in range(args.warmup):
+        oracle.image_batch(ws.ant_xyz, layers, vis, "fft", n_threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.image_batch(ws.ant_xyz, layers, vis, "fft", n_threads=cores)
+    el = time.perf_counter() - t0
+    value = args.steps * len(layers) / el
+    sample = (f"each step: 20 time steps x 32 channels ({len(layers)} images of 180^2, "
+              "uniform) of the workload; FP64 C oracle, FFT route, OpenMP over images")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "station 256 ant, 32640 baselines, 1000 x 32 ch, 180^2, uniform",
+                   "sample_layers_per_step": len(layers)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2405_13478_gb300 import binding, build
+
+    rank, world, local = dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = tdist
+    if rank == 0:
+        build.build()
+    if pg:
+        pg.barrier()
+    lib = binding.lib()  # noqa: F841  (fails loudly when the library is missing)
+
+    # Each rank images its own 1000 x 32 batch (weak scaling, no data-path collective).
+    ws = synth.config2(seed=rank, n_times=args.n_times)
+    layers = ws.layers()
+    L = len(layers)
+    B = ws.n_baselines
+    N = 180
+    layers, total = binding.layer_out_offsets(layers)
+    vis = ws.vis("cuda").reshape(-1)                     # complex64, 8.36 GB at 1000 steps
+    images = torch.empty(total, dtype=torch.float32, device="cuda")
+    wsum = torch.empty(L, dtype=torch.float32, device="cuda")
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    ctx = binding.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        plan = binding.Plan(ctx, d_xyz, layers)   # a1-a2 + tables (one host sync)
+        if ev:
+            ev[0].record(stream)
+        plan.image(vis, images, wsum)              # a3-a7
+        if ev:
+            ev[1].record(stream)
+        plan.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(kev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * L * args.steps / (ms / 1e3)
+    err = sampled_error(ctx, ws, d_xyz, vis, images, layers) if rank == 0 else None
+
+    # e2e: host buffers, copies inside the timed region (pinned host memory)
+    h_vis = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
+    h_vis.copy_(vis)
+    h_img = torch.empty(images.shape, dtype=images.dtype, pin_memory=True)
+    h_ws = torch.empty(wsum.shape, dtype=wsum.dtype, pin_memory=True)
+    d_vis2 = torch.empty_like(vis)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        d_vis2.copy_(h_vis, non_blocking=True)
+        ctx.image_batch(d_xyz, layers, d_vis2, images, wsum)
+        h_img.copy_(images, non_blocking=True)
+        h_ws.copy_(wsum, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([e2e_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * L * args.e2e_steps / (e2e_ms / 1e3)
+    del h_vis, d_vis2
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(synth.config2(seed=0, n_times=20))
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        bytes_per_layer = B * 8 + N * N * 4          # vis in + image out (algorithmic)
+        kms = statistics.mean(kern_ms)
+        achieved = L * bytes_per_layer / (kms / 1e3) / 1e9
+        tr = ncu_traffic()
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "station: 256 antennas in a 38 m disk, 32640 baselines, "
+                                   "1000 time steps x 32 channels (150-180 MHz), 180^2 all-sky "
+                                   "images, uniform weighting, 20 sources + sigma=1 noise",
+                       "layers_per_gpu": L, "n_px": N, "baselines": B,
+                       "l2": "inputs larger than L2 (8.36 GB of visibilities per GPU)",
+                       "parallelism": f"replicas x{world} (independent layers, no collective)"},
+            "gvis_per_s": value * B / 1e9,
+            "err_vs_oracle": err,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": (tr * L) if tr is not None else None,
+                         "kernel": KERNEL, "kernel_ms": kms,
+                         "algorithmic_bytes_per_launch": L * bytes_per_layer},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(vis.numel() * 8),
+                    "d2h_bytes_per_step": int(images.numel() * 4 + wsum.numel() * 4)},
+            "gpu_launches": 3 * args.steps,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

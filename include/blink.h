@@ -1,0 +1,153 @@
+/*
+ * blink.h -- C ABI of the GB300 (sm_103a) BLINK dirty-image library.
+ *
+ * The library turns batches of complex visibilities into dirty images, one
+ * image per (time step, frequency channel) "layer" (Sokolowski et al.,
+ * arXiv 2405.13478, Sec. 5.2.4).  For every layer it
+ *   a1  computes each baseline's (u,v) in wavelengths from the antenna
+ *       positions and the layer frequency, in FP64 (Sec. 5.2.1 step 1; the
+ *       Fig. 7 listing; w is dropped for a coplanar zenith-phased array,
+ *       Sec. 4.3 Eqs. 4-5);
+ *   a2  assigns the grid cell k = round-half-away(u / delta_u), zero spatial
+ *       frequency in the centre bin, keeping |k_u|,|k_v| <= N/2-1 (Sec. 4.4.1
+ *       Eq. 9; Sec. 5.2.1 step 1);
+ *   a3  grids V at k and conj(V) at -k (Sec. 5.2.1 steps 2-3);
+ *   a4  applies natural or uniform (1/count) weighting (Sec. 4.4.2);
+ *   a5-a7  inverse 2-D FFT with FFT shifts and real part (Sec. 4.3 Eq. 6,
+ *       Sec. 5.2.2), unnormalised: a unit source at the phase centre gives a
+ *       centre pixel equal to the summed weight.
+ *
+ * Conventions for every entry point:
+ *   - Pointers prefixed d_ are device pointers on the context's device; h_
+ *     pointers are host memory.  The caller owns all of them; the library
+ *     never frees caller memory.
+ *   - Complex numbers are interleaved float pairs (re, im) = complex64.
+ *   - Baselines are the cross-correlation pairs (i < j) in lexicographic
+ *     order, B = n_ant (n_ant - 1) / 2; baseline b of pair (i, j) has
+ *     u = (x_j - x_i) / lambda.
+ *   - Antenna positions are float64 [n_ant][3] metres (x east, y north, z up;
+ *     z is ignored).
+ *   - Images are float32 [N][N] row-major: row y <-> m (v axis), column x <->
+ *     l (u axis), phase centre at pixel (N/2, N/2).  Grids are complex64
+ *     [N][N] with the same orientation (row = k_v + N/2, column = k_u + N/2).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is enqueued asynchronously on it unless stated.
+ *   - Every call returns a blink_status.  Invalid arguments are rejected on the
+ *     host before anything is launched; blink_last_error() then describes the
+ *     problem.  No C++ exception crosses this boundary.
+ *   - A context is not thread safe: use one per host thread (or lock).
+ */
+#ifndef BLINK_H
+#define BLINK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BLINK_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define BLINK_API __attribute__((visibility("default")))
+#else
+#define BLINK_API
+#endif
+
+typedef enum {
+    BLINK_OK = 0,
+    BLINK_ERR_INVALID = -1,     /* bad argument (caught on the host) */
+    BLINK_ERR_UNSUPPORTED = -2, /* valid but not implemented (e.g. image size) */
+    BLINK_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    BLINK_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    BLINK_ERR_WORKSPACE = -5    /* device memory for the workspace ran out */
+} blink_status;
+
+typedef enum { BLINK_NATURAL = 0, BLINK_UNIFORM = 1 } blink_weighting;
+
+/* Flags of blink_image_batch / blink_plan_image. */
+#define BLINK_NORMALIZE 0x1u /* divide each image by its summed weight */
+
+/* One image ("layer", Sec. 5.2.4). */
+typedef struct {
+    int32_t n_px;       /* image side N: even, one of blink_supported_sizes() */
+    int32_t weighting;  /* blink_weighting */
+    double freq_hz;     /* channel frequency nu (> 0) */
+    double delta_u;     /* cell size in wavelengths, 1 / (N dx) (Sec. 4.4.1 Eq. 9) (> 0) */
+    int64_t vis_offset; /* complex64 element offset of this layer's B visibilities */
+    int64_t out_offset; /* element offset of this layer's N*N output
+                           (float32 for images, complex64 for grids) */
+} blink_layer;
+
+typedef struct blink_ctx blink_ctx;
+typedef struct blink_plan blink_plan;
+
+/* ---------------------------------------------------------------- context */
+/* Version of this ABI (BLINK_ABI_VERSION). */
+BLINK_API int blink_abi_version(void);
+
+/* Writes up to `cap` supported image sizes N into `sizes`; returns how many
+ * sizes exist (call with cap = 0 to count). */
+BLINK_API int blink_supported_sizes(int32_t *sizes, int cap);
+
+/* Creates a context on CUDA device `device` (makes it current for the call).
+ * The context owns a device workspace that grows on demand and is freed by
+ * blink_ctx_destroy.  *out is NULL on failure. */
+BLINK_API int blink_ctx_create(blink_ctx **out, int device);
+BLINK_API void blink_ctx_destroy(blink_ctx *ctx);
+
+/* Text of the last error recorded on `ctx` ("" if none).  The string belongs
+ * to the context and stays valid until its next call. */
+BLINK_API const char *blink_last_error(const blink_ctx *ctx);
+
+/* ------------------------------------------------------------ a1-a2 only */
+/* Cell indices of every baseline of every layer, bit-exact FP64 rounding
+ * (a1-a2).  d_cells: int32 [n_layers][B][2] = (k_u, k_v) per baseline, or
+ * (INT32_MIN, INT32_MIN) when the baseline falls outside |k| <= N/2-1 and is
+ * not gridded.  vis_offset/out_offset of h_layers are ignored. */
+BLINK_API int blink_cells(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+                int n_layers, int32_t *d_cells, void *stream);
+
+/* ------------------------------------------------------------ a1-a4 grid */
+/* Gridded, weighted visibilities of every layer (a1-a4), Hermitian-complete:
+ * d_grid + out_offset holds complex64 [N][N] with zero spatial frequency at
+ * (N/2, N/2) (Sec. 5.2.1 step 1).  d_wsum (float32 [n_layers], may be NULL)
+ * receives each layer's summed weight.  d_vis holds the complex64 visibilities
+ * addressed by vis_offset.  Gridding runs in shared memory without global
+ * atomics. */
+BLINK_API int blink_grid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+               int n_layers, const float *d_vis, float *d_grid, float *d_wsum, void *stream);
+
+/* ----------------------------------------------------- a1-a7 dirty images */
+/* Dirty images of every layer (a1-a7): d_images + out_offset receives the
+ * float32 [N][N] FFT-shifted real image, unnormalised unless flags has
+ * BLINK_NORMALIZE.  d_wsum (float32 [n_layers], may be NULL) receives the
+ * summed weights.  Layers of different sizes may be mixed.
+ * This call builds the per-channel tables on `stream` and synchronises that
+ * stream once to size the image kernels; use a plan (below) to build the
+ * tables once and image many batches asynchronously. */
+BLINK_API int blink_image_batch(blink_ctx *ctx, const double *d_ant_xyz, int n_ant,
+                      const blink_layer *h_layers, int n_layers, const float *d_vis,
+                      float *d_images, float *d_wsum, uint32_t flags, void *stream);
+
+/* ------------------------------------------------------------------ plans */
+/* A plan fixes the array and the layer descriptors, runs a1-a2 and the
+ * weighting tables once (on `stream`, which it synchronises once), and keeps
+ * them on the device.  blink_plan_image then only launches the gridding and
+ * FFT kernels: it is asynchronous and may be captured in a CUDA graph.  The
+ * plan reads d_ant_xyz only during blink_plan_create. */
+BLINK_API int blink_plan_create(blink_ctx *ctx, const double *d_ant_xyz, int n_ant,
+                      const blink_layer *h_layers, int n_layers, blink_plan **out, void *stream);
+BLINK_API int blink_plan_image(blink_plan *plan, const float *d_vis, float *d_images, float *d_wsum,
+                     uint32_t flags, void *stream);
+BLINK_API void blink_plan_destroy(blink_plan *plan);
+
+/* Summed weight and kept-baseline count of layer `layer` of a plan (host
+ * copies; no device work). */
+BLINK_API int blink_plan_layer_info(const blink_plan *plan, int layer, float *wsum, int64_t *n_kept);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLINK_H */

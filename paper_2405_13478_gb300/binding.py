@@ -1,0 +1,220 @@
+"""Thin ctypes binding of the C ABI in ``include/blink.h``.
+
+Argument marshalling only: PyTorch supplies device memory and the current
+CUDA stream; every step of the imaging path runs in the library's kernels.
+There is no CPU fallback -- if ``libblink.so`` is missing or no GPU is present
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Sequence
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libblink.so")
+
+OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE = 0, -1, -2, -3, -4, -5
+NATURAL, UNIFORM = 0, 1
+NORMALIZE = 0x1
+DROPPED = -(2 ** 31)
+
+# Symbols declared in include/blink.h (checked by the CPU test suite).
+EXPORTS = (
+    "blink_abi_version", "blink_supported_sizes", "blink_ctx_create", "blink_ctx_destroy",
+    "blink_last_error", "blink_cells", "blink_grid", "blink_image_batch", "blink_plan_create",
+    "blink_plan_image", "blink_plan_destroy", "blink_plan_layer_info",
+)
+
+
+class BlinkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"blink status {status}: {msg}")
+        self.status = status
+
+
+class Layer(ctypes.Structure):
+    _fields_ = [("n_px", ctypes.c_int32), ("weighting", ctypes.c_int32),
+                ("freq_hz", ctypes.c_double), ("delta_u", ctypes.c_double),
+                ("vis_offset", ctypes.c_int64), ("out_offset", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """Load libblink.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"BLINK CUDA library not built: {path} is missing "
+                           "(run paper_2405_13478_gb300/build.py)")
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    L.blink_abi_version.restype = I
+    L.blink_supported_sizes.restype = I
+    L.blink_supported_sizes.argtypes = [ctypes.POINTER(ctypes.c_int32), I]
+    L.blink_ctx_create.restype = I
+    L.blink_ctx_create.argtypes = [ctypes.POINTER(P), I]
+    L.blink_ctx_destroy.restype = None
+    L.blink_ctx_destroy.argtypes = [P]
+    L.blink_last_error.restype = ctypes.c_char_p
+    L.blink_last_error.argtypes = [P]
+    LP = ctypes.POINTER(Layer)
+    L.blink_cells.restype = I
+    L.blink_cells.argtypes = [P, P, I, LP, I, P, P]
+    L.blink_grid.restype = I
+    L.blink_grid.argtypes = [P, P, I, LP, I, P, P, P, P]
+    L.blink_image_batch.restype = I
+    L.blink_image_batch.argtypes = [P, P, I, LP, I, P, P, P, ctypes.c_uint32, P]
+    L.blink_plan_create.restype = I
+    L.blink_plan_create.argtypes = [P, P, I, LP, I, ctypes.POINTER(P), P]
+    L.blink_plan_image.restype = I
+    L.blink_plan_image.argtypes = [P, P, P, P, ctypes.c_uint32, P]
+    L.blink_plan_destroy.restype = None
+    L.blink_plan_destroy.argtypes = [P]
+    L.blink_plan_layer_info.restype = I
+    L.blink_plan_layer_info.argtypes = [P, I, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_int64)]
+    _lib = L
+    return L
+
+
+def supported_sizes():
+    L = lib()
+    n = L.blink_supported_sizes(None, 0)
+    buf = (ctypes.c_int32 * n)()
+    L.blink_supported_sizes(buf, n)
+    return list(buf)
+
+
+def make_layers(layers: Sequence[dict]):
+    arr = (Layer * max(1, len(layers)))()
+    for k, d in enumerate(layers):
+        arr[k] = Layer(int(d["n_px"]), int(d["weighting"]), float(d["freq_hz"]),
+                       float(d["delta_u"]), int(d["vis_offset"]), int(d.get("out_offset", 0)))
+    return arr
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_dev(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensors passed to the BLINK library must be CUDA tensors")
+        if t is not None and not t.is_contiguous():
+            raise ValueError("tensors passed to the BLINK library must be contiguous")
+
+
+class Context:
+    """A library context on one CUDA device (owns the device workspace pool)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        st = self._lib.blink_ctx_create(ctypes.byref(h), int(device))
+        if st != OK:
+            raise BlinkError(st, f"blink_ctx_create(device={device}) failed")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.blink_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, st):
+        if st != OK:
+            raise BlinkError(st, self._lib.blink_last_error(self.handle).decode())
+
+    def cells(self, ant_xyz, layers, cells_out, stream=None):
+        """a1-a2: int32 [n_layers][B][2] cell indices."""
+        _check_dev(ant_xyz, cells_out)
+        arr = make_layers(layers)
+        self._raise(self._lib.blink_cells(self.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
+                                          len(layers), _ptr(cells_out), _stream(stream)))
+
+    def grid(self, ant_xyz, layers, vis, grid_out, wsum_out=None, stream=None):
+        """a1-a4: complex64 Hermitian-complete grids (DC at N/2, N/2)."""
+        _check_dev(ant_xyz, vis, grid_out, wsum_out)
+        arr = make_layers(layers)
+        self._raise(self._lib.blink_grid(self.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
+                                         len(layers), _ptr(vis), _ptr(grid_out), _ptr(wsum_out),
+                                         _stream(stream)))
+
+    def image_batch(self, ant_xyz, layers, vis, images_out, wsum_out=None, flags=0, stream=None):
+        """a1-a7: float32 dirty images."""
+        _check_dev(ant_xyz, vis, images_out, wsum_out)
+        arr = make_layers(layers)
+        self._raise(self._lib.blink_image_batch(self.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
+                                                len(layers), _ptr(vis), _ptr(images_out),
+                                                _ptr(wsum_out), int(flags), _stream(stream)))
+
+    def plan(self, ant_xyz, layers, stream=None) -> "Plan":
+        return Plan(self, ant_xyz, layers, stream)
+
+
+class Plan:
+    """Tables built once (a1-a2, weights); image() launches a3-a7 only."""
+
+    def __init__(self, ctx: Context, ant_xyz, layers, stream=None):
+        _check_dev(ant_xyz)
+        self.ctx = ctx
+        self.n_layers = len(layers)
+        arr = make_layers(layers)
+        h = ctypes.c_void_p()
+        ctx._raise(ctx._lib.blink_plan_create(ctx.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
+                                              len(layers), ctypes.byref(h), _stream(stream)))
+        self.handle = h
+
+    def image(self, vis, images_out, wsum_out=None, flags=0, stream=None):
+        _check_dev(vis, images_out, wsum_out)
+        self.ctx._raise(self.ctx._lib.blink_plan_image(self.handle, _ptr(vis), _ptr(images_out),
+                                                       _ptr(wsum_out), int(flags),
+                                                       _stream(stream)))
+
+    def layer_info(self, layer: int):
+        w = ctypes.c_float()
+        n = ctypes.c_int64()
+        self.ctx._raise(self.ctx._lib.blink_plan_layer_info(self.handle, int(layer),
+                                                            ctypes.byref(w), ctypes.byref(n)))
+        return float(w.value), int(n.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx._lib.blink_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def layer_out_offsets(layers: Iterable[dict]):
+    """Packs images contiguously: returns (layers with out_offset, total floats)."""
+    out, off = [], 0
+    for d in layers:
+        d = dict(d)
+        d["out_offset"] = off
+        off += int(d["n_px"]) ** 2
+        out.append(d)
+    return out, off

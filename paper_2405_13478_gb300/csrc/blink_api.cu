@@ -1,0 +1,447 @@
+// blink_api.cu -- the C ABI declared in include/blink.h.
+//
+// Host-side runtime: argument validation, channel deduplication, device
+// workspace (a per-context stream-ordered memory pool), per-size grouping of
+// layers and kernel dispatch.  No compute happens on the host.
+#include "blink.h"
+#include "blink_common.cuh"
+#include "blink_kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+using blink::ChanGeom;
+using blink::ChanInfo;
+using blink::DevLayer;
+using blink::Error;
+
+struct blink_ctx {
+    int device = 0;
+    cudaMemPool_t pool = nullptr;
+    std::string err;
+};
+
+struct blink_plan {
+    blink_ctx *ctx = nullptr;
+    int n_ant = 0;
+    int64_t nb = 0;
+    int n_layers = 0;
+    int n_chan = 0;
+    bool any_uniform = false;
+    std::vector<ChanGeom> geoms;
+    std::vector<ChanInfo> infos;
+    std::vector<int32_t> layer_chan;
+    struct Group {
+        int n_px;
+        int first;
+        int count;
+        int r_alloc;
+    };
+    std::vector<Group> groups;
+    // device memory (one pool allocation for the tables, one for scratch)
+    char *d_block = nullptr;
+    ChanGeom *d_geom = nullptr;
+    ChanInfo *d_info = nullptr;
+    uint32_t *d_codes = nullptr;
+    float *d_wgt = nullptr;
+    DevLayer *d_layers = nullptr;
+    int2 *d_cells = nullptr;
+    float2 *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+constexpr size_t kScratchCap = size_t(256) << 20;  // bytes of row-transform scratch per plan
+
+// Runs f with ctx->device current and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(blink_ctx *ctx, int status, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return status;
+}
+
+int fail(blink_ctx *ctx, const Error &e) { return fail(ctx, e.status, e.msg); }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct ChanKey {
+    int32_t n_px, weighting;
+    uint64_t freq_bits, du_bits;
+    bool operator==(const ChanKey &o) const {
+        return n_px == o.n_px && weighting == o.weighting && freq_bits == o.freq_bits &&
+               du_bits == o.du_bits;
+    }
+};
+struct ChanKeyHash {
+    size_t operator()(const ChanKey &k) const {
+        uint64_t h = k.freq_bits * 0x9E3779B97F4A7C15ull;
+        h ^= (k.du_bits + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2));
+        h ^= uint64_t(uint32_t(k.n_px)) * 0xC2B2AE3D27D4EB4Full + uint64_t(k.weighting);
+        return size_t(h ^ (h >> 29));
+    }
+};
+
+ChanKey key_of(const blink_layer &L) {
+    ChanKey k;
+    k.n_px = L.n_px;
+    k.weighting = L.weighting;
+    std::memcpy(&k.freq_bits, &L.freq_hz, 8);
+    std::memcpy(&k.du_bits, &L.delta_u, 8);
+    return k;
+}
+
+int validate(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+             int n_layers) {
+    if (!ctx) return BLINK_ERR_INVALID;
+    if (n_ant < 2) return fail(ctx, BLINK_ERR_INVALID, "n_ant must be >= 2");
+    if (int64_t(n_ant) * (n_ant - 1) / 2 > (int64_t(1) << 31))
+        return fail(ctx, BLINK_ERR_UNSUPPORTED, "too many baselines (n_ant too large)");
+    if (!d_ant_xyz) return fail(ctx, BLINK_ERR_INVALID, "d_ant_xyz is NULL");
+    if (n_layers < 0) return fail(ctx, BLINK_ERR_INVALID, "n_layers < 0");
+    if (n_layers > 0 && !h_layers) return fail(ctx, BLINK_ERR_INVALID, "h_layers is NULL");
+    for (int l = 0; l < n_layers; ++l) {
+        const blink_layer &L = h_layers[l];
+        const std::string at = " (layer " + std::to_string(l) + ")";
+        if (L.n_px < 4 || (L.n_px & 1))
+            return fail(ctx, BLINK_ERR_INVALID, "n_px must be even and >= 4" + at);
+        if (!blink::image_size_supported(L.n_px))
+            return fail(ctx, BLINK_ERR_UNSUPPORTED,
+                        "image size " + std::to_string(L.n_px) + " not supported" + at);
+        if (L.weighting != BLINK_NATURAL && L.weighting != BLINK_UNIFORM)
+            return fail(ctx, BLINK_ERR_INVALID, "weighting must be 0 or 1" + at);
+        if (!(std::isfinite(L.freq_hz) && L.freq_hz > 0))
+            return fail(ctx, BLINK_ERR_INVALID, "freq_hz must be finite and > 0" + at);
+        if (!(std::isfinite(L.delta_u) && L.delta_u > 0))
+            return fail(ctx, BLINK_ERR_INVALID, "delta_u must be finite and > 0" + at);
+        if (L.vis_offset < 0 || L.out_offset < 0)
+            return fail(ctx, BLINK_ERR_INVALID, "offsets must be >= 0" + at);
+    }
+    return BLINK_OK;
+}
+
+void free_plan_memory(blink_plan *p, cudaStream_t st) {
+    if (p->d_block) cudaFreeAsync(p->d_block, st);
+    if (p->d_scratch) cudaFreeAsync(p->d_scratch, st);
+    p->d_block = nullptr;
+    p->d_scratch = nullptr;
+}
+
+// Builds the channel tables of a plan on `st` and waits for them.
+int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+               int n_layers, bool want_cells, blink_plan *p, cudaStream_t st) {
+    p->ctx = ctx;
+    p->n_ant = n_ant;
+    p->nb = int64_t(n_ant) * (n_ant - 1) / 2;
+    p->n_layers = n_layers;
+    p->last_stream = st;
+    // distinct channels
+    std::unordered_map<ChanKey, int, ChanKeyHash> chan_of;
+    chan_of.reserve(64);
+    p->layer_chan.resize(size_t(n_layers));
+    int prev_chan = -1;
+    ChanKey prev_key{};
+    for (int l = 0; l < n_layers; ++l) {
+        const ChanKey k = key_of(h_layers[l]);
+        int c;
+        if (prev_chan >= 0 && k == prev_key) {
+            c = prev_chan;
+        } else {
+            auto it = chan_of.find(k);
+            if (it == chan_of.end()) {
+                c = int(p->geoms.size());
+                chan_of.emplace(k, c);
+                p->geoms.push_back(ChanGeom{h_layers[l].freq_hz, h_layers[l].delta_u,
+                                            h_layers[l].n_px, h_layers[l].weighting});
+            } else {
+                c = it->second;
+            }
+        }
+        p->layer_chan[size_t(l)] = c;
+        prev_chan = c;
+        prev_key = k;
+    }
+    p->n_chan = int(p->geoms.size());
+    // channel table offsets
+    p->infos.assign(size_t(p->n_chan), ChanInfo{});
+    int64_t wgt_total = 0;
+    for (int c = 0; c < p->n_chan; ++c) {
+        ChanInfo &ci = p->infos[size_t(c)];
+        ci.n_px = p->geoms[size_t(c)].n_px;
+        ci.weighting = p->geoms[size_t(c)].weighting;
+        ci.code_off = int64_t(c) * p->nb;
+        if (ci.weighting == BLINK_UNIFORM) {
+            ci.wgt_off = wgt_total;
+            wgt_total += int64_t(ci.n_px / 2) * ci.n_px;
+            p->any_uniform = true;
+        } else {
+            ci.wgt_off = -1;
+        }
+    }
+    // layers grouped by image size, stable within a size
+    std::vector<int> order(static_cast<size_t>(n_layers));
+    for (int l = 0; l < n_layers; ++l) order[size_t(l)] = l;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return h_layers[a].n_px < h_layers[b].n_px; });
+    std::vector<DevLayer> dl(static_cast<size_t>(n_layers));
+    for (int k = 0; k < n_layers; ++k) {
+        const int l = order[size_t(k)];
+        dl[size_t(k)] = DevLayer{h_layers[l].vis_offset, h_layers[l].out_offset,
+                                 p->layer_chan[size_t(l)], l};
+        if (p->groups.empty() || p->groups.back().n_px != h_layers[l].n_px)
+            p->groups.push_back(blink_plan::Group{h_layers[l].n_px, k, 0, 1});
+        p->groups.back().count++;
+    }
+    // one device block for every table
+    const size_t a = 256;
+    size_t off = 0;
+    const size_t o_geom = off; off = align_up(off + sizeof(ChanGeom) * size_t(p->n_chan), a);
+    const size_t o_info = off; off = align_up(off + sizeof(ChanInfo) * size_t(p->n_chan), a);
+    const size_t o_codes = off; off = align_up(off + sizeof(uint32_t) * size_t(p->n_chan) * size_t(p->nb), a);
+    const size_t o_wgt = off; off = align_up(off + sizeof(float) * size_t(std::max<int64_t>(wgt_total, 1)), a);
+    const size_t o_layers = off; off = align_up(off + sizeof(DevLayer) * size_t(std::max(n_layers, 1)), a);
+    const size_t o_cells = off;
+    if (want_cells) off = align_up(off + sizeof(int2) * size_t(p->n_chan) * size_t(p->nb), a);
+    void *blk = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&blk, std::max<size_t>(off, a), ctx->pool, st);
+    if (e != cudaSuccess)
+        return fail(ctx, BLINK_ERR_WORKSPACE, std::string("table allocation: ") + cudaGetErrorString(e));
+    p->d_block = static_cast<char *>(blk);
+    p->d_geom = reinterpret_cast<ChanGeom *>(p->d_block + o_geom);
+    p->d_info = reinterpret_cast<ChanInfo *>(p->d_block + o_info);
+    p->d_codes = reinterpret_cast<uint32_t *>(p->d_block + o_codes);
+    p->d_wgt = reinterpret_cast<float *>(p->d_block + o_wgt);
+    p->d_layers = reinterpret_cast<DevLayer *>(p->d_block + o_layers);
+    p->d_cells = want_cells ? reinterpret_cast<int2 *>(p->d_block + o_cells) : nullptr;
+#define TRY(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, BLINK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+    if (p->n_chan) {
+        TRY(cudaMemcpyAsync(p->d_geom, p->geoms.data(), sizeof(ChanGeom) * p->geoms.size(),
+                            cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(p->d_info, p->infos.data(), sizeof(ChanInfo) * p->infos.size(),
+                            cudaMemcpyHostToDevice, st));
+    }
+    if (n_layers)
+        TRY(cudaMemcpyAsync(p->d_layers, dl.data(), sizeof(DevLayer) * dl.size(),
+                            cudaMemcpyHostToDevice, st));
+    if (p->any_uniform) TRY(cudaMemsetAsync(p->d_wgt, 0, sizeof(float) * size_t(wgt_total), st));
+    Error er = blink::launch_tables(d_ant_xyz, n_ant, p->nb, p->n_chan, p->d_geom, p->d_info,
+                                    p->d_codes, p->d_cells, p->d_wgt, p->any_uniform, st);
+    if (er.status) return fail(ctx, er);
+    if (p->n_chan)
+        TRY(cudaMemcpyAsync(p->infos.data(), p->d_info, sizeof(ChanInfo) * p->infos.size(),
+                            cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    // support rows per size group, scratch for the large-image path
+    size_t scratch = 0;
+    for (auto &g : p->groups) {
+        int r = 1;
+        for (int k = g.first; k < g.first + g.count; ++k)
+            r = std::max(r, p->infos[size_t(dl[size_t(k)].chan)].rows);
+        g.r_alloc = r;
+        const size_t per = blink::image_scratch_per_layer(g.n_px, r);
+        if (per) scratch = std::max(scratch, std::max(per, std::min(per * size_t(g.count), kScratchCap)));
+    }
+    if (scratch) {
+        void *s = nullptr;
+        e = cudaMallocFromPoolAsync(&s, scratch, ctx->pool, st);
+        if (e != cudaSuccess)
+            return fail(ctx, BLINK_ERR_WORKSPACE, std::string("scratch allocation: ") + cudaGetErrorString(e));
+        p->d_scratch = static_cast<float2 *>(s);
+        p->scratch_bytes = scratch;
+    }
+#undef TRY
+    return BLINK_OK;
+}
+
+blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, const float *d_vis,
+                            void *out, float *d_wsum, uint32_t flags) {
+    blink::ImageArgs a{};
+    a.vis = reinterpret_cast<const float2 *>(d_vis);
+    a.out = out;
+    a.wsum_out = d_wsum;
+    a.layers = p->d_layers + g.first;
+    a.n_layers = g.count;
+    a.chans = p->d_info;
+    a.codes = p->d_codes;
+    a.wgt = p->d_wgt;
+    a.nb = p->nb;
+    a.flags = flags;
+    a.r_alloc = g.r_alloc;
+    a.scratch = p->d_scratch;
+    a.scratch_bytes = p->scratch_bytes;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int blink_abi_version(void) { return BLINK_ABI_VERSION; }
+
+int blink_supported_sizes(int32_t *sizes, int cap) { return blink::supported_sizes(sizes, cap); }
+
+int blink_ctx_create(blink_ctx **out, int device) {
+    if (!out) return BLINK_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return BLINK_ERR_INVALID;
+    blink_ctx *ctx = new (std::nothrow) blink_ctx();
+    if (!ctx) return BLINK_ERR_WORKSPACE;
+    ctx->device = device;
+    DeviceGuard g(device);
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) {
+        delete ctx;
+        return BLINK_ERR_CUDA;
+    }
+    uint64_t keep = std::numeric_limits<uint64_t>::max();
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    *out = ctx;
+    return BLINK_OK;
+}
+
+void blink_ctx_destroy(blink_ctx *ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    }
+    delete ctx;
+}
+
+const char *blink_last_error(const blink_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int blink_plan_create(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+                      int n_layers, blink_plan **out, void *stream) {
+    if (!ctx || !out) return BLINK_ERR_INVALID;
+    *out = nullptr;
+    int st = validate(ctx, d_ant_xyz, n_ant, h_layers, n_layers);
+    if (st) return st;
+    DeviceGuard g(ctx->device);
+    blink_plan *p = new (std::nothrow) blink_plan();
+    if (!p) return fail(ctx, BLINK_ERR_WORKSPACE, "host allocation failed");
+    st = build_plan(ctx, d_ant_xyz, n_ant, h_layers, n_layers, false, p, static_cast<cudaStream_t>(stream));
+    if (st) {
+        free_plan_memory(p, static_cast<cudaStream_t>(stream));
+        delete p;
+        return st;
+    }
+    ctx->err.clear();
+    *out = p;
+    return BLINK_OK;
+}
+
+int blink_plan_image(blink_plan *p, const float *d_vis, float *d_images, float *d_wsum, uint32_t flags,
+                     void *stream) {
+    if (!p) return BLINK_ERR_INVALID;
+    blink_ctx *ctx = p->ctx;
+    if (p->n_layers && (!d_vis || !d_images)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    if (flags & ~uint32_t(BLINK_NORMALIZE)) return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    p->last_stream = st;
+    for (const auto &grp : p->groups) {
+        Error e = blink::launch_image_group(grp.n_px, group_args(p, grp, d_vis, d_images, d_wsum, flags), st);
+        if (e.status) return fail(ctx, e);
+    }
+    return BLINK_OK;
+}
+
+void blink_plan_destroy(blink_plan *p) {
+    if (!p) return;
+    {
+        DeviceGuard g(p->ctx->device);
+        free_plan_memory(p, p->last_stream);
+    }
+    delete p;
+}
+
+int blink_plan_layer_info(const blink_plan *p, int layer, float *wsum, int64_t *n_kept) {
+    if (!p || layer < 0 || layer >= p->n_layers) return BLINK_ERR_INVALID;
+    const ChanInfo &ci = p->infos[size_t(p->layer_chan[size_t(layer)])];
+    if (wsum) *wsum = ci.wsum;
+    if (n_kept) *n_kept = ci.n_kept;
+    return BLINK_OK;
+}
+
+int blink_image_batch(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+                      int n_layers, const float *d_vis, float *d_images, float *d_wsum, uint32_t flags,
+                      void *stream) {
+    blink_plan *p = nullptr;
+    int st = blink_plan_create(ctx, d_ant_xyz, n_ant, h_layers, n_layers, &p, stream);
+    if (st) return st;
+    st = blink_plan_image(p, d_vis, d_images, d_wsum, flags, stream);
+    blink_plan_destroy(p);
+    return st;
+}
+
+int blink_cells(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+                int n_layers, int32_t *d_cells, void *stream) {
+    int st = validate(ctx, d_ant_xyz, n_ant, h_layers, n_layers);
+    if (st) return st;
+    if (n_layers && !d_cells) return fail(ctx, BLINK_ERR_INVALID, "d_cells is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    blink_plan p;
+    st = build_plan(ctx, d_ant_xyz, n_ant, h_layers, n_layers, true, &p, s);
+    if (!st) {
+        Error e = blink::launch_expand_cells(p.d_cells, p.d_layers, n_layers, p.nb,
+                                             reinterpret_cast<int2 *>(d_cells), s);
+        if (e.status) st = fail(ctx, e);
+    }
+    free_plan_memory(&p, s);
+    if (!st) ctx->err.clear();
+    return st;
+}
+
+int blink_grid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+               int n_layers, const float *d_vis, float *d_grid, float *d_wsum, void *stream) {
+    int st = validate(ctx, d_ant_xyz, n_ant, h_layers, n_layers);
+    if (st) return st;
+    if (n_layers && (!d_vis || !d_grid)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    blink_plan p;
+    st = build_plan(ctx, d_ant_xyz, n_ant, h_layers, n_layers, false, &p, s);
+    if (!st) {
+        for (const auto &grp : p.groups) {
+            Error e = blink::launch_grid_group(grp.n_px, group_args(&p, grp, d_vis, d_grid, d_wsum, 0), s);
+            if (e.status) {
+                st = fail(ctx, e);
+                break;
+            }
+        }
+    }
+    free_plan_memory(&p, s);
+    if (!st) ctx->err.clear();
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,42 @@
+// blink_kernels.cuh -- host-side launchers of the library's kernels.
+#pragma once
+
+#include "blink_common.cuh"
+
+namespace blink {
+
+// a1-a2 and weighting tables for n_chan channels (blink_tables.cu).
+// info[] must hold n_px, weighting, code_off, wgt_off and zeroed accumulators;
+// for uniform channels wgt + wgt_off must hold (N/2)*N zeroed int32 counts.
+Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, const ChanGeom *geom,
+                    ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_uniform,
+                    cudaStream_t st);
+Error launch_expand_cells(const int2 *cells, const DevLayer *layers, int n_layers, int64_t nb,
+                          int2 *out, cudaStream_t st);
+
+// Arguments shared by the gridding / imaging launchers (blink_image.cu).
+struct ImageArgs {
+    const float2 *vis;          // visibilities, complex64
+    void *out;                  // images (float) or grids (float2)
+    float *wsum_out;            // [caller layers] or null
+    const DevLayer *layers;     // this group's layers (device)
+    int n_layers;               // layers in the group
+    const ChanInfo *chans;      // device channel table
+    const uint32_t *codes;      // packed canonical cells
+    const float *wgt;           // uniform weights
+    int64_t nb;                 // baselines per layer
+    uint32_t flags;             // BLINK_NORMALIZE ...
+    int r_alloc;                // max support rows over the group's channels
+    float2 *scratch;            // large-image row-transform buffer (or null)
+    size_t scratch_bytes;
+};
+
+bool image_size_supported(int n_px);
+int supported_sizes(int32_t *out, int cap);
+// Bytes of row-transform scratch one layer of size n_px with r_alloc rows needs
+// on the large-image path (0 if the fused single-CTA path takes the group).
+size_t image_scratch_per_layer(int n_px, int r_alloc);
+Error launch_image_group(int n_px, const ImageArgs &a, cudaStream_t st);
+Error launch_grid_group(int n_px, const ImageArgs &a, cudaStream_t st);
+
+}  // namespace blink
