@@ -147,6 +147,44 @@ BLINK_API void blink_plan_destroy(blink_plan *plan);
  * copies; no device work). */
 BLINK_API int blink_plan_layer_info(const blink_plan *plan, int layer, float *wsum, int64_t *n_kept);
 
+/* ------------------------------------------------- allocation-free variant */
+/* The paper has no counterpart of this entry point; it serves callers that
+ * must not allocate device memory while they run -- for example a real-time
+ * telescope pipeline that reserves all GPU memory when an observation starts
+ * and forbids allocation (and its unpredictable latency) afterwards, or a
+ * host framework whose own allocator already owns the whole device.
+ *
+ * Same result as blink_image_batch (a1-a7 on every layer), but it allocates
+ * nothing: no cudaMalloc, no cudaFree, no memory pool, no context.  All of
+ * its scratch -- channel tables, layer descriptors and the row-transform
+ * buffer of large images -- lives in one static device array of
+ * BLINK_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
+ * until the process exits.
+ *
+ * Limits: all layers of a call share one n_px; at most
+ * BLINK_NOALLOC_MAX_CHANNELS distinct (freq_hz, delta_u, weighting) channels;
+ * the tables (4 bytes per baseline per channel, plus N*N/2 floats per
+ * uniform-weighted channel, plus 56 bytes per layer) and one layer's
+ * row-transform buffer (large images only) must fit in the static array.
+ * A request beyond a limit returns BLINK_ERR_WORKSPACE (or BLINK_ERR_INVALID
+ * for mixed sizes) before any launch, with a message in err_msg.
+ *
+ * Runs on the calling thread's current device and on `stream`, which it
+ * synchronises once (like blink_image_batch).  The first call on each device
+ * looks up the device address of the static array (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call reuses the same
+ * array and clears what must start at zero; calls whose GPU work overlaps
+ * (other streams or host threads at the same time) race on it, so serialise
+ * them.  err_msg (may be NULL) receives a NUL-terminated description of a
+ * failure, truncated to err_cap bytes. */
+#define BLINK_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define BLINK_NOALLOC_MAX_CHANNELS 256
+BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int n_ant,
+                                        const blink_layer *h_layers, int n_layers,
+                                        const float *d_vis, float *d_images, float *d_wsum,
+                                        uint32_t flags, void *stream, char *err_msg,
+                                        size_t err_cap);
+
 #ifdef __cplusplus
 }
 #endif

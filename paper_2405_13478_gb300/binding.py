@@ -24,6 +24,7 @@ EXPORTS = (
     "blink_abi_version", "blink_supported_sizes", "blink_ctx_create", "blink_ctx_destroy",
     "blink_last_error", "blink_cells", "blink_grid", "blink_image_batch", "blink_plan_create",
     "blink_plan_image", "blink_plan_destroy", "blink_plan_layer_info",
+    "blink_image_batch_noalloc",
 )
 
 

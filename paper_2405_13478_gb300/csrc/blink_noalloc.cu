@@ -1,0 +1,204 @@
+// blink_noalloc.cu -- dirty images without any device memory allocation.
+//
+// Some callers cannot allocate device memory while they run: a real-time
+// telescope pipeline that reserves all GPU memory when an observation starts
+// and forbids allocation (and its latency) afterwards, or a host framework
+// whose own allocator already owns the whole device.  For them this file
+// provides blink_image_batch_noalloc: the same imaging kernels as
+// blink_image_batch, with every piece of scratch (channel tables, layer
+// descriptors, the row-transform buffer of large images) carved out of one
+// file-scope static device array of BLINK_NOALLOC_SCRATCH_BYTES bytes.  It
+// calls no cudaMalloc, cudaFree or allocating library routine.
+//
+// The array exists once per GPU that loads the library and lives until the
+// process exits.  Every call reuses it: what must start at zero is cleared on
+// each call, and calls whose work overlaps on the GPU (different streams or
+// host threads at the same time) race on it.
+#include "blink.h"
+#include "blink_common.cuh"
+#include "blink_kernels.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+using blink::ChanGeom;
+using blink::ChanInfo;
+using blink::DevLayer;
+
+namespace {
+
+constexpr size_t kBytes = BLINK_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxChannels = BLINK_NOALLOC_MAX_CHANNELS;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_scratch[kBytes];
+
+// Host-side device address of g_scratch, looked up once per device.
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {};
+
+int scratch_address(int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) return BLINK_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return BLINK_ERR_CUDA;
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return BLINK_OK;
+}
+
+int say(char *msg, size_t cap, int status, const char *text) {
+    if (msg && cap) std::snprintf(msg, cap, "%s", text);
+    return status;
+}
+
+size_t up(size_t x) { return (x + 255) / 256 * 256; }
+
+bool same_channel(const blink_layer &a, const ChanGeom &g) {
+    return a.n_px == g.n_px && a.weighting == g.weighting &&
+           std::memcmp(&a.freq_hz, &g.freq_hz, 8) == 0 && std::memcmp(&a.delta_u, &g.delta_u, 8) == 0;
+}
+
+// Caller's layer descriptors -> device work items (channel by exact match).
+__global__ void k_layers(const blink_layer *__restrict__ raw, int n, const ChanGeom *__restrict__ geom,
+                         int n_chan, DevLayer *__restrict__ out) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const blink_layer L = raw[l];
+    int ch = 0;
+    for (int c = 0; c < n_chan; ++c) {
+        const ChanGeom g = geom[c];
+        if (L.n_px == g.n_px && L.weighting == g.weighting &&
+            __double_as_longlong(L.freq_hz) == __double_as_longlong(g.freq_hz) &&
+            __double_as_longlong(L.delta_u) == __double_as_longlong(g.delta_u)) {
+            ch = c;
+            break;
+        }
+    }
+    out[l] = DevLayer{L.vis_offset, L.out_offset, ch, l};
+}
+
+}  // namespace
+
+extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int n_ant,
+                                                   const blink_layer *h_layers, int n_layers,
+                                                   const float *d_vis, float *d_images, float *d_wsum,
+                                                   uint32_t flags, void *stream, char *err_msg,
+                                                   size_t err_cap) {
+    if (err_msg && err_cap) err_msg[0] = '\0';
+    if (n_layers == 0) return BLINK_OK;
+    if (n_ant < 2 || !d_ant_xyz || n_layers < 0 || !h_layers || !d_vis || !d_images)
+        return say(err_msg, err_cap, BLINK_ERR_INVALID, "bad array, layer or data argument");
+    if (flags & ~uint32_t(BLINK_NORMALIZE)) return say(err_msg, err_cap, BLINK_ERR_INVALID, "unknown flags");
+    const int64_t nb = int64_t(n_ant) * (n_ant - 1) / 2;
+    const int n_px = h_layers[0].n_px;
+    // distinct channels in a fixed-size host array (no heap)
+    ChanGeom geoms[kMaxChannels];
+    ChanInfo infos[kMaxChannels];
+    int n_chan = 0, prev = -1;
+    for (int l = 0; l < n_layers; ++l) {
+        const blink_layer &L = h_layers[l];
+        if (L.n_px != n_px)
+            return say(err_msg, err_cap, BLINK_ERR_INVALID, "all layers of one call must share n_px");
+        if (!blink::image_size_supported(L.n_px))
+            return say(err_msg, err_cap, BLINK_ERR_UNSUPPORTED, "image size not supported");
+        if ((L.weighting != BLINK_NATURAL && L.weighting != BLINK_UNIFORM) ||
+            !(std::isfinite(L.freq_hz) && L.freq_hz > 0) || !(std::isfinite(L.delta_u) && L.delta_u > 0) ||
+            L.vis_offset < 0 || L.out_offset < 0)
+            return say(err_msg, err_cap, BLINK_ERR_INVALID, "bad layer descriptor");
+        if (prev >= 0 && same_channel(L, geoms[prev])) continue;
+        int c = 0;
+        while (c < n_chan && !same_channel(L, geoms[c])) ++c;
+        if (c == n_chan) {
+            if (n_chan == kMaxChannels)
+                return say(err_msg, err_cap, BLINK_ERR_WORKSPACE, "more distinct channels than the static limit");
+            geoms[n_chan++] = ChanGeom{L.freq_hz, L.delta_u, L.n_px, L.weighting};
+        }
+        prev = c;
+    }
+    // layout of the static scratch
+    int64_t wgt_total = 0;
+    bool any_uniform = false;
+    for (int c = 0; c < n_chan; ++c) {
+        ChanInfo ci{};
+        ci.n_px = geoms[c].n_px;
+        ci.weighting = geoms[c].weighting;
+        ci.code_off = int64_t(c) * nb;
+        ci.wgt_off = -1;
+        if (ci.weighting == BLINK_UNIFORM) {
+            ci.wgt_off = wgt_total;
+            wgt_total += int64_t(n_px / 2) * n_px;
+            any_uniform = true;
+        }
+        infos[c] = ci;
+    }
+    size_t off = 0;
+    const size_t o_geom = off; off = up(off + sizeof(ChanGeom) * n_chan);
+    const size_t o_info = off; off = up(off + sizeof(ChanInfo) * n_chan);
+    const size_t o_raw = off; off = up(off + sizeof(blink_layer) * size_t(n_layers));
+    const size_t o_layers = off; off = up(off + sizeof(DevLayer) * size_t(n_layers));
+    const size_t o_codes = off; off = up(off + sizeof(uint32_t) * size_t(n_chan) * size_t(nb));
+    const size_t o_wgt = off; off = up(off + sizeof(float) * size_t(wgt_total > 0 ? wgt_total : 1));
+    const size_t o_rows = off;
+    if (off > kBytes)
+        return say(err_msg, err_cap, BLINK_ERR_WORKSPACE,
+                   "request needs more than BLINK_NOALLOC_SCRATCH_BYTES of tables");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return say(err_msg, err_cap, BLINK_ERR_CUDA, "no current device");
+    void *base_v = nullptr;
+    int st = scratch_address(dev, &base_v);
+    if (st) return say(err_msg, err_cap, st, "cudaGetSymbolAddress of the static scratch failed");
+    unsigned char *base = static_cast<unsigned char *>(base_v);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ChanGeom *d_geom = reinterpret_cast<ChanGeom *>(base + o_geom);
+    ChanInfo *d_info = reinterpret_cast<ChanInfo *>(base + o_info);
+    blink_layer *d_raw = reinterpret_cast<blink_layer *>(base + o_raw);
+    DevLayer *d_layers = reinterpret_cast<DevLayer *>(base + o_layers);
+    uint32_t *d_codes = reinterpret_cast<uint32_t *>(base + o_codes);
+    float *d_wgt = reinterpret_cast<float *>(base + o_wgt);
+    float2 *d_rows = reinterpret_cast<float2 *>(base + o_rows);
+#define NA_TRY(call)                                                                      \
+    do {                                                                                  \
+        if ((call) != cudaSuccess) return say(err_msg, err_cap, BLINK_ERR_CUDA, #call);   \
+    } while (0)
+    NA_TRY(cudaMemcpyAsync(d_geom, geoms, sizeof(ChanGeom) * n_chan, cudaMemcpyHostToDevice, s));
+    NA_TRY(cudaMemcpyAsync(d_info, infos, sizeof(ChanInfo) * n_chan, cudaMemcpyHostToDevice, s));
+    NA_TRY(cudaMemcpyAsync(d_raw, h_layers, sizeof(blink_layer) * size_t(n_layers), cudaMemcpyHostToDevice, s));
+    k_layers<<<(n_layers + 255) / 256, 256, 0, s>>>(d_raw, n_layers, d_geom, n_chan, d_layers);
+    NA_TRY(cudaGetLastError());
+    if (any_uniform) NA_TRY(cudaMemsetAsync(d_wgt, 0, sizeof(float) * size_t(wgt_total), s));
+    blink::Error e = blink::launch_tables(d_ant_xyz, n_ant, nb, n_chan, d_geom, d_info, d_codes, nullptr,
+                                          d_wgt, any_uniform, s);
+    if (e.status) return say(err_msg, err_cap, e.status, e.msg.c_str());
+    NA_TRY(cudaMemcpyAsync(infos, d_info, sizeof(ChanInfo) * n_chan, cudaMemcpyDeviceToHost, s));
+    NA_TRY(cudaStreamSynchronize(s));
+#undef NA_TRY
+    int r_alloc = 1;
+    for (int c = 0; c < n_chan; ++c) r_alloc = infos[c].rows > r_alloc ? infos[c].rows : r_alloc;
+    const size_t per_layer = blink::image_scratch_per_layer(n_px, r_alloc);
+    const size_t rows_bytes = kBytes - o_rows;
+    if (per_layer > rows_bytes)
+        return say(err_msg, err_cap, BLINK_ERR_WORKSPACE,
+                   "one layer's row-transform buffer does not fit in BLINK_NOALLOC_SCRATCH_BYTES");
+    blink::ImageArgs a{};
+    a.vis = reinterpret_cast<const float2 *>(d_vis);
+    a.out = d_images;
+    a.wsum_out = d_wsum;
+    a.layers = d_layers;
+    a.n_layers = n_layers;
+    a.chans = d_info;
+    a.codes = d_codes;
+    a.wgt = d_wgt;
+    a.nb = nb;
+    a.flags = flags;
+    a.r_alloc = r_alloc;
+    a.scratch = per_layer ? d_rows : nullptr;
+    a.scratch_bytes = per_layer ? rows_bytes : 0;
+    e = blink::launch_image_group(n_px, a, s);
+    if (e.status) return say(err_msg, err_cap, e.status, e.msg.c_str());
+    return BLINK_OK;
+}
