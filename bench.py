@@ -240,6 +240,9 @@ def run_ours(args):
     B = ws.n_baselines
     N = 180
     layers, total = binding.layer_out_offsets(layers)
+    larr = binding.layer_array([d["n_px"] for d in layers], [d["weighting"] for d in layers],
+                               [d["freq_hz"] for d in layers], [d["delta_u"] for d in layers],
+                               [d["vis_offset"] for d in layers], [d["out_offset"] for d in layers])
     vis = ws.vis("cuda").reshape(-1)                     # complex64, 8.36 GB at 1000 steps
     images = torch.empty(total, dtype=torch.float32, device="cuda")
     wsum = torch.empty(L, dtype=torch.float32, device="cuda")
@@ -248,7 +251,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
-        plan = binding.Plan(ctx, d_xyz, layers)   # a1-a2 + tables (one host sync)
+        plan = binding.Plan(ctx, d_xyz, larr)     # a1-a2 + tables (one host sync)
         if ev:
             ev[0].record(stream)
         plan.image(vis, images, wsum)              # a3-a7
@@ -299,7 +302,7 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(args.e2e_steps):
         d_vis2.copy_(h_vis, non_blocking=True)
-        ctx.image_batch(d_xyz, layers, d_vis2, images, wsum)
+        ctx.image_batch(d_xyz, larr, d_vis2, images, wsum)
         h_img.copy_(images, non_blocking=True)
         h_ws.copy_(wsum, non_blocking=True)
     e1.record(stream)

@@ -91,7 +91,41 @@ def supported_sizes():
     return list(buf)
 
 
-def make_layers(layers: Sequence[dict]):
+LAYER_DTYPE = None
+
+
+def layer_dtype():
+    """numpy structured dtype with the memory layout of blink_layer."""
+    global LAYER_DTYPE
+    if LAYER_DTYPE is None:
+        import numpy as np
+        LAYER_DTYPE = np.dtype([("n_px", "<i4"), ("weighting", "<i4"), ("freq_hz", "<f8"),
+                                ("delta_u", "<f8"), ("vis_offset", "<i8"), ("out_offset", "<i8")])
+        assert LAYER_DTYPE.itemsize == ctypes.sizeof(Layer)
+    return LAYER_DTYPE
+
+
+def layer_array(n_px, weighting, freq_hz, delta_u, vis_offset, out_offset):
+    """Vectorised blink_layer array from equal-length array-likes."""
+    import numpy as np
+    n = len(np.atleast_1d(vis_offset))
+    arr = np.zeros(n, dtype=layer_dtype())
+    arr["n_px"] = n_px
+    arr["weighting"] = weighting
+    arr["freq_hz"] = freq_hz
+    arr["delta_u"] = delta_u
+    arr["vis_offset"] = vis_offset
+    arr["out_offset"] = out_offset
+    return arr
+
+
+def make_layers(layers):
+    """blink_layer array for the C ABI from a list of dicts or a layer_array()."""
+    import numpy as np
+    if isinstance(layers, np.ndarray):
+        if layers.dtype != layer_dtype() or not layers.flags.c_contiguous:
+            raise ValueError("layer arrays must come from layer_array()")
+        return layers.ctypes.data_as(ctypes.POINTER(Layer))
     arr = (Layer * max(1, len(layers)))()
     for k, d in enumerate(layers):
         arr[k] = Layer(int(d["n_px"]), int(d["weighting"]), float(d["freq_hz"]),

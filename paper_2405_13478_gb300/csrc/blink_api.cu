@@ -42,6 +42,9 @@ struct blink_plan {
         int first;
         int count;
         int r_alloc;
+        int sched_ok;   // every channel of the group has a gridding schedule
+        int max_chunk;  // largest staging chunk among those channels
+        int max_seg;    // longest per-chunk schedule segment among them
     };
     std::vector<Group> groups;
     // device memory (one pool allocation for the tables, one for scratch)
@@ -54,6 +57,7 @@ struct blink_plan {
     int2 *d_cells = nullptr;
     float2 *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    unsigned char *d_sched = nullptr;
     cudaStream_t last_stream = nullptr;
 };
 
@@ -141,9 +145,15 @@ int validate(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_lay
 void free_plan_memory(blink_plan *p, cudaStream_t st) {
     if (p->d_block) cudaFreeAsync(p->d_block, st);
     if (p->d_scratch) cudaFreeAsync(p->d_scratch, st);
+    if (p->d_sched) cudaFreeAsync(p->d_sched, st);
     p->d_block = nullptr;
     p->d_scratch = nullptr;
+    p->d_sched = nullptr;
 }
+
+// Images up to this size are gridded by the fused kernels, which can use the
+// register-accumulation schedule.
+constexpr int kSchedMaxPx = 256;
 
 // Builds the channel tables of a plan on `st` and waits for them.
 int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
@@ -183,12 +193,24 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     // channel table offsets
     p->infos.assign(size_t(p->n_chan), ChanInfo{});
     int64_t wgt_total = 0;
+    int64_t sched_total = 0;
     for (int c = 0; c < p->n_chan; ++c) {
         ChanInfo &ci = p->infos[size_t(c)];
         ci.n_px = p->geoms[size_t(c)].n_px;
         ci.weighting = p->geoms[size_t(c)].weighting;
         ci.code_off = int64_t(c) * p->nb;
-        if (ci.weighting == BLINK_UNIFORM) {
+        ci.sched_off = -1;
+        const bool sched = ci.n_px <= kSchedMaxPx;
+        if (sched) {
+            const int q = int((p->nb + blink::kSchedMaxChunk - 1) / blink::kSchedMaxChunk);
+            int k = int((p->nb + q - 1) / q);
+            k += k & 1;
+            ci.n_chunks = q;
+            ci.chunk = k;
+            ci.sched_off = sched_total;
+            sched_total += blink::SchedLayout(ci.n_px, p->nb, q).bytes;
+        }
+        if (ci.weighting == BLINK_UNIFORM || sched) {
             ci.wgt_off = wgt_total;
             wgt_total += int64_t(ci.n_px / 2) * ci.n_px;
             p->any_uniform = true;
@@ -199,15 +221,18 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     // layers grouped by image size, stable within a size
     std::vector<int> order(static_cast<size_t>(n_layers));
     for (int l = 0; l < n_layers; ++l) order[size_t(l)] = l;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return h_layers[a].n_px < h_layers[b].n_px; });
+    bool grouped = true;
+    for (int l = 1; l < n_layers && grouped; ++l) grouped = h_layers[l - 1].n_px <= h_layers[l].n_px;
+    if (!grouped)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return h_layers[a].n_px < h_layers[b].n_px; });
     std::vector<DevLayer> dl(static_cast<size_t>(n_layers));
     for (int k = 0; k < n_layers; ++k) {
         const int l = order[size_t(k)];
         dl[size_t(k)] = DevLayer{h_layers[l].vis_offset, h_layers[l].out_offset,
                                  p->layer_chan[size_t(l)], l};
         if (p->groups.empty() || p->groups.back().n_px != h_layers[l].n_px)
-            p->groups.push_back(blink_plan::Group{h_layers[l].n_px, k, 0, 1});
+            p->groups.push_back(blink_plan::Group{h_layers[l].n_px, k, 0, 1, 0, 0, 0});
         p->groups.back().count++;
     }
     // one device block for every table
@@ -247,8 +272,16 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         TRY(cudaMemcpyAsync(p->d_layers, dl.data(), sizeof(DevLayer) * dl.size(),
                             cudaMemcpyHostToDevice, st));
     if (p->any_uniform) TRY(cudaMemsetAsync(p->d_wgt, 0, sizeof(float) * size_t(wgt_total), st));
+    if (sched_total) {
+        void *sb = nullptr;
+        e = cudaMallocFromPoolAsync(&sb, size_t(sched_total), ctx->pool, st);
+        if (e != cudaSuccess)
+            return fail(ctx, BLINK_ERR_WORKSPACE, std::string("schedule allocation: ") + cudaGetErrorString(e));
+        p->d_sched = static_cast<unsigned char *>(sb);
+        TRY(cudaMemsetAsync(p->d_sched, 0, size_t(sched_total), st));
+    }
     Error er = blink::launch_tables(d_ant_xyz, n_ant, p->nb, p->n_chan, p->d_geom, p->d_info,
-                                    p->d_codes, p->d_cells, p->d_wgt, p->any_uniform, st);
+                                    p->d_codes, p->d_cells, p->d_wgt, p->any_uniform, st, p->d_sched);
     if (er.status) return fail(ctx, er);
     if (p->n_chan)
         TRY(cudaMemcpyAsync(p->infos.data(), p->d_info, sizeof(ChanInfo) * p->infos.size(),
@@ -258,8 +291,16 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     size_t scratch = 0;
     for (auto &g : p->groups) {
         int r = 1;
-        for (int k = g.first; k < g.first + g.count; ++k)
-            r = std::max(r, p->infos[size_t(dl[size_t(k)].chan)].rows);
+        g.sched_ok = p->d_sched != nullptr;
+        g.max_chunk = 0;
+        g.max_seg = 0;
+        for (int k = g.first; k < g.first + g.count; ++k) {
+            const ChanInfo &ci = p->infos[size_t(dl[size_t(k)].chan)];
+            r = std::max(r, ci.rows);
+            g.sched_ok = g.sched_ok && ci.sched_off >= 0 && ci.sched == 1;
+            g.max_chunk = std::max(g.max_chunk, ci.chunk);
+            g.max_seg = std::max(g.max_seg, ci.max_seg);
+        }
         g.r_alloc = r;
         const size_t per = blink::image_scratch_per_layer(g.n_px, r);
         if (per) scratch = std::max(scratch, std::max(per, std::min(per * size_t(g.count), kScratchCap)));
@@ -292,6 +333,10 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.r_alloc = g.r_alloc;
     a.scratch = p->d_scratch;
     a.scratch_bytes = p->scratch_bytes;
+    a.sched = p->d_sched;
+    a.sched_ok = g.sched_ok;
+    a.max_chunk = g.max_chunk;
+    a.max_seg = g.max_seg;
     return a;
 }
 

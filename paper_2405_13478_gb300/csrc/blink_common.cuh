@@ -31,9 +31,53 @@ struct ChanInfo {
     int32_t kmax_u;    // max |k_u| over kept baselines
     int64_t n_kept;    // baselines kept (|k| <= N/2-1)
     float wsum;        // summed weight of all grid entries
-    int32_t pad;
+    int32_t sched;     // 1 if the register-accumulation gridding schedule is built
     int64_t code_off;  // element offset into the packed-code table ([B] per channel)
-    int64_t wgt_off;   // element offset into the weight table ([N/2][N] floats), -1 if natural
+    int64_t wgt_off;   // element offset into the count/weight table ([N/2][N]), -1 if none
+    int32_t m_slots;   // cell slots per thread used by the schedule
+    int32_t n_chunks;  // staging chunks per layer
+    int32_t chunk;     // baselines per staging chunk
+    int32_t stream_len;  // entries in the schedule stream
+    int64_t sched_off;   // byte offset of this channel's schedule block (-1 if none)
+    int32_t max_seg;     // longest per-chunk stream segment (entries)
+    int32_t pad2;
+};
+
+// Register-accumulation gridding schedule (one block per channel).
+//
+// A layer's visibilities are staged in shared memory in n_chunks chunks of
+// `chunk` baselines.  Thread t of the imaging CTA owns up to kSchedSlots
+// occupied canonical cells (slot j of thread t), handed out in order of
+// decreasing entry count so the 32 lanes of a warp carry similar loads.  For
+// chunk q, slot j and warp w the entries of the 32 lanes are interleaved
+// (entry k of lane l at stream[base + 32 k + l]), padded to the longest lane
+// with a sentinel that points at a zero staging element.  An entry is the
+// baseline's index inside the chunk (15 bits) and a conjugate flag (bit 15).
+constexpr int kSchedThreads = 384;
+constexpr int kSchedWarps = kSchedThreads / 32;
+constexpr int kSchedSlots = 16;
+constexpr int kSchedMaxChunk = 8192;        // baselines per staging chunk (64 KB)
+constexpr uint32_t kSlotEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kSlotOrigin = 1u << 30;  // slot is the origin cell: 2 Re(sum) * w
+constexpr uint32_t kSlotMirror = 1u << 31;  // row-0 slot: also write conj at N - c
+
+struct SchedLayout {
+    int64_t cnt_q, rank, cell_slot, slot_pos, slot_w, meta, stream, bytes;
+    int64_t stream_cap;
+    __host__ __device__ SchedLayout(int n_px, int64_t nb, int n_chunks) {
+        const int64_t cells = int64_t(n_px / 2) * n_px;
+        auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
+        int64_t o = 0;
+        cnt_q = o; o = up(o + 4 * cells * n_chunks);
+        rank = o; o = up(o + 4 * nb);
+        cell_slot = o; o = up(o + 4 * cells);
+        slot_pos = o; o = up(o + 4 * int64_t(kSchedSlots) * kSchedThreads);
+        slot_w = o; o = up(o + 4 * int64_t(kSchedSlots) * kSchedThreads);
+        meta = o; o = up(o + 8 * int64_t(n_chunks) * kSchedSlots * kSchedWarps);
+        stream_cap = 4 * nb + 32 * int64_t(n_chunks) * kSchedSlots * kSchedWarps;
+        stream = o; o = up(o + 2 * (stream_cap + 16));
+        bytes = o;
+    }
 };
 
 // Per-layer work item on the device.

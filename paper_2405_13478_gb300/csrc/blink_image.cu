@@ -189,15 +189,176 @@ __device__ __forceinline__ void grid_rows(float2 *G, int S, int r0, int nrows, c
 }
 
 // ------------------------------------------------------------- small path
+// One CTA per layer; every step of a1..a7 after the tables happens in shared
+// memory.  Thread layout: 16-lane groups.  In the four-step A steps a lane is
+// n2 (its twiddles W_N^(n2 k1) live in registers for the whole kernel) and a
+// group is a row (pass 1) or a column pair (pass 2); in pass-1 step B a lane
+// is k1; in pass-2 step B a lane is a column pair so image stores coalesce.
 template <int N>
 struct SmallCfg {
     static constexpr int NT = 384;
-    static constexpr int P = std::min(32, NT / Plan<N>::N1);
+    static constexpr int GROUPS = NT / 16;  // 16-lane groups per CTA
+    static constexpr int P = GROUPS;        // column pairs per pass-2 chunk
+    static_assert(N > 256 || (Plan<N>::N1 <= 16 && Plan<N>::N2 <= 16), "small path needs N1, N2 <= 16");
 };
 
+// Grid one layer into G (stride S) with shared-memory float atomics.  Four
+// baselines per 16-byte code load and two 16-byte visibility loads; two quads
+// in flight per thread before any atomic.
+template <int NT>
+__device__ __forceinline__ void grid_layer_vec(float2 *G, int S, const uint32_t *code,
+                                               const float2 *vis, int64_t nb, int tid) {
+    auto put = [&](uint32_t cd, float re, float im) {
+        if (cd == kCodeDropped) return;
+        float2 *cell = G + code_row(cd) * S + code_col(cd);
+        atomicAdd(&cell->x, re);
+        atomicAdd(&cell->y, code_conj(cd) ? -im : im);
+    };
+    int64_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(code) | reinterpret_cast<uintptr_t>(vis)) & 15) == 0) {
+        const int64_t nq = nb >> 2;
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(code);
+        const float4 *v4 = reinterpret_cast<const float4 *>(vis);
+        for (int64_t q = tid; q < nq; q += 2 * NT) {
+            const bool two = q + NT < nq;
+            const uint4 ca = __ldg(c4 + q);
+            const float4 va = __ldcs(v4 + 2 * q), vb = __ldcs(v4 + 2 * q + 1);
+            uint4 cb = make_uint4(kCodeDropped, kCodeDropped, kCodeDropped, kCodeDropped);
+            float4 vc = make_float4(0.f, 0.f, 0.f, 0.f), vd = vc;
+            if (two) {
+                cb = __ldg(c4 + q + NT);
+                vc = __ldcs(v4 + 2 * (q + NT));
+                vd = __ldcs(v4 + 2 * (q + NT) + 1);
+            }
+            put(ca.x, va.x, va.y);
+            put(ca.y, va.z, va.w);
+            put(ca.z, vb.x, vb.y);
+            put(ca.w, vb.z, vb.w);
+            put(cb.x, vc.x, vc.y);
+            put(cb.y, vc.z, vc.w);
+            put(cb.z, vd.x, vd.y);
+            put(cb.w, vd.z, vd.w);
+        }
+        done = nq << 2;
+    }
+    for (int64_t b = done + tid; b < nb; b += NT) {
+        const float2 v = __ldcs(vis + b);
+        put(__ldg(code + b), v.x, v.y);
+    }
+}
+
+// Both passes of the transform for one layer whose canonical rows [0, R) are
+// in G (stride N + 1), Hermitian-complete in row 0.  Rows >= 1 are multiplied
+// by w_rows (uniform weights, [N/2][N]) on the way in when it is not null.
 template <int N>
-__global__ void __launch_bounds__(SmallCfg<N>::NT) k_image_small(ImageArgs a) {
-    constexpr int NT = SmallCfg<N>::NT, P = SmallCfg<N>::P, S = N + 1, H = N / 2;
+__device__ __forceinline__ void small_transform(float2 *G, float2 *Z, int R, const float *w_rows,
+                                                float *img, float scale, int tid) {
+    constexpr int NT = SmallCfg<N>::NT, GR = SmallCfg<N>::GROUPS, P = SmallCfg<N>::P;
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, S = N + 1, H = N / 2;
+    const int ln = tid & 15, grp = tid >> 4;
+    // four-step twiddles W_N^(n2 k1) for n2 = ln (kept in registers)
+    c32 tw[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) tw[k1] = c_roots<N, +1>.v[(ln * k1) % N];
+
+    // pass 1, step A
+    for (int r = grp; r < R; r += GR) {
+        if (ln < N2) {
+            float2 *row = G + r * S + ln;
+            float2 x[N1];
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+                float2 g = row[N2 * n1];
+                if (w_rows && r > 0) {
+                    const float wv = __ldg(w_rows + r * N + N2 * n1 + ln);
+                    g.x *= wv;
+                    g.y *= wv;
+                }
+                x[n1] = g;
+            }
+            dft<N1, +1>(x);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) row[N2 * k1] = k1 == 0 ? x[0] : cmulc(x[k1], tw[k1]);
+        }
+    }
+    __syncthreads();
+    // pass 1, step B: lanes are k1; result stays in place (transposed order)
+    for (int r = grp; r < R; r += GR) {
+        if (ln < N1) {
+            float2 *run = G + r * S + N2 * ln;
+            float2 y[N2];
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) y[n2] = run[n2];
+            dft<N2, +1>(y);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) run[k2] = y[k2];
+        }
+    }
+    __syncthreads();
+
+    for (int j0 = 0; j0 < H; j0 += P) {
+        // pass 2, step A: group = column pair, lane = n2
+        {
+            const int ja = j0 + grp;
+            if (ja < H && ln < N2) {
+                const int jb = ja + H;
+                const int pa = N2 * (ja % N1) + ja / N1, pb = N2 * (jb % N1) + jb / N1;
+                float2 x[N1];
+#pragma unroll
+                for (int n1 = 0; n1 < N1; ++n1) {
+                    const int k = N2 * n1 + ln;
+                    float2 z = make_float2(0.f, 0.f);
+                    if (k < H) {
+                        if (k < R) {
+                            const float2 u = G[k * S + pa], v = G[k * S + pb];
+                            z = make_float2(u.x - v.y, u.y + v.x);  // H_a + i H_b
+                        }
+                    } else if (k > H) {
+                        const int m = N - k;
+                        if (m < R) {
+                            const float2 u = G[m * S + pa], v = G[m * S + pb];
+                            z = make_float2(u.x + v.y, v.x - u.y);  // conj(H_a) + i conj(H_b)
+                        }
+                    }
+                    x[n1] = z;
+                }
+                dft<N1, +1>(x);
+                float2 *zp = Z + grp * S + ln;
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) zp[N2 * k1] = k1 == 0 ? x[0] : cmulc(x[k1], tw[k1]);
+            }
+        }
+        __syncthreads();
+        // pass 2, step B: lane = column pair (coalesced stores), warp = k1
+        {
+            const int jj = tid & 31, ja = j0 + jj;
+            if (jj < P && ja < H) {
+                for (int k1 = tid >> 5; k1 < N1; k1 += NT / 32) {
+                    const float2 *zp = Z + jj * S + N2 * k1;
+                    float2 y[N2];
+#pragma unroll
+                    for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[n2];
+                    dft<N2, +1>(y);
+#pragma unroll
+                    for (int k2 = 0; k2 < N2; ++k2) {
+                        const int q = k1 + N1 * k2;
+                        const int row = q < H ? q + H : q - H;
+                        float *o = img + int64_t(row) * N;
+                        __stcs(o + ja + H, y[k2].x * scale);
+                        __stcs(o + ja, y[k2].y * scale);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Fused layer with shared-memory float atomics for the gridding (used when a
+// channel has no register-accumulation schedule).
+template <int N>
+__global__ void __launch_bounds__(SmallCfg<N>::NT, 2) k_image_small(ImageArgs a) {
+    constexpr int NT = SmallCfg<N>::NT, S = N + 1, H = N / 2;
     extern __shared__ float2 sm[];
     const DevLayer L = a.layers[blockIdx.x];
     const ChanInfo ci = a.chans[L.chan];
@@ -205,22 +366,179 @@ __global__ void __launch_bounds__(SmallCfg<N>::NT) k_image_small(ImageArgs a) {
     float2 *G = sm;
     float2 *Z = sm + size_t(a.r_alloc) * S;
     const int tid = threadIdx.x;
-    for (int i = tid; i < R * S; i += NT) G[i] = make_float2(0.f, 0.f);
+    const float *w = ci.weighting == 1 ? a.wgt + ci.wgt_off : nullptr;
+    {
+        float4 *g4 = reinterpret_cast<float4 *>(G);
+        const int n4 = (R * S) >> 1;
+        for (int i = tid; i < n4; i += NT) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (((R * S) & 1) && tid == 0) G[R * S - 1] = make_float2(0.f, 0.f);
+    }
     __syncthreads();
-    grid_rows<NT>(G, S, 0, R, a.codes + ci.code_off, a.vis + L.vis_off, a.nb, tid);
+    grid_layer_vec<NT>(G, S, a.codes + ci.code_off, a.vis + L.vis_off, a.nb, tid);
     __syncthreads();
-    weight_and_complete<N>(G, S, 0, R, ci, a.wgt, tid, NT);
+    // row 0: weights, origin doubling and Hermitian completion
+    for (int c = tid; c < H; c += NT) {
+        const float wv = w ? w[c] : 1.f;
+        const float2 g = G[c];
+        if (c == 0) {
+            G[0] = make_float2(2.f * g.x * wv, 0.f);
+        } else {
+            G[c] = make_float2(g.x * wv, g.y * wv);
+            G[N - c] = make_float2(g.x * wv, -g.y * wv);
+        }
+    }
     __syncthreads();
-    rows_fft<N>(G, S, R, tid, NT);
     const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
-    float *img = static_cast<float *>(a.out) + L.out_off;
-    auto hrow = [&](int k, int p) { return G[k * S + pos_after_rows<N>(p)]; };
-    for (int j0 = 0; j0 < H; j0 += P) {
-        cols_step_a<N, P>(Z, S, R, j0, hrow, tid, NT);
+    small_transform<N>(G, Z, R, w, static_cast<float *>(a.out) + L.out_off, scale, tid);
+    if (tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return uint32_t(__cvta_generic_to_shared(p));
+}
+
+// Copy n complex64 values global -> shared with cp.async (16-byte pieces
+// when the source is 16-byte aligned, else 8-byte pieces).  No wait here.
+template <int NT>
+__device__ __forceinline__ void stage_async(float2 *dst, const float2 *src, int n, int tid) {
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int n2 = n >> 1;
+        for (int i = tid; i < n2; i += NT)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst + 2 * i)),
+                         "l"(src + 2 * i)
+                         : "memory");
+        if ((n & 1) && tid == 0)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst + n - 1)),
+                         "l"(src + n - 1)
+                         : "memory");
+    } else {
+        for (int i = tid; i < n; i += NT)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst + i)), "l"(src + i)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared-memory layout of the staging phase of k_image_sched: the chunk's
+// visibilities (plus one zero element, the sentinel target), the chunk's
+// stream segment (16-byte aligned copy) and its (slot, warp) metadata.
+struct StageLayout {
+    int vis, ent, meta, bytes;
+    __host__ __device__ StageLayout(int chunk, int max_seg, int m_slots) {
+        auto up16 = [](int x) { return (x + 15) / 16 * 16; };
+        vis = 0;
+        ent = up16((chunk + 1) * 8);
+        meta = up16(ent + (max_seg + 16) * 2);
+        bytes = meta + m_slots * kSchedWarps * 8;
+    }
+};
+
+template <int NT>
+__device__ __forceinline__ void cp16_async(void *dst, const void *src, int n16, int tid) {
+    for (int i = tid; i < n16; i += NT)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(static_cast<char *>(dst) + 16 * i)),
+                     "l"(static_cast<const char *>(src) + 16 * i)
+                     : "memory");
+}
+
+// Fused layer with atomic-free gridding: for every chunk the visibilities,
+// the chunk's entry stream and its metadata go to shared memory with
+// cp.async; each thread gathers the entries of the cells it owns into
+// registers (schedule in ChanInfo / SchedLayout), then writes every owned cell
+// once, weighted, with row 0 completed.  Results do not depend on the plan.
+template <int N>
+__global__ void __launch_bounds__(SmallCfg<N>::NT, 2) k_image_sched(ImageArgs a) {
+    constexpr int NT = SmallCfg<N>::NT, S = N + 1;
+    static_assert(NT == kSchedThreads, "schedule built for a different CTA size");
+    extern __shared__ float2 sm[];
+    const DevLayer L = a.layers[blockIdx.x];
+    const ChanInfo ci = a.chans[L.chan];
+    const int R = ci.rows, Q = ci.n_chunks, K = ci.chunk, M = ci.m_slots;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SchedLayout lay(N, a.nb, Q);
+    const StageLayout sl(a.max_chunk, a.max_seg, kSchedSlots);
+    const unsigned char *blk = a.sched + ci.sched_off;
+    const uint2 *meta_g = reinterpret_cast<const uint2 *>(blk + lay.meta);
+    const uint16_t *stream_g = reinterpret_cast<const uint16_t *>(blk + lay.stream);
+    char *smc = reinterpret_cast<char *>(sm);
+    float2 *stage = reinterpret_cast<float2 *>(smc + sl.vis);
+    const uint16_t *ent = reinterpret_cast<const uint16_t *>(smc + sl.ent);
+    const uint2 *meta = reinterpret_cast<const uint2 *>(smc + sl.meta);
+    const float2 *vis = a.vis + L.vis_off;
+
+    float2 acc[kSchedSlots];
+#pragma unroll
+    for (int j = 0; j < kSchedSlots; ++j) acc[j] = make_float2(0.f, 0.f);
+    if (tid == 0) stage[K] = make_float2(0.f, 0.f);  // sentinel target
+    const int per_chunk = M * kSchedWarps;
+    for (int q = 0; q < Q; ++q) {
+        const int64_t rem = a.nb - int64_t(q) * K;
+        const int n_q = int(rem < K ? rem : int64_t(K));
+        const int s_beg = int(meta_g[q * per_chunk].x);
+        const int s_end = q + 1 < Q ? int(meta_g[(q + 1) * per_chunk].x) : ci.stream_len;
+        const int s0 = s_beg & ~7;
+        stage_async<NT>(stage, vis + int64_t(q) * K, n_q, tid);
+        cp16_async<NT>(smc + sl.ent, stream_g + s0, (s_end - s0 + 7) >> 3, tid);
+        cp16_async<NT>(smc + sl.meta, meta_g + q * per_chunk, per_chunk >> 1, tid);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        stage_wait();
         __syncthreads();
-        cols_step_b<N, P>(Z, S, j0, img, scale, tid, NT);
+        const int shift = -s0;
+#pragma unroll
+        for (int j = 0; j < kSchedSlots; ++j) {
+            if (j < M) {
+                const uint2 m = meta[j * kSchedWarps + warp];
+                const uint16_t *e = ent + int(m.x) + shift + lane;
+                float2 s = make_float2(0.f, 0.f);
+#pragma unroll 4
+                for (uint32_t k = 0; k < m.y; ++k) {
+                    const uint32_t code = e[32 * k];
+                    const float2 v = stage[code & 0x7FFFu];
+                    s.x += v.x;
+                    s.y += (code & 0x8000u) ? -v.y : v.y;
+                }
+                acc[j].x += s.x;
+                acc[j].y += s.y;
+            }
+        }
         __syncthreads();
     }
+    // the staging area becomes the grid: zero the support rows, write the slots
+    float2 *G = sm;
+    float2 *Z = sm + size_t(a.r_alloc) * S;
+    {
+        float4 *g4 = reinterpret_cast<float4 *>(G);
+        const int n4 = (R * S) >> 1;
+        for (int i = tid; i < n4; i += NT) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (((R * S) & 1) && tid == 0) G[R * S - 1] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    {
+        const uint32_t *slot_pos = reinterpret_cast<const uint32_t *>(blk + lay.slot_pos);
+        const float *slot_w = reinterpret_cast<const float *>(blk + lay.slot_w);
+#pragma unroll
+        for (int j = 0; j < kSchedSlots; ++j) {
+            if (j < M) {
+                const uint32_t sp = __ldg(slot_pos + j * NT + tid);
+                if (sp != kSlotEmpty) {
+                    const float wv = __ldg(slot_w + j * NT + tid);
+                    const int p = int(sp & 0x3FFFFFFFu);
+                    if (sp & kSlotOrigin) {
+                        G[p] = make_float2(2.f * acc[j].x * wv, 0.f);
+                    } else {
+                        const float2 g = make_float2(acc[j].x * wv, acc[j].y * wv);
+                        G[p] = g;
+                        if (sp & kSlotMirror) G[N - p] = make_float2(g.x, -g.y);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
+    small_transform<N>(G, Z, R, nullptr, static_cast<float *>(a.out) + L.out_off, scale, tid);
     if (tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
 }
 
@@ -356,7 +674,11 @@ constexpr size_t kSmallSmemLimit = 200 * 1024;
 
 template <int N>
 bool use_small(int r_alloc) {
-    return N <= 256 && small_smem<N>(r_alloc) <= kSmallSmemLimit;
+    if constexpr (N <= 256) {
+        return small_smem<N>(r_alloc) <= kSmallSmemLimit;
+    } else {
+        return false;
+    }
 }
 
 template <int N>
@@ -364,14 +686,16 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     if (a.n_layers == 0) return Error{0, ""};
     if constexpr (N <= 256) {
       if (use_small<N>(a.r_alloc)) {
-        const size_t smem = small_smem<N>(a.r_alloc);
-        BLINK_CUDA_TRY(cudaFuncSetAttribute(k_image_small<N>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        size_t smem = small_smem<N>(a.r_alloc);
+        const bool sched = a.sched && a.sched_ok;
+        if (sched) smem = std::max(smem, size_t(StageLayout(a.max_chunk, a.max_seg, kSchedSlots).bytes));
+        auto kern = sched ? k_image_sched<N> : k_image_small<N>;
+        BLINK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         for (int l0 = 0; l0 < a.n_layers; l0 += 1 << 30) {
             ImageArgs b = a;
             b.layers = a.layers + l0;
             const int cnt = std::min(a.n_layers - l0, 1 << 30);
-            k_image_small<N><<<cnt, SmallCfg<N>::NT, smem, st>>>(b);
+            kern<<<cnt, SmallCfg<N>::NT, smem, st>>>(b);
             BLINK_CUDA_TRY(cudaGetLastError());
         }
         return Error{0, ""};

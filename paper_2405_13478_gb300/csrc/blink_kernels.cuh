@@ -6,11 +6,15 @@
 namespace blink {
 
 // a1-a2 and weighting tables for n_chan channels (blink_tables.cu).
-// info[] must hold n_px, weighting, code_off, wgt_off and zeroed accumulators;
-// for uniform channels wgt + wgt_off must hold (N/2)*N zeroed int32 counts.
+// info[] must hold n_px, weighting, code_off, wgt_off, the schedule fields
+// and zeroed accumulators; channels with wgt_off >= 0 must have (N/2)*N
+// zeroed int32 counts at wgt + wgt_off (they become 1/n weights for uniform
+// weighting).
+// sched (may be null): per-channel schedule blocks at ChanInfo::sched_off,
+// zeroed, for channels imaged by the register-accumulation gridding.
 Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, const ChanGeom *geom,
-                    ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_uniform,
-                    cudaStream_t st);
+                    ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_counts,
+                    cudaStream_t st, unsigned char *sched = nullptr);
 Error launch_expand_cells(const int2 *cells, const DevLayer *layers, int n_layers, int64_t nb,
                           int2 *out, cudaStream_t st);
 
@@ -29,6 +33,10 @@ struct ImageArgs {
     int r_alloc;                // max support rows over the group's channels
     float2 *scratch;            // large-image row-transform buffer (or null)
     size_t scratch_bytes;
+    const unsigned char *sched; // register-accumulation schedules (or null)
+    int sched_ok;               // every channel of the group has a schedule
+    int max_chunk;              // largest staging chunk of the group's channels
+    int max_seg;                // longest per-chunk schedule segment (entries)
 };
 
 bool image_size_supported(int n_px);

@@ -42,11 +42,18 @@ __device__ __forceinline__ bool axis_cell(double w, double delta_u, int n_px, in
 __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t nb,
                         const ChanGeom *__restrict__ geom, ChanInfo *__restrict__ info,
                         uint32_t *__restrict__ codes, int2 *__restrict__ cells,
-                        int32_t *__restrict__ counts) {
+                        int32_t *__restrict__ counts, unsigned char *__restrict__ sched) {
     const int ch = blockIdx.y;
     const ChanGeom g = geom[ch];
-    const int64_t code_off = info[ch].code_off;
-    int32_t *cnt = (counts && g.weighting == 1) ? counts + info[ch].wgt_off : nullptr;
+    const ChanInfo ci0 = info[ch];
+    const int64_t code_off = ci0.code_off;
+    int32_t *cnt = (counts && ci0.wgt_off >= 0) ? counts + ci0.wgt_off : nullptr;
+    int32_t *cnt_q = nullptr, *rank = nullptr;
+    if (sched && ci0.sched_off >= 0) {
+        const SchedLayout lay(g.n_px, nb, ci0.n_chunks);
+        cnt_q = reinterpret_cast<int32_t *>(sched + ci0.sched_off + lay.cnt_q);
+        rank = reinterpret_cast<int32_t *>(sched + ci0.sched_off + lay.rank);
+    }
     __shared__ double s_lambda;
     if (threadIdx.x == 0) s_lambda = __ddiv_rn(kSpeedOfLight, g.freq_hz);  // lambda = c / nu
     __syncthreads();
@@ -73,7 +80,12 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
             row = r;
             kabs = abs(ku);
             kept = 1;
-            if (cnt) atomicAdd(cnt + int64_t(r) * n + c, 1);
+            const int64_t cell = int64_t(r) * n + c;
+            if (cnt) atomicAdd(cnt + cell, 1);
+            if (cnt_q) {
+                const int q = int(b / ci0.chunk);
+                rank[b] = atomicAdd(cnt_q + int64_t(q) * (n / 2) * n + cell, 1);
+            }
         } else {
             ku = kDropped;
             kv = kDropped;
@@ -135,6 +147,181 @@ __global__ void k_finalize(ChanInfo *__restrict__ info, float *__restrict__ wgt)
     (void)h;
 }
 
+// Register-accumulation schedule, step 1 (one CTA per scheduled channel):
+// hand the occupied cells out to (slot j, thread t) in order of decreasing
+// entry count, then size every (chunk, slot, warp) block of the entry stream
+// to its longest lane.  Falls back (sched = 0) when the cells need more than
+// kSchedSlots slots per thread or the padded stream outgrows its buffer.
+constexpr int kHistBins = 1024;
+constexpr int kMaxItems = 4096;
+
+__global__ void __launch_bounds__(1024) k_sched_slots(ChanInfo *__restrict__ info, const float *__restrict__ wgt,
+                                                      unsigned char *__restrict__ sched, int64_t nb) {
+    const int ch = blockIdx.x;
+    ChanInfo ci = info[ch];
+    if (ci.sched_off < 0) return;
+    const int n = ci.n_px, S = n + 1, R = max(ci.rows, 1), Q = ci.n_chunks;
+    const SchedLayout lay(n, nb, Q);
+    unsigned char *blk = sched + ci.sched_off;
+    const int32_t *cnt = reinterpret_cast<const int32_t *>(wgt + ci.wgt_off);
+    const int32_t *cnt_q = reinterpret_cast<const int32_t *>(blk + lay.cnt_q);
+    int32_t *cell_slot = reinterpret_cast<int32_t *>(blk + lay.cell_slot);
+    uint32_t *slot_pos = reinterpret_cast<uint32_t *>(blk + lay.slot_pos);
+    float *slot_w = reinterpret_cast<float *>(blk + lay.slot_w);
+    uint2 *meta = reinterpret_cast<uint2 *>(blk + lay.meta);
+    __shared__ int hist[kHistBins];
+    __shared__ int cursor[kHistBins];
+    __shared__ int items_l[kMaxItems];
+    __shared__ int s_occ, s_ok;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < kHistBins; i += nt) hist[i] = 0;
+    if (tid == 0) s_occ = 0;
+    __syncthreads();
+    const int cells = R * n;
+    int occ = 0;
+    for (int idx = tid; idx < cells; idx += nt) {
+        const int m = cnt[idx];
+        if (m > 0) {
+            atomicAdd(&hist[min(m, kHistBins - 1)], 1);
+            ++occ;
+        }
+    }
+    atomicAdd(&s_occ, occ);
+    __syncthreads();
+    const int n_occ = s_occ;
+    const int M = (n_occ + kSchedThreads - 1) / kSchedThreads;
+    const int items = Q * max(M, 1) * kSchedWarps;
+    if (M == 0 || M > kSchedSlots || items > kMaxItems) {
+        if (tid == 0) {
+            info[ch].sched = 0;
+        }
+        return;
+    }
+    if (tid == 0) {
+        int acc = 0;  // bucket starts, largest counts first
+        for (int b = kHistBins - 1; b >= 1; --b) {
+            cursor[b] = acc;
+            acc += hist[b];
+        }
+    }
+    for (int i = tid; i < kSchedSlots * kSchedThreads; i += nt) {
+        slot_pos[i] = kSlotEmpty;
+        slot_w[i] = 0.f;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < cells; idx += nt) {
+        const int m = cnt[idx];
+        if (m <= 0) continue;
+        const int i = atomicAdd(&cursor[min(m, kHistBins - 1)], 1);
+        const int t = i % kSchedThreads, j = i / kSchedThreads;
+        const int r = idx / n, c = idx % n;
+        uint32_t pos = uint32_t(r * S + c);
+        const bool origin = idx == 0;
+        if (origin) pos |= kSlotOrigin;
+        else if (r == 0) pos |= kSlotMirror;
+        float w = 1.f;
+        if (ci.weighting == 1) w = __frcp_rn(float(origin ? 2 * m : m));
+        slot_pos[j * kSchedThreads + t] = pos;
+        slot_w[j * kSchedThreads + t] = w;
+        cell_slot[idx] = (j << 16) | t;
+    }
+    __syncthreads();
+    const int64_t cells_all = int64_t(n / 2) * n;
+    for (int it = tid; it < items; it += nt) {
+        const int q = it / (M * kSchedWarps), j = (it / kSchedWarps) % M, w = it % kSchedWarps;
+        int L = 0;
+        for (int lane = 0; lane < 32; ++lane) {
+            const uint32_t sp = slot_pos[j * kSchedThreads + w * 32 + lane];
+            if (sp == kSlotEmpty) continue;
+            const int p = int(sp & 0x3FFFFFFFu);
+            const int cell = (p / S) * n + (p % S);
+            L = max(L, cnt_q[int64_t(q) * cells_all + cell]);
+        }
+        items_l[it] = L;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int64_t acc = 0, seg = 0, max_seg = 0;
+        const int per_chunk = M * kSchedWarps;
+        for (int it = 0; it < items; ++it) {
+            if (it % per_chunk == 0) seg = 0;
+            meta[it] = make_uint2(uint32_t(acc), uint32_t(items_l[it]));
+            acc += 32 * int64_t(items_l[it]);
+            seg += 32 * int64_t(items_l[it]);
+            max_seg = max(max_seg, seg);
+        }
+        s_ok = acc <= lay.stream_cap;
+        info[ch].stream_len = int32_t(acc);
+        info[ch].max_seg = int32_t(max_seg);
+        info[ch].m_slots = M;
+        info[ch].sched = s_ok;
+    }
+}
+
+// Step 2: every stream entry starts as the sentinel (index `chunk`, a zero
+// staging element); step 3 then overwrites the real entries.
+__global__ void k_sched_fill(const ChanInfo *__restrict__ info, unsigned char *__restrict__ sched, int64_t nb) {
+    const ChanInfo ci = info[blockIdx.y];
+    if (ci.sched_off < 0 || !ci.sched) return;
+    const SchedLayout lay(ci.n_px, nb, ci.n_chunks);
+    uint16_t *stream = reinterpret_cast<uint16_t *>(sched + ci.sched_off + lay.stream);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < ci.stream_len;
+         i += int64_t(gridDim.x) * blockDim.x)
+        stream[i] = uint16_t(ci.chunk);
+}
+
+// Step 3: place every kept baseline in its lane's interleaved run.
+__global__ void k_sched_entries(const ChanInfo *__restrict__ info, const uint32_t *__restrict__ codes,
+                                unsigned char *__restrict__ sched, int64_t nb) {
+    const int ch = blockIdx.y;
+    const ChanInfo ci = info[ch];
+    if (ci.sched_off < 0 || !ci.sched) return;
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const uint32_t cd = codes[ci.code_off + b];
+    if (cd == kCodeDropped) return;
+    const int n = ci.n_px;
+    const SchedLayout lay(n, nb, ci.n_chunks);
+    const unsigned char *blk = sched + ci.sched_off;
+    const int32_t *cell_slot = reinterpret_cast<const int32_t *>(blk + lay.cell_slot);
+    const int32_t *rank = reinterpret_cast<const int32_t *>(blk + lay.rank);
+    const uint2 *meta = reinterpret_cast<const uint2 *>(blk + lay.meta);
+    uint16_t *stream = reinterpret_cast<uint16_t *>(sched + ci.sched_off + lay.stream);
+    const int cell = int(code_row(cd)) * n + int(code_col(cd));
+    const int cs = cell_slot[cell];
+    const int j = cs >> 16, t = cs & 0xFFFF;
+    const int q = int(b / ci.chunk);
+    const uint2 m = meta[(q * ci.m_slots + j) * kSchedWarps + t / 32];
+    const int64_t e = int64_t(m.x) + int64_t(rank[b]) * 32 + (t & 31);
+    stream[e] = uint16_t((b - int64_t(q) * ci.chunk) | (code_conj(cd) << 15));
+}
+
+// Step 4: order every lane's run by baseline index (the atomic placement of
+// step 3 is in arbitrary order), so each cell sums its visibilities in
+// baseline order and the images do not depend on how the plan was built.
+__global__ void k_sched_sort(const ChanInfo *__restrict__ info, unsigned char *__restrict__ sched, int64_t nb) {
+    const ChanInfo ci = info[blockIdx.y];
+    if (ci.sched_off < 0 || !ci.sched) return;
+    const SchedLayout lay(ci.n_px, nb, ci.n_chunks);
+    const uint2 *meta = reinterpret_cast<const uint2 *>(sched + ci.sched_off + lay.meta);
+    uint16_t *stream = reinterpret_cast<uint16_t *>(sched + ci.sched_off + lay.stream);
+    const int items = ci.n_chunks * ci.m_slots * kSchedThreads;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+        const int t = it % kSchedThreads, qj = it / kSchedThreads;
+        const uint2 m = meta[qj * kSchedWarps + t / 32];
+        uint16_t *e = stream + m.x + (t & 31);
+        for (uint32_t a = 1; a < m.y; ++a) {  // insertion sort on the low 15 bits
+            const uint16_t v = e[32 * a];
+            uint32_t b = a;
+            while (b > 0 && (e[32 * (b - 1)] & 0x7FFFu) > (v & 0x7FFFu)) {
+                e[32 * b] = e[32 * (b - 1)];
+                --b;
+            }
+            e[32 * b] = v;
+        }
+    }
+}
+
 // Per-layer copy of the per-channel signed cells (blink_cells).
 __global__ void k_expand_cells(const int2 *__restrict__ cells, const DevLayer *__restrict__ layers,
                                int n_layers, int64_t nb, int2 *__restrict__ out) {
@@ -147,14 +334,24 @@ __global__ void k_expand_cells(const int2 *__restrict__ cells, const DevLayer *_
 }
 
 Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, const ChanGeom *geom,
-                    ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_uniform,
-                    cudaStream_t st) {
+                    ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_counts,
+                    cudaStream_t st, unsigned char *sched) {
     if (n_chan == 0) return Error{0, ""};
     const int tpb = 256;
     dim3 grid(unsigned((nb + tpb - 1) / tpb), unsigned(n_chan));
     k_cells<<<grid, tpb, 0, st>>>(ant_xyz, n_ant, nb, geom, info, codes, cells,
-                                  any_uniform ? reinterpret_cast<int32_t *>(wgt) : nullptr);
+                                  any_counts ? reinterpret_cast<int32_t *>(wgt) : nullptr, sched);
     BLINK_CUDA_TRY(cudaGetLastError());
+    if (sched) {
+        k_sched_slots<<<n_chan, 1024, 0, st>>>(info, wgt, sched, nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_sched_fill<<<dim3(64, unsigned(n_chan)), 256, 0, st>>>(info, sched, nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_sched_entries<<<grid, tpb, 0, st>>>(info, codes, sched, nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_sched_sort<<<dim3(32, unsigned(n_chan)), 256, 0, st>>>(info, sched, nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+    }
     k_finalize<<<n_chan, 512, 0, st>>>(info, wgt);
     BLINK_CUDA_TRY(cudaGetLastError());
     return Error{0, ""};

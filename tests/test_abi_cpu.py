@@ -66,3 +66,20 @@ def test_ctx_create_without_gpu_returns_error(lib):
     h = ctypes.c_void_p()
     assert lib.blink_ctx_create(ctypes.byref(h), 0) != 0
     assert not h.value
+
+
+def test_layer_array_matches_the_c_struct():
+    import ctypes
+
+    import numpy as np
+
+    from paper_2405_13478_gb300 import binding
+    arr = binding.layer_array([180, 256], [1, 0], [1.5e8, 1.6e8], [0.5, 0.25], [0, 32640],
+                              [0, 32400])
+    assert arr.itemsize == ctypes.sizeof(binding.Layer) == 40
+    p = binding.make_layers(arr)
+    assert p[1].n_px == 256 and p[1].weighting == 0 and p[1].freq_hz == 1.6e8
+    assert p[1].delta_u == 0.25 and p[1].vis_offset == 32640 and p[1].out_offset == 32400
+    d = binding.make_layers([dict(n_px=180, weighting=1, freq_hz=1.5e8, delta_u=0.5,
+                                  vis_offset=0, out_offset=0)])
+    assert bytes(d[0]) == np.asarray(arr[0:1]).tobytes()

@@ -356,3 +356,21 @@ def test_config2_full_batch_sampled_layers(torch, ctx):
     # summed weight depends only on the channel
     assert np.array_equal(w.reshape(1000, 32), np.broadcast_to(w[:32], (1000, 32)))
     del vis, out
+
+
+def test_scheduled_gridding_is_bit_reproducible(torch, ctx):
+    # The station workload uses the atomic-free register-accumulation
+    # gridding: every cell sums its visibilities in a fixed order, so two runs
+    # give the same bits.
+    from paper_2405_13478_gb300 import binding
+    ws = synth.config2(seed=14, n_times=2)
+    layers, vis = ws_sub(ws, [0, 1], list(range(0, 32, 3)))
+    layers, total = binding.layer_out_offsets(layers)
+    d_xyz = to_dev(torch, ws.ant_xyz)
+    d_vis = vis.reshape(-1).cuda()
+    a = torch.empty(total, device="cuda")
+    b = torch.empty(total, device="cuda")
+    ctx.image_batch(d_xyz, layers, d_vis, a)
+    ctx.image_batch(d_xyz, layers, d_vis, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
