@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "dirty images/s and Gvis/s gridded on 1 GB300, % roofline, error vs FP64 oracle"
 UNIT = "images/s"
-KERNEL = "k_image_small<180>"
+KERNEL = "k_image_sched<180>"
 CSRC = os.path.join(ROOT, "paper_2405_13478_gb300", "csrc")
 
 
@@ -288,32 +288,27 @@ def run_ours(args):
     value = world * L * args.steps / (ms / 1e3)
     err = sampled_error(ctx, ws, d_xyz, vis, images, layers) if rank == 0 else None
 
-    # e2e: host buffers, copies inside the timed region (pinned host memory)
+    # e2e: the host-buffer entry point (pinned host memory), copies inside the
+    # timed region, overlapped with the kernels by the library's pipeline
     h_vis = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
     h_vis.copy_(vis)
     h_img = torch.empty(images.shape, dtype=images.dtype, pin_memory=True)
     h_ws = torch.empty(wsum.shape, dtype=wsum.dtype, pin_memory=True)
-    d_vis2 = torch.empty_like(vis)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    del vis
     if pg:
         pg.barrier()
-    e0.record(stream)
+    t_e2e = time.perf_counter()
     for _ in range(args.e2e_steps):
-        d_vis2.copy_(h_vis, non_blocking=True)
-        ctx.image_batch(d_xyz, larr, d_vis2, images, wsum)
-        h_img.copy_(images, non_blocking=True)
-        h_ws.copy_(wsum, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+        ctx.image_batch_host(ws.ant_xyz, larr, h_vis, h_img, h_ws)
+    e2e_ms = (time.perf_counter() - t_e2e) * 1e3
     if pg:
         t = torch.tensor([e2e_ms], device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_value = world * L * args.e2e_steps / (e2e_ms / 1e3)
-    del h_vis, d_vis2
+    h2d_bytes = int(h_vis.numel() * 8)
+    del h_vis
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -346,7 +341,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": int(vis.numel() * 8),
+                    "h2d_bytes_per_step": h2d_bytes,
                     "d2h_bytes_per_step": int(images.numel() * 4 + wsum.numel() * 4)},
             "gpu_launches": 3 * args.steps,
         }

@@ -131,6 +131,20 @@ BLINK_API int blink_image_batch(blink_ctx *ctx, const double *d_ant_xyz, int n_a
                       const blink_layer *h_layers, int n_layers, const float *d_vis,
                       float *d_images, float *d_wsum, uint32_t flags, void *stream);
 
+/* -------------------------------------------------- host-resident buffers */
+/* blink_image_batch for data in host memory: h_ant_xyz, h_vis and h_images
+ * (and h_wsum, may be NULL) are host pointers addressed like their d_
+ * counterparts.  The call builds the plan once, then streams the layers in
+ * chunks through double-buffered device staging: the host-to-device copy of
+ * chunk i+1 and the device-to-host copy of chunk i-1 overlap the kernels of
+ * chunk i (the copy/compute overlap and pinned host memory suggested in the
+ * paper's summary, Sec. 7).  Pinned host memory (cudaHostAlloc /
+ * cudaHostRegister) gives full copy bandwidth; pageable memory works but
+ * serialises the copies.  Returns after the images are in h_images. */
+BLINK_API int blink_image_batch_host(blink_ctx *ctx, const double *h_ant_xyz, int n_ant,
+                                     const blink_layer *h_layers, int n_layers, const float *h_vis,
+                                     float *h_images, float *h_wsum, uint32_t flags, void *stream);
+
 /* ------------------------------------------------------------------ plans */
 /* A plan fixes the array and the layer descriptors, runs a1-a2 and the
  * weighting tables once (on `stream`, which it synchronises once), and keeps

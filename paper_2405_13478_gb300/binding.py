@@ -24,7 +24,7 @@ EXPORTS = (
     "blink_abi_version", "blink_supported_sizes", "blink_ctx_create", "blink_ctx_destroy",
     "blink_last_error", "blink_cells", "blink_grid", "blink_image_batch", "blink_plan_create",
     "blink_plan_image", "blink_plan_destroy", "blink_plan_layer_info",
-    "blink_image_batch_noalloc",
+    "blink_image_batch_noalloc", "blink_image_batch_host",
 )
 
 
@@ -76,6 +76,8 @@ def lib(path: str = LIB_PATH):
     L.blink_plan_image.argtypes = [P, P, P, P, ctypes.c_uint32, P]
     L.blink_plan_destroy.restype = None
     L.blink_plan_destroy.argtypes = [P]
+    L.blink_image_batch_host.restype = I
+    L.blink_image_batch_host.argtypes = [P, P, I, LP, I, P, P, P, ctypes.c_uint32, P]
     L.blink_plan_layer_info.restype = I
     L.blink_plan_layer_info.argtypes = [P, I, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int64)]
@@ -201,6 +203,29 @@ class Context:
         self._raise(self._lib.blink_image_batch(self.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
                                                 len(layers), _ptr(vis), _ptr(images_out),
                                                 _ptr(wsum_out), int(flags), _stream(stream)))
+
+    def image_batch_host(self, ant_xyz, layers, vis, images_out, wsum_out=None, flags=0,
+                         stream=None):
+        """a1-a7 with host-resident inputs and outputs (numpy arrays or CPU
+        tensors; pinned memory gives full copy bandwidth)."""
+        import numpy as np
+
+        def hp(x):
+            if x is None:
+                return ctypes.c_void_p(0)
+            if isinstance(x, np.ndarray):
+                if not x.flags.c_contiguous:
+                    raise ValueError("host arrays must be contiguous")
+                return ctypes.c_void_p(x.ctypes.data)
+            if x.is_cuda or not x.is_contiguous():
+                raise ValueError("host tensors must be contiguous CPU tensors")
+            return ctypes.c_void_p(x.data_ptr())
+
+        arr = make_layers(layers)
+        xyz = np.ascontiguousarray(ant_xyz, dtype=np.float64)
+        self._raise(self._lib.blink_image_batch_host(
+            self.handle, ctypes.c_void_p(xyz.ctypes.data), xyz.shape[0], arr, len(layers), hp(vis),
+            hp(images_out), hp(wsum_out), int(flags), _stream(stream)))
 
     def plan(self, ant_xyz, layers, stream=None) -> "Plan":
         return Plan(self, ant_xyz, layers, stream)

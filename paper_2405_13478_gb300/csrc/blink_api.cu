@@ -24,6 +24,8 @@ using blink::Error;
 struct blink_ctx {
     int device = 0;
     cudaMemPool_t pool = nullptr;
+    cudaStream_t copy_in = nullptr;   // host-buffer pipeline: host -> device copies
+    cudaStream_t copy_out = nullptr;  // host-buffer pipeline: device -> host copies
     std::string err;
 };
 
@@ -376,6 +378,8 @@ void blink_ctx_destroy(blink_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
+        if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+        if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
@@ -485,6 +489,201 @@ int blink_grid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         }
     }
     free_plan_memory(&p, s);
+    if (!st) ctx->err.clear();
+    return st;
+}
+
+
+// ------------------------------------------------------------ host buffers
+}  // extern "C"
+
+namespace {
+
+// Resources of one blink_image_batch_host call (released by host_release).
+struct HostPipe {
+    double *d_xyz = nullptr;
+    float2 *d_vis[2] = {nullptr, nullptr};
+    float *d_out[2] = {nullptr, nullptr};
+    float *d_ws = nullptr;
+    DevLayer *d_cl = nullptr;
+    blink_plan plan;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+};
+
+struct HostChunk {
+    int l0, l1;
+    int64_t vis_base, vis_end, out_base, out_end;
+};
+
+struct HostGroup {
+    int chunk, n_px, first, count, r_alloc, sched_ok, max_chunk, max_seg;
+};
+
+#define HTRY(call)                                                                                   \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(ctx, BLINK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+int host_pipeline(blink_ctx *ctx, HostPipe &hp, const double *h_ant_xyz, int n_ant, const blink_layer *h_layers,
+                  int n_layers, const float *h_vis, float *h_images, float *h_wsum, uint32_t flags,
+                  cudaStream_t s) {
+    const int64_t nb = int64_t(n_ant) * (n_ant - 1) / 2;
+    // chunks of consecutive layers bounded by the staging sizes
+    const size_t cap_vis = size_t(512) << 20, cap_out = size_t(512) << 20;
+    std::vector<HostChunk> chunks;
+    for (int l = 0; l < n_layers;) {
+        HostChunk c{l, l, INT64_MAX, 0, INT64_MAX, 0};
+        while (c.l1 < n_layers && c.l1 - c.l0 < 65535) {
+            const blink_layer &L = h_layers[c.l1];
+            const int64_t vb = std::min(c.vis_base, L.vis_offset), ve = std::max(c.vis_end, L.vis_offset + nb);
+            const int64_t ob = std::min(c.out_base, L.out_offset);
+            const int64_t oe = std::max(c.out_end, L.out_offset + int64_t(L.n_px) * L.n_px);
+            if (c.l1 > c.l0 && (size_t(ve - vb) * 8 > cap_vis || size_t(oe - ob) * 4 > cap_out)) break;
+            c.vis_base = vb, c.vis_end = ve, c.out_base = ob, c.out_end = oe;
+            ++c.l1;
+        }
+        chunks.push_back(c);
+        l = c.l1;
+    }
+    size_t need_vis = 0, need_out = 0;
+    for (auto &c : chunks) {
+        need_vis = std::max(need_vis, size_t(c.vis_end - c.vis_base) * 8);
+        need_out = std::max(need_out, size_t(c.out_end - c.out_base) * 4);
+    }
+    const int nbuf = chunks.size() > 1 ? 2 : 1;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        return cudaMallocFromPoolAsync(ptr, std::max<size_t>(bytes, 256), ctx->pool, s) == cudaSuccess;
+    };
+    bool ok = alloc(reinterpret_cast<void **>(&hp.d_xyz), sizeof(double) * 3 * size_t(n_ant)) &&
+              alloc(reinterpret_cast<void **>(&hp.d_ws), sizeof(float) * size_t(n_layers));
+    for (int b = 0; b < nbuf && ok; ++b)
+        ok = alloc(reinterpret_cast<void **>(&hp.d_vis[b]), need_vis) &&
+             alloc(reinterpret_cast<void **>(&hp.d_out[b]), need_out);
+    if (!ok) return fail(ctx, BLINK_ERR_WORKSPACE, "staging allocation failed");
+    HTRY(cudaMemcpyAsync(hp.d_xyz, h_ant_xyz, sizeof(double) * 3 * size_t(n_ant), cudaMemcpyHostToDevice, s));
+    int st = build_plan(ctx, hp.d_xyz, n_ant, h_layers, n_layers, false, &hp.plan, s);
+    if (st) return st;
+    const blink_plan &p = hp.plan;
+    // per chunk: layers rebased onto the staging buffers, grouped by size
+    std::vector<DevLayer> cl;
+    std::vector<HostGroup> groups;
+    for (int ci = 0; ci < int(chunks.size()); ++ci) {
+        const HostChunk &c = chunks[size_t(ci)];
+        std::vector<int> idx;
+        for (int l = c.l0; l < c.l1; ++l) idx.push_back(l);
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return h_layers[x].n_px < h_layers[y].n_px; });
+        for (int l : idx) {
+            const int ch = p.layer_chan[size_t(l)];
+            const ChanInfo &inf = p.infos[size_t(ch)];
+            if (groups.empty() || groups.back().chunk != ci || groups.back().n_px != h_layers[l].n_px)
+                groups.push_back(HostGroup{ci, h_layers[l].n_px, int(cl.size()), 0, 1, 1, 0, 0});
+            HostGroup &gg = groups.back();
+            gg.count++;
+            gg.r_alloc = std::max(gg.r_alloc, inf.rows);
+            gg.sched_ok = gg.sched_ok && p.d_sched && inf.sched_off >= 0 && inf.sched == 1;
+            gg.max_chunk = std::max(gg.max_chunk, inf.chunk);
+            gg.max_seg = std::max(gg.max_seg, inf.max_seg);
+            cl.push_back(DevLayer{h_layers[l].vis_offset - c.vis_base, h_layers[l].out_offset - c.out_base, ch, l});
+        }
+    }
+    if (!alloc(reinterpret_cast<void **>(&hp.d_cl), sizeof(DevLayer) * cl.size()))
+        return fail(ctx, BLINK_ERR_WORKSPACE, "layer table allocation failed");
+    HTRY(cudaMemcpyAsync(hp.d_cl, cl.data(), sizeof(DevLayer) * cl.size(), cudaMemcpyHostToDevice, s));
+    for (int b = 0; b < 2; ++b) {
+        HTRY(cudaEventCreateWithFlags(&hp.ev_in[b], cudaEventDisableTiming));
+        HTRY(cudaEventCreateWithFlags(&hp.ev_comp[b], cudaEventDisableTiming));
+        HTRY(cudaEventCreateWithFlags(&hp.ev_out[b], cudaEventDisableTiming));
+    }
+    // staging, plan and layer table are ready on s before the copy streams start
+    HTRY(cudaEventRecord(hp.ev_comp[1], s));
+    HTRY(cudaStreamWaitEvent(ctx->copy_in, hp.ev_comp[1], 0));
+    HTRY(cudaStreamWaitEvent(ctx->copy_out, hp.ev_comp[1], 0));
+    size_t gi = 0;
+    for (int ci = 0; ci < int(chunks.size()); ++ci) {
+        const HostChunk &c = chunks[size_t(ci)];
+        const int b = ci % nbuf;
+        if (ci >= nbuf) HTRY(cudaStreamWaitEvent(ctx->copy_in, hp.ev_comp[b], 0));  // vis buffer free
+        HTRY(cudaMemcpyAsync(hp.d_vis[b], h_vis + 2 * c.vis_base, size_t(c.vis_end - c.vis_base) * 8,
+                             cudaMemcpyHostToDevice, ctx->copy_in));
+        HTRY(cudaEventRecord(hp.ev_in[b], ctx->copy_in));
+        HTRY(cudaStreamWaitEvent(s, hp.ev_in[b], 0));
+        if (ci >= nbuf) HTRY(cudaStreamWaitEvent(s, hp.ev_out[b], 0));  // image buffer drained
+        for (; gi < groups.size() && groups[gi].chunk == ci; ++gi) {
+            const HostGroup &gg = groups[gi];
+            blink_plan::Group grp{gg.n_px, 0, gg.count, gg.r_alloc, gg.sched_ok, gg.max_chunk, gg.max_seg};
+            blink::ImageArgs a =
+                group_args(&p, grp, reinterpret_cast<const float *>(hp.d_vis[b]), hp.d_out[b], hp.d_ws, flags);
+            a.layers = hp.d_cl + gg.first;
+            Error e = blink::launch_image_group(gg.n_px, a, s);
+            if (e.status) return fail(ctx, e);
+        }
+        HTRY(cudaEventRecord(hp.ev_comp[b], s));
+        HTRY(cudaStreamWaitEvent(ctx->copy_out, hp.ev_comp[b], 0));
+        HTRY(cudaMemcpyAsync(h_images + c.out_base, hp.d_out[b], size_t(c.out_end - c.out_base) * 4,
+                             cudaMemcpyDeviceToHost, ctx->copy_out));
+        HTRY(cudaEventRecord(hp.ev_out[b], ctx->copy_out));
+    }
+    if (h_wsum) HTRY(cudaMemcpyAsync(h_wsum, hp.d_ws, sizeof(float) * size_t(n_layers), cudaMemcpyDeviceToHost, s));
+    HTRY(cudaEventRecord(hp.ev_in[0], ctx->copy_out));
+    HTRY(cudaStreamWaitEvent(s, hp.ev_in[0], 0));
+    return BLINK_OK;
+}
+#undef HTRY
+
+// Frees everything on s after the pipeline (or whatever part of it ran).
+int host_release(blink_ctx *ctx, HostPipe &hp, cudaStream_t s, int st) {
+    // whatever was queued on the copy streams must finish before the frees
+    cudaEvent_t fin = nullptr;
+    if (cudaEventCreateWithFlags(&fin, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(fin, ctx->copy_in);
+        cudaStreamWaitEvent(s, fin, 0);
+        cudaEventRecord(fin, ctx->copy_out);
+        cudaStreamWaitEvent(s, fin, 0);
+    }
+    free_plan_memory(&hp.plan, s);
+    for (void *ptr : {static_cast<void *>(hp.d_xyz), static_cast<void *>(hp.d_ws), static_cast<void *>(hp.d_cl)})
+        if (ptr) cudaFreeAsync(ptr, s);
+    if (hp.d_vis[0]) cudaFreeAsync(hp.d_vis[0], s);
+    if (hp.d_out[0]) cudaFreeAsync(hp.d_out[0], s);
+    if (hp.d_vis[1]) cudaFreeAsync(hp.d_vis[1], s);
+    if (hp.d_out[1]) cudaFreeAsync(hp.d_out[1], s);
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (fin) cudaEventDestroy(fin);
+    for (int b = 0; b < 2; ++b) {
+        if (hp.ev_in[b]) cudaEventDestroy(hp.ev_in[b]);
+        if (hp.ev_comp[b]) cudaEventDestroy(hp.ev_comp[b]);
+        if (hp.ev_out[b]) cudaEventDestroy(hp.ev_out[b]);
+    }
+    if (!st && se != cudaSuccess) st = fail(ctx, BLINK_ERR_CUDA, std::string("pipeline: ") + cudaGetErrorString(se));
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Chunked pipeline: H2D of chunk i+1 and D2H of chunk i-1 overlap the image
+// kernels of chunk i (double-buffered device staging from the context pool).
+int blink_image_batch_host(blink_ctx *ctx, const double *h_ant_xyz, int n_ant, const blink_layer *h_layers,
+                           int n_layers, const float *h_vis, float *h_images, float *h_wsum, uint32_t flags,
+                           void *stream) {
+    if (!ctx) return BLINK_ERR_INVALID;
+    int st = validate(ctx, h_ant_xyz, n_ant, h_layers, n_layers);
+    if (st) return st;
+    if (n_layers == 0) return BLINK_OK;
+    if (!h_vis || !h_images) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    if (flags & ~uint32_t(BLINK_NORMALIZE)) return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!ctx->copy_in && cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ctx, BLINK_ERR_CUDA, "copy stream creation failed");
+    if (!ctx->copy_out && cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ctx, BLINK_ERR_CUDA, "copy stream creation failed");
+    HostPipe hp;
+    st = host_pipeline(ctx, hp, h_ant_xyz, n_ant, h_layers, n_layers, h_vis, h_images, h_wsum, flags, s);
+    st = host_release(ctx, hp, s, st);
     if (!st) ctx->err.clear();
     return st;
 }

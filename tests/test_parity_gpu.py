@@ -326,6 +326,30 @@ def test_plan_reuse_matches_batch(torch, ctx):
     plan.close()
 
 
+def test_host_buffer_path_matches_device_path(torch, ctx):
+    """blink_image_batch_host: host inputs and outputs, several pipeline
+    chunks (the 512 MB staging limit is crossed), mixed sizes in a chunk."""
+    from paper_2405_13478_gb300 import binding
+    ws = synth.config2(seed=15, n_times=70)          # 2240 layers, 585 MB of visibilities
+    vis = ws.vis("cpu")
+    layers = ws.layers()
+    layers[5] = dict(layers[5], n_px=256, delta_u=0.3, weighting=0)
+    layers, total = binding.layer_out_offsets(layers)
+    h_vis = vis.reshape(-1).pin_memory()
+    h_img = torch.empty(total, dtype=torch.float32).pin_memory()
+    h_ws = torch.empty(len(layers), dtype=torch.float32)
+    ctx.image_batch_host(ws.ant_xyz, layers, h_vis, h_img, h_ws)
+    d_img = torch.empty(total, dtype=torch.float32, device="cuda")
+    d_ws = torch.empty(len(layers), dtype=torch.float32, device="cuda")
+    ctx.image_batch(to_dev(torch, ws.ant_xyz), layers, vis.reshape(-1).cuda(), d_img, d_ws)
+    torch.cuda.synchronize()
+    h, d = h_img.numpy(), d_img.cpu().numpy()
+    for L in layers:
+        o, n = L["out_offset"], L["n_px"] ** 2
+        assert np.abs(h[o:o + n] - d[o:o + n]).max() <= 1e-6 * np.abs(d[o:o + n]).max()
+    assert torch.equal(h_ws, d_ws.cpu())
+
+
 # ------------------------------------------------- full bench configuration
 def test_config2_full_batch_sampled_layers(torch, ctx):
     """The bench workload (32000 layers of 180^2, uniform) in one call;
