@@ -79,6 +79,14 @@ def _load():
         lib.orc_image_fft.argtypes = [D, ctypes.c_int, D, D]
         lib.orc_fft1d.restype = ctypes.c_int
         lib.orc_fft1d.argtypes = [D, ctypes.c_int, ctypes.c_int, D]
+        lib.orc_grid_c128.restype = ctypes.c_int
+        lib.orc_grid_c128.argtypes = [I32, I32, D, ctypes.c_int64, ctypes.c_int, ctypes.c_int, D,
+                                      I32, D]
+        for fn in ("orc_degrid_direct", "orc_degrid_fft"):
+            getattr(lib, fn).restype = ctypes.c_int
+            getattr(lib, fn).argtypes = [I32, I32, ctypes.c_int64, ctypes.c_int, ctypes.c_int, D, D]
+        lib.orc_gain_grad.restype = None
+        lib.orc_gain_grad.argtypes = [ctypes.c_int, D, D, D, D]
         lib.orc_image_batch.restype = ctypes.c_int
         lib.orc_image_batch.argtypes = [D, ctypes.c_int, ctypes.c_int, I32, I32, D, D, I64, I64,
                                         F, D, D, ctypes.c_int, ctypes.c_int]
@@ -205,3 +213,48 @@ def image(ant_xyz, freq_hz, delta_u, n_px, weighting, vis, mode: str = "fft"):
     g, _, ws = grid(ku, kv, vis, n_px, weighting)
     img, mi = image_direct(g) if mode == "direct" else image_fft(g)
     return img, ws, mi
+
+
+def grid_c128(ku, kv, vis, n_px: int, weighting: int):
+    """grid() with complex128 visibilities (finite-difference pins)."""
+    ku = np.ascontiguousarray(ku, np.int32)
+    kv = np.ascontiguousarray(kv, np.int32)
+    vis = np.ascontiguousarray(vis, np.complex128)
+    g = np.empty((n_px, n_px), np.complex128)
+    cnt = np.empty((n_px, n_px), np.int32)
+    ws = np.zeros(1, np.float64)
+    st = _load().orc_grid_c128(_p(ku, ctypes.c_int32), _p(kv, ctypes.c_int32),
+                               _p(vis.view(np.float64), ctypes.c_double), ku.size, int(n_px),
+                               int(weighting), _p(g.view(np.float64), ctypes.c_double),
+                               _p(cnt, ctypes.c_int32), _p(ws, ctypes.c_double))
+    if st != 0:
+        raise ValueError("orc_grid_c128 rejected its arguments")
+    return g, cnt, float(ws[0])
+
+
+def degrid(ku, kv, resid, weighting: int, mode: str = "fft"):
+    """Adjoint: gradient w.r.t. the visibilities of a loss whose image
+    gradient is ``resid``: gamma_b = 2 w_b H[k_b] (dL/dRe + i dL/dIm)."""
+    ku = np.ascontiguousarray(ku, np.int32)
+    kv = np.ascontiguousarray(kv, np.int32)
+    r = np.ascontiguousarray(resid, np.float64)
+    gam = np.empty(ku.size, np.complex128)
+    fn = _load().orc_degrid_direct if mode == "direct" else _load().orc_degrid_fft
+    if fn(_p(ku, ctypes.c_int32), _p(kv, ctypes.c_int32), ku.size, r.shape[0], int(weighting),
+          _p(r, ctypes.c_double), _p(gam.view(np.float64), ctypes.c_double)) != 0:
+        raise ValueError("orc_degrid rejected its arguments")
+    return gam
+
+
+def gain_grad(n_ant: int, gamma_v, gains, model, out=None):
+    """Chain rule from visibility gradients to per-antenna gain gradients
+    (V_ij = g_i conj(g_j) M_ij); accumulates into ``out``."""
+    gv = np.ascontiguousarray(gamma_v, np.complex128)
+    g = np.ascontiguousarray(gains, np.complex128)
+    m = np.ascontiguousarray(model, np.complex128)
+    out = np.zeros(n_ant, np.complex128) if out is None else out
+    _load().orc_gain_grad(int(n_ant), _p(gv.view(np.float64), ctypes.c_double),
+                          _p(g.view(np.float64), ctypes.c_double),
+                          _p(m.view(np.float64), ctypes.c_double),
+                          _p(out.view(np.float64), ctypes.c_double))
+    return out

@@ -118,8 +118,24 @@ int64_t orc_cells(const double *u, const double *v, int64_t nb, double delta_u, 
  * count: [N][N] number of entries per cell (may be NULL).
  * weighting: 0 natural, 1 uniform.  *wsum = summed weight of all entries.
  * Returns 0, or -1 on a bad argument. */
+static int orc_grid_any(const int32_t *ku, const int32_t *kv, const float *vis32, const double *vis64,
+                        int64_t nb, int n_px, int weighting, double *grid, int32_t *count,
+                        double *wsum);
+
 int orc_grid(const int32_t *ku, const int32_t *kv, const float *vis, int64_t nb, int n_px,
              int weighting, double *grid, int32_t *count, double *wsum) {
+    return orc_grid_any(ku, kv, vis, NULL, nb, n_px, weighting, grid, count, wsum);
+}
+
+/* Same with complex128 visibilities (used by the finite-difference pins). */
+int orc_grid_c128(const int32_t *ku, const int32_t *kv, const double *vis, int64_t nb, int n_px,
+                  int weighting, double *grid, int32_t *count, double *wsum) {
+    return orc_grid_any(ku, kv, NULL, vis, nb, n_px, weighting, grid, count, wsum);
+}
+
+static int orc_grid_any(const int32_t *ku, const int32_t *kv, const float *vis32, const double *vis64,
+                        int64_t nb, int n_px, int weighting, double *grid, int32_t *count,
+                        double *wsum) {
     if (n_px < 4 || (n_px & 1) || (weighting != 0 && weighting != 1)) return -1;
     const int64_t npix = (int64_t)n_px * n_px;
     int32_t *cnt = count ? count : (int32_t *)malloc(sizeof(int32_t) * (size_t)npix);
@@ -130,7 +146,8 @@ int orc_grid(const int32_t *ku, const int32_t *kv, const float *vis, int64_t nb,
     int64_t entries = 0;
     for (int64_t b = 0; b < nb; ++b) {
         if (ku[b] == ORC_DROPPED) continue;
-        const double re = (double)vis[2 * b], im = (double)vis[2 * b + 1];
+        const double re = vis32 ? (double)vis32[2 * b] : vis64[2 * b];
+        const double im = vis32 ? (double)vis32[2 * b + 1] : vis64[2 * b + 1];
         /* V_ij at (u, v) */
         const int64_t p = (int64_t)(kv[b] + h) * n_px + (ku[b] + h);
         grid[2 * p] += re;
@@ -325,6 +342,135 @@ int orc_image_fft(const double *grid, int n_px, double *image, double *max_abs_i
     if (max_abs_imag) *max_abs_imag = worst;
     free(a); free(col); free(tw); free(tmp);
     return 0;
+}
+
+/* ------------------------------------------------- adjoint (degridding) */
+/* Gradient of a real loss L(image) with respect to the visibilities.  The
+ * image is linear in V: I[p] = sum_b w_b 2 Re(V_b E(k_b, p)) with
+ * E(k, p) = exp(+2 pi i k.(p - N/2) / N) (Sec. 4.3 Eq. 6 with the gridding of
+ * Sec. 5.2.1; w_b = 1 natural, 1/n(cell) uniform).  With R = dL/dI, the
+ * gradient in the convention dL/dRe V + i dL/dIm V is
+ *     gamma_b = 2 w_b H[k_b],  H[k] = sum_p R[p] exp(-2 pi i k.(p - N/2) / N),
+ * and zero for baselines that are not gridded.  This reading of the
+ * "differentiation" extension is listed in the design doc. */
+static int orc_entry_weights(const int32_t *ku, const int32_t *kv, int64_t nb, int n_px,
+                             int weighting, double *w) {
+    const int h = n_px / 2;
+    int32_t *cnt = (int32_t *)calloc((size_t)n_px * n_px, sizeof(int32_t));
+    if (!cnt) return -1;
+    for (int64_t b = 0; b < nb; ++b) {
+        if (ku[b] == ORC_DROPPED) continue;
+        cnt[(int64_t)(kv[b] + h) * n_px + (ku[b] + h)] += 1;
+        cnt[(int64_t)(-kv[b] + h) * n_px + (-ku[b] + h)] += 1;
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+        if (ku[b] == ORC_DROPPED) {
+            w[b] = 0.0;
+        } else if (weighting == 1) {
+            w[b] = 1.0 / (double)cnt[(int64_t)(kv[b] + h) * n_px + (ku[b] + h)];
+        } else {
+            w[b] = 1.0;
+        }
+    }
+    free(cnt);
+    return 0;
+}
+
+/* Direct sum over pixels (small images).  resid: [N][N]; gamma: [B] complex. */
+int orc_degrid_direct(const int32_t *ku, const int32_t *kv, int64_t nb, int n_px, int weighting,
+                      const double *resid, double *gamma) {
+    if (n_px < 4 || (n_px & 1)) return -1;
+    const int n = n_px, h = n_px / 2;
+    double *w = (double *)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+    double *tw = orc_twiddles(n);
+    if (!w || !tw || orc_entry_weights(ku, kv, nb, n, weighting, w)) { free(w); free(tw); return -1; }
+    for (int64_t b = 0; b < nb; ++b) {
+        double re = 0.0, im = 0.0;
+        if (ku[b] != ORC_DROPPED) {
+            for (int py = 0; py < n; ++py)
+                for (int px = 0; px < n; ++px) {
+                    int64_t e = (int64_t)ku[b] * (px - h) + (int64_t)kv[b] * (py - h);
+                    e %= n;
+                    if (e < 0) e += n;
+                    const double r = resid[(int64_t)py * n + px];
+                    re += r * tw[2 * e];
+                    im -= r * tw[2 * e + 1]; /* exp(-i theta) */
+                }
+        }
+        gamma[2 * b] = 2.0 * w[b] * re;
+        gamma[2 * b + 1] = 2.0 * w[b] * im;
+    }
+    free(w); free(tw);
+    return 0;
+}
+
+/* Same through an FP64 forward 2-D FFT of the ifftshifted residual. */
+int orc_degrid_fft(const int32_t *ku, const int32_t *kv, int64_t nb, int n_px, int weighting,
+                   const double *resid, double *gamma) {
+    if (n_px < 4 || (n_px & 1)) return -1;
+    const int n = n_px, h = n_px / 2;
+    const size_t npix = (size_t)n * n;
+    double *a = (double *)malloc(sizeof(double) * 2 * npix);
+    double *col = (double *)malloc(sizeof(double) * 4 * (size_t)n);
+    double *tw = orc_twiddles(n);
+    double *tmp = (double *)malloc(sizeof(double) * 4 * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+    if (!a || !col || !tw || !tmp || !w || orc_entry_weights(ku, kv, nb, n, weighting, w)) {
+        free(a); free(col); free(tw); free(tmp); free(w);
+        return -1;
+    }
+    /* a[n_y][n_x] = R[(n_y + h) mod n][(n_x + h) mod n]: pixel offset p - N/2 in FFT order */
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x) {
+            a[2 * ((size_t)y * n + x)] = resid[(size_t)((y + h) % n) * n + (size_t)((x + h) % n)];
+            a[2 * ((size_t)y * n + x) + 1] = 0.0;
+        }
+    for (int y = 0; y < n; ++y) {
+        orc_fft_rec(a + 2 * (size_t)y * n, 1, n, col, -1, tw, n, tmp);
+        memcpy(a + 2 * (size_t)y * n, col, sizeof(double) * 2 * (size_t)n);
+    }
+    for (int x = 0; x < n; ++x) {
+        orc_fft_rec(a + 2 * (size_t)x, n, n, col, -1, tw, n, tmp);
+        for (int y = 0; y < n; ++y) {
+            a[2 * ((size_t)y * n + x)] = col[2 * y];
+            a[2 * ((size_t)y * n + x) + 1] = col[2 * y + 1];
+        }
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+        if (ku[b] == ORC_DROPPED) {
+            gamma[2 * b] = gamma[2 * b + 1] = 0.0;
+            continue;
+        }
+        const size_t y = (size_t)((kv[b] % n + n) % n), x = (size_t)((ku[b] % n + n) % n);
+        gamma[2 * b] = 2.0 * w[b] * a[2 * (y * n + x)];
+        gamma[2 * b + 1] = 2.0 * w[b] * a[2 * (y * n + x) + 1];
+    }
+    free(a); free(col); free(tw); free(tmp); free(w);
+    return 0;
+}
+
+/* Chain rule to per-antenna gains for V_ij = g_i conj(g_j) M_ij (i < j):
+ * gamma(g_i) += sum_{j>i} gamma(V_ij) g_j conj(M_ij)
+ *             + sum_{k<i} conj(gamma(V_ki)) g_k M_ki          (accumulates). */
+void orc_gain_grad(int n_ant, const double *gamma_v, const double *gains, const double *model,
+                   double *gamma_g) {
+    int64_t b = 0;
+    for (int i = 0; i < n_ant; ++i) {
+        for (int j = i + 1; j < n_ant; ++j, ++b) {
+            const double gr = gamma_v[2 * b], gi = gamma_v[2 * b + 1];
+            const double mr = model[2 * b], mi = model[2 * b + 1];
+            /* term for g_i: gamma * g_j * conj(M) */
+            const double tr = gains[2 * j] * mr + gains[2 * j + 1] * mi;  /* g_j conj(M) */
+            const double ti = gains[2 * j + 1] * mr - gains[2 * j] * mi;
+            gamma_g[2 * i] += gr * tr - gi * ti;
+            gamma_g[2 * i + 1] += gr * ti + gi * tr;
+            /* term for g_j: conj(gamma) * g_i * M */
+            const double ur = gains[2 * i] * mr - gains[2 * i + 1] * mi;  /* g_i M */
+            const double ui = gains[2 * i] * mi + gains[2 * i + 1] * mr;
+            gamma_g[2 * j] += gr * ur + gi * ui;
+            gamma_g[2 * j + 1] += gr * ui - gi * ur;
+        }
+    }
 }
 
 /* --------------------------------------------------- whole path, batched */

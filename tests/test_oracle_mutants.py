@@ -13,6 +13,7 @@ import tempfile
 import pytest
 
 import oracle
+from tests import test_oracle_adjoint as adj
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "blink_oracle.c")
@@ -47,6 +48,18 @@ MUTANTS = {
     "uniform_half_count": ("        cnt[q] += 1;\n", ""),
     # summed weight of natural weighting counting baselines, not entries
     "natural_wsum": ("entries += 2;", "entries += 1;"),
+    # adjoint with the inverse instead of the forward kernel (direct route)
+    "degrid_wrong_sign": ("im -= r * tw[2 * e + 1]; /* exp(-i theta) */",
+                          "im += r * tw[2 * e + 1];"),
+    # adjoint missing the factor 2 of V and conj(V) (FFT route)
+    "degrid_no_factor_two": ("gamma[2 * b] = 2.0 * w[b] * a[2 * (y * n + x)];",
+                             "gamma[2 * b] = w[b] * a[2 * (y * n + x)];"),
+    # adjoint ignoring the uniform weights
+    "degrid_no_uniform_weight": ("w[b] = 1.0 / (double)cnt[(int64_t)(kv[b] + h) * n_px + (ku[b] + h)];",
+                                 "w[b] = 1.0;"),
+    # gain chain rule without the conjugate on the second antenna's term
+    "gain_grad_conjugate": ("gamma_g[2 * j + 1] += gr * ui - gi * ur;",
+                            "gamma_g[2 * j + 1] += gr * ui + gi * ur;"),
 }
 
 PINS = [
@@ -61,6 +74,10 @@ PINS = [
     pins.test_single_cell_shift_theorem,
     lambda: pins.test_image_fft_matches_numpy_shifted_ifft2(16),
     lambda: pins.test_grid_counts_match_bruteforce_histogram(5),
+    lambda: adj.test_adjoint_dot_product_identity(1, "direct"),
+    lambda: adj.test_adjoint_dot_product_identity(0, "fft"),
+    lambda: adj.test_visibility_gradient_matches_finite_differences(1),
+    adj.test_gain_gradient_matches_finite_differences,
 ]
 
 
@@ -85,7 +102,8 @@ def test_pins_catch_mutant(name, workdir, monkeypatch):
     real = oracle._load()
     mlib = ctypes.CDLL(so_path)
     for fn in ("orc_version", "orc_n_baselines", "orc_uv", "orc_cells", "orc_grid",
-               "orc_image_direct", "orc_image_fft", "orc_fft1d", "orc_image_batch"):
+               "orc_image_direct", "orc_image_fft", "orc_fft1d", "orc_image_batch",
+               "orc_grid_c128", "orc_degrid_direct", "orc_degrid_fft", "orc_gain_grad"):
         getattr(mlib, fn).restype = getattr(real, fn).restype
         getattr(mlib, fn).argtypes = getattr(real, fn).argtypes
     monkeypatch.setattr(oracle, "_lib", mlib)
