@@ -131,6 +131,36 @@ BLINK_API int blink_image_batch(blink_ctx *ctx, const double *d_ant_xyz, int n_a
                       const blink_layer *h_layers, int n_layers, const float *d_vis,
                       float *d_images, float *d_wsum, uint32_t flags, void *stream);
 
+/* --------------------------------------------------------------- adjoint */
+/* The paper images only; these calls differentiate its image path.  The
+ * dirty image is linear in the visibilities (Sec. 4.3 Eq. 6 with the gridding
+ * of Sec. 5.2.1): I[p] = sum_b w_b 2 Re(V_b exp(+2 pi i k_b.(p - N/2) / N)).
+ * Given d_dimage = dL/dI of a real loss L (float32 [N][N] at out_offset, same
+ * layout and flags as the forward images), blink_degrid writes
+ *     d_dvis[b] = dL/dRe V_b + i dL/dIm V_b = 2 w_b H[k_b]
+ * (complex64 at vis_offset), H the forward 2-D DFT of dL/dI
+ * (exp(-2 pi i k.(p - N/2) / N)); zero for baselines that are not gridded.
+ * It recomputes from the layer description (no state of the forward pass is
+ * kept).  With BLINK_NORMALIZE the forward scaling by 1/sum(w) is included. */
+BLINK_API int blink_degrid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
+                           int n_layers, const float *d_dimage, float *d_dvis, uint32_t flags, void *stream);
+BLINK_API int blink_plan_degrid(blink_plan *plan, const float *d_dimage, float *d_dvis, uint32_t flags,
+                                void *stream);
+
+/* Per-antenna complex gains g (complex64 [n_ant]) on model visibilities
+ * (antenna-level calibration, Sec. 4.2): d_vis[b] = g_i conj(g_j) d_model[b]
+ * for baseline b = (i < j) of every layer (vis_offset addressing; other layer
+ * fields ignored). */
+BLINK_API int blink_apply_gains(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int n_layers,
+                                const float *d_model, const float *d_gains, float *d_vis, void *stream);
+/* Chain rule of blink_degrid's output to the gains, summed over all layers:
+ * d_dgains[i] = sum_l [ sum_{j>i} d_dvis(ij) g_j conj(M_ij)
+ *                     + sum_{k<i} conj(d_dvis(ki)) g_k M_ki ]
+ * (dL/dRe g + i dL/dIm g), accumulated in FP64, overwrites d_dgains. */
+BLINK_API int blink_gain_grad(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int n_layers,
+                              const float *d_dvis, const float *d_model, const float *d_gains, float *d_dgains,
+                              void *stream);
+
 /* -------------------------------------------------- host-resident buffers */
 /* blink_image_batch for data in host memory: h_ant_xyz, h_vis and h_images
  * (and h_wsum, may be NULL) are host pointers addressed like their d_

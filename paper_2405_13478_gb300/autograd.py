@@ -1,0 +1,69 @@
+"""torch.autograd wrappers of the imaging path and its adjoint.
+
+``dirty_images(vis, plan)`` images complex64 visibilities with the plan's
+kernels; its backward runs the library's adjoint kernels (forward FFT of the
+image gradient + degridding, ``blink_plan_degrid``), recomputing from the
+plan instead of storing grids.  ``apply_gains(gains, model, ...)`` forms
+V_ij = g_i conj(g_j) M_ij with ``blink_apply_gains``; its backward is
+``blink_gain_grad``.  Gradients follow torch's complex convention
+dL/dRe + i dL/dIm.  No computation happens in torch: it only allocates the
+tensors and carries the graph.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding
+
+
+class _DirtyImages(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, vis, plan, n_out, flags):
+        if vis.dtype != torch.complex64 or not vis.is_cuda:
+            raise ValueError("vis must be a complex64 CUDA tensor")
+        vis = vis.contiguous()
+        out = torch.empty(n_out, dtype=torch.float32, device=vis.device)
+        plan.image(vis, out, None, flags)
+        ctx.plan = plan
+        ctx.flags = flags
+        ctx.vis_shape = vis.shape
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        grad_out = grad_out.contiguous()
+        dvis = torch.zeros(ctx.vis_shape, dtype=torch.complex64, device=grad_out.device)
+        ctx.plan.degrid(grad_out, dvis, ctx.flags)
+        return dvis, None, None, None
+
+
+def dirty_images(vis: torch.Tensor, plan: "binding.Plan", n_out: int, flags: int = 0):
+    """Float32 images (packed at the plan's out_offsets, ``n_out`` floats)."""
+    return _DirtyImages.apply(vis, plan, n_out, flags)
+
+
+class _ApplyGains(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, gains, model, lib_ctx, n_ant, layers):
+        if gains.dtype != torch.complex64 or model.dtype != torch.complex64:
+            raise ValueError("gains and model must be complex64")
+        gains = gains.contiguous()
+        model = model.contiguous()
+        vis = torch.empty_like(model)
+        lib_ctx.apply_gains(n_ant, layers, model, gains, vis)
+        ctx.save_for_backward(gains, model)
+        ctx.lib_ctx, ctx.n_ant, ctx.layers = lib_ctx, n_ant, layers
+        return vis
+
+    @staticmethod
+    def backward(ctx, grad_vis):
+        gains, model = ctx.saved_tensors
+        dg = torch.empty_like(gains)
+        ctx.lib_ctx.gain_grad(ctx.n_ant, ctx.layers, grad_vis.contiguous(), model, gains, dg)
+        return dg, None, None, None, None
+
+
+def apply_gains(gains: torch.Tensor, model: torch.Tensor, lib_ctx: "binding.Context", n_ant: int,
+                layers):
+    """V_ij = g_i conj(g_j) M_ij for every layer (vis_offset addressing)."""
+    return _ApplyGains.apply(gains, model, lib_ctx, n_ant, layers)

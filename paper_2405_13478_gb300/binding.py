@@ -24,7 +24,8 @@ EXPORTS = (
     "blink_abi_version", "blink_supported_sizes", "blink_ctx_create", "blink_ctx_destroy",
     "blink_last_error", "blink_cells", "blink_grid", "blink_image_batch", "blink_plan_create",
     "blink_plan_image", "blink_plan_destroy", "blink_plan_layer_info",
-    "blink_image_batch_noalloc", "blink_image_batch_host",
+    "blink_image_batch_noalloc", "blink_image_batch_host", "blink_degrid", "blink_plan_degrid",
+    "blink_apply_gains", "blink_gain_grad",
 )
 
 
@@ -78,6 +79,14 @@ def lib(path: str = LIB_PATH):
     L.blink_plan_destroy.argtypes = [P]
     L.blink_image_batch_host.restype = I
     L.blink_image_batch_host.argtypes = [P, P, I, LP, I, P, P, P, ctypes.c_uint32, P]
+    L.blink_degrid.restype = I
+    L.blink_degrid.argtypes = [P, P, I, LP, I, P, P, ctypes.c_uint32, P]
+    L.blink_plan_degrid.restype = I
+    L.blink_plan_degrid.argtypes = [P, P, P, ctypes.c_uint32, P]
+    L.blink_apply_gains.restype = I
+    L.blink_apply_gains.argtypes = [P, I, LP, I, P, P, P, P]
+    L.blink_gain_grad.restype = I
+    L.blink_gain_grad.argtypes = [P, I, LP, I, P, P, P, P, P]
     L.blink_plan_layer_info.restype = I
     L.blink_plan_layer_info.argtypes = [P, I, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int64)]
@@ -227,6 +236,30 @@ class Context:
             self.handle, ctypes.c_void_p(xyz.ctypes.data), xyz.shape[0], arr, len(layers), hp(vis),
             hp(images_out), hp(wsum_out), int(flags), _stream(stream)))
 
+    def degrid(self, ant_xyz, layers, dimage, dvis_out, flags=0, stream=None):
+        """Adjoint: dL/dV (complex64 at vis_offset) from dL/dimage."""
+        _check_dev(ant_xyz, dimage, dvis_out)
+        arr = make_layers(layers)
+        self._raise(self._lib.blink_degrid(self.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
+                                           len(layers), _ptr(dimage), _ptr(dvis_out), int(flags),
+                                           _stream(stream)))
+
+    def apply_gains(self, n_ant, layers, model, gains, vis_out, stream=None):
+        """vis = g_i conj(g_j) model for every baseline of every layer."""
+        _check_dev(model, gains, vis_out)
+        arr = make_layers(layers)
+        self._raise(self._lib.blink_apply_gains(self.handle, int(n_ant), arr, len(layers),
+                                                _ptr(model), _ptr(gains), _ptr(vis_out),
+                                                _stream(stream)))
+
+    def gain_grad(self, n_ant, layers, dvis, model, gains, dgains_out, stream=None):
+        """Per-antenna gain gradient from visibility gradients (summed over layers)."""
+        _check_dev(dvis, model, gains, dgains_out)
+        arr = make_layers(layers)
+        self._raise(self._lib.blink_gain_grad(self.handle, int(n_ant), arr, len(layers),
+                                              _ptr(dvis), _ptr(model), _ptr(gains),
+                                              _ptr(dgains_out), _stream(stream)))
+
     def plan(self, ant_xyz, layers, stream=None) -> "Plan":
         return Plan(self, ant_xyz, layers, stream)
 
@@ -249,6 +282,11 @@ class Plan:
         self.ctx._raise(self.ctx._lib.blink_plan_image(self.handle, _ptr(vis), _ptr(images_out),
                                                        _ptr(wsum_out), int(flags),
                                                        _stream(stream)))
+
+    def degrid(self, dimage, dvis_out, flags=0, stream=None):
+        _check_dev(dimage, dvis_out)
+        self.ctx._raise(self.ctx._lib.blink_plan_degrid(self.handle, _ptr(dimage), _ptr(dvis_out),
+                                                        int(flags), _stream(stream)))
 
     def layer_info(self, layer: int):
         w = ctypes.c_float()

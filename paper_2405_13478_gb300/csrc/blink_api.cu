@@ -60,6 +60,8 @@ struct blink_plan {
     float2 *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     unsigned char *d_sched = nullptr;
+    float2 *d_dscratch = nullptr;  // adjoint column-transform scratch (allocated on first use)
+    size_t dscratch_bytes = 0;
     cudaStream_t last_stream = nullptr;
 };
 
@@ -148,9 +150,11 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     if (p->d_block) cudaFreeAsync(p->d_block, st);
     if (p->d_scratch) cudaFreeAsync(p->d_scratch, st);
     if (p->d_sched) cudaFreeAsync(p->d_sched, st);
+    if (p->d_dscratch) cudaFreeAsync(p->d_dscratch, st);
     p->d_block = nullptr;
     p->d_scratch = nullptr;
     p->d_sched = nullptr;
+    p->d_dscratch = nullptr;
 }
 
 // Images up to this size are gridded by the fused kernels, which can use the
@@ -430,6 +434,114 @@ void blink_plan_destroy(blink_plan *p) {
         free_plan_memory(p, p->last_stream);
     }
     delete p;
+}
+
+int blink_plan_degrid(blink_plan *p, const float *d_dimage, float *d_dvis, uint32_t flags, void *stream) {
+    if (!p) return BLINK_ERR_INVALID;
+    blink_ctx *ctx = p->ctx;
+    if (p->n_layers && (!d_dimage || !d_dvis)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    if (flags & ~uint32_t(BLINK_NORMALIZE)) return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!p->d_dscratch && p->n_layers) {
+        size_t need = 0;
+        for (const auto &grp : p->groups) {
+            const size_t per = blink::degrid_scratch_per_layer(grp.n_px, grp.r_alloc);
+            need = std::max(need, std::max(per, std::min(per * size_t(grp.count), kScratchCap)));
+        }
+        void *ptr = nullptr;
+        const cudaError_t e = cudaMallocFromPoolAsync(&ptr, need, ctx->pool, st);
+        if (e != cudaSuccess)
+            return fail(ctx, BLINK_ERR_WORKSPACE, std::string("adjoint scratch: ") + cudaGetErrorString(e));
+        p->d_dscratch = static_cast<float2 *>(ptr);
+        p->dscratch_bytes = need;
+    }
+    p->last_stream = st;
+    for (const auto &grp : p->groups) {
+        blink::ImageArgs a = group_args(p, grp, nullptr, nullptr, nullptr, flags);
+        a.scratch = p->d_dscratch;
+        a.scratch_bytes = p->dscratch_bytes;
+        Error e = blink::launch_degrid_group(grp.n_px, a, d_dimage, reinterpret_cast<float2 *>(d_dvis), st);
+        if (e.status) return fail(ctx, e);
+    }
+    return BLINK_OK;
+}
+
+int blink_degrid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers, int n_layers,
+                 const float *d_dimage, float *d_dvis, uint32_t flags, void *stream) {
+    blink_plan *p = nullptr;
+    int st = blink_plan_create(ctx, d_ant_xyz, n_ant, h_layers, n_layers, &p, stream);
+    if (st) return st;
+    st = blink_plan_degrid(p, d_dimage, d_dvis, flags, stream);
+    blink_plan_destroy(p);
+    return st;
+}
+
+// Per-layer visibility offsets of h_layers in a stream-ordered device array.
+static int upload_offsets(blink_ctx *ctx, const blink_layer *h_layers, int n_layers, cudaStream_t st, int64_t **out) {
+    std::vector<int64_t> off(static_cast<size_t>(n_layers));
+    for (int l = 0; l < n_layers; ++l) off[size_t(l)] = h_layers[l].vis_offset;
+    void *ptr = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&ptr, sizeof(int64_t) * off.size(), ctx->pool, st);
+    if (e != cudaSuccess) return fail(ctx, BLINK_ERR_WORKSPACE, "offset table allocation failed");
+    e = cudaMemcpyAsync(ptr, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(ptr, st);
+        return fail(ctx, BLINK_ERR_CUDA, std::string("offset upload: ") + cudaGetErrorString(e));
+    }
+    *out = static_cast<int64_t *>(ptr);
+    return BLINK_OK;
+}
+
+static int check_gain_args(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int n_layers) {
+    if (!ctx) return BLINK_ERR_INVALID;
+    if (n_ant < 2) return fail(ctx, BLINK_ERR_INVALID, "n_ant must be >= 2");
+    if (n_layers < 0 || (n_layers && !h_layers)) return fail(ctx, BLINK_ERR_INVALID, "bad layer array");
+    for (int l = 0; l < n_layers; ++l)
+        if (h_layers[l].vis_offset < 0) return fail(ctx, BLINK_ERR_INVALID, "offsets must be >= 0");
+    return BLINK_OK;
+}
+
+int blink_apply_gains(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int n_layers, const float *d_model,
+                      const float *d_gains, float *d_vis, void *stream) {
+    int st = check_gain_args(ctx, n_ant, h_layers, n_layers);
+    if (st || n_layers == 0) return st;
+    if (!d_model || !d_gains || !d_vis) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t *d_off = nullptr;
+    st = upload_offsets(ctx, h_layers, n_layers, s, &d_off);
+    if (st) return st;
+    Error e = blink::launch_apply_gains(reinterpret_cast<const float2 *>(d_model), reinterpret_cast<const float2 *>(d_gains),
+                                        d_off, n_layers, n_ant, int64_t(n_ant) * (n_ant - 1) / 2,
+                                        reinterpret_cast<float2 *>(d_vis), s);
+    cudaFreeAsync(d_off, s);
+    if (e.status) return fail(ctx, e);
+    ctx->err.clear();
+    return BLINK_OK;
+}
+
+int blink_gain_grad(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int n_layers, const float *d_dvis,
+                    const float *d_model, const float *d_gains, float *d_dgains, void *stream) {
+    int st = check_gain_args(ctx, n_ant, h_layers, n_layers);
+    if (st) return st;
+    if (!d_dvis || !d_model || !d_gains || !d_dgains) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_layers == 0) {
+        const cudaError_t e = cudaMemsetAsync(d_dgains, 0, sizeof(float2) * size_t(n_ant), s);
+        return e == cudaSuccess ? BLINK_OK : fail(ctx, BLINK_ERR_CUDA, "memset failed");
+    }
+    int64_t *d_off = nullptr;
+    st = upload_offsets(ctx, h_layers, n_layers, s, &d_off);
+    if (st) return st;
+    Error e = blink::launch_gain_grad(reinterpret_cast<const float2 *>(d_dvis), reinterpret_cast<const float2 *>(d_model),
+                                      reinterpret_cast<const float2 *>(d_gains), d_off, n_layers, n_ant,
+                                      reinterpret_cast<float2 *>(d_dgains), s);
+    cudaFreeAsync(d_off, s);
+    if (e.status) return fail(ctx, e);
+    ctx->err.clear();
+    return BLINK_OK;
 }
 
 int blink_plan_layer_info(const blink_plan *p, int layer, float *wsum, int64_t *n_kept) {

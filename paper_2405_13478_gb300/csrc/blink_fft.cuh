@@ -83,9 +83,16 @@ struct RootTable {
     }
 };
 
-// Table for runtime exponents (the four-step twiddles W_N^(n2 k1)).
+// Table for runtime exponents (the four-step twiddles W_N^(n2 k1)); the
+// forward direction uses the conjugates (root_rt).
 template <int N, int S>
 __constant__ RootTable<N, S> c_roots = RootTable<N, S>();
+
+template <int N, int S>
+__device__ __forceinline__ c32 root_rt(int e) {
+    const c32 w = c_roots<N, +1>.v[e];
+    return S > 0 ? w : c32{w.x, -w.y};
+}
 
 // ----------------------------------------------------------- complex helpers
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

@@ -70,7 +70,7 @@ __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begi
 
 // Pass 1 on rows [0, nrows) of G (row stride S): N-point inverse DFT of each
 // row in place.  Output frequency p ends at position N2 * (p % N1) + p / N1.
-template <int N>
+template <int N, int SIGN = +1>
 __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     // step A: N1-point transforms along stride N2, then twiddle W_N^(n2 k1)
@@ -80,9 +80,9 @@ __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, i
         float2 x[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) x[n1] = row[N2 * n1];
-        dft<N1, +1>(x);
+        dft<N1, SIGN>(x);
 #pragma unroll
-        for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmulc(x[k1], c_roots<N, +1>.v[n2 * k1]);
+        for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmulc(x[k1], root_rt<N, SIGN>(n2 * k1));
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) row[N2 * k1] = x[k1];
     }
@@ -94,7 +94,7 @@ __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, i
         float2 y[N2];
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) y[n2] = run[n2];
-        dft<N2, +1>(y);
+        dft<N2, SIGN>(y);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) run[k2] = y[k2];
     }
@@ -670,6 +670,162 @@ __global__ void __launch_bounds__(kGridNT) k_grid_full(ImageArgs a, int n) {
     if (blockIdx.x == 0 && tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
 }
 
+// ------------------------------------------------------------ adjoint
+// Gradient of a real image loss with respect to the visibilities:
+// gamma_b = 2 w_b H[k_b], H = forward 2-D DFT (exp(-2 pi i k.(p - N/2)/N)) of
+// the image gradient R, conjugated for baselines mirrored into the canonical
+// half, zero for dropped baselines.  H is needed only on the canonical
+// support rows.  Pass 1 (k_degrid_cols): the real columns of R, two at a time
+// packed as one complex column, forward N-point transforms along v; rows
+// k < R of both columns to scratch.  Pass 2 (k_degrid_rows): forward
+// transforms of those rows along u, then every baseline of the band reads
+// its cell.
+template <int N>
+struct DegridCfg {
+    static constexpr int NT = 256;
+    static constexpr int S = N + 1;
+    // column pairs per CTA: keep strip + exchange buffer near 64 KB
+    static constexpr int P = std::max(1, std::min({32, NT / Plan<N>::N1, int(65536 / (16 * S))}));
+    static constexpr int SW = 2 * P + 1;  // strip row stride in floats (odd)
+    static constexpr int RB = LargeCfg<N>::RB;
+};
+
+template <int N>
+size_t degrid_cols_smem() {
+    using C = DegridCfg<N>;
+    return std::max(size_t(N) * C::SW / 2 + 1, size_t(C::P) * N) * sizeof(float2) +
+           size_t(C::P) * C::S * sizeof(float2);
+}
+
+// Grid: (ceil(N/2 / P), layers in wave).  R (float [N][N]) is read at
+// out_off; rows k < R of the column transforms go to scratch[lw][k][n].
+template <int N>
+__global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, const float *resid, int l0) {
+    using C = DegridCfg<N>;
+    constexpr int NT = C::NT, S = C::S, P = C::P, SW = C::SW, H = N / 2;
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    extern __shared__ float2 sm[];
+    float *strip = reinterpret_cast<float *>(sm);          // [N][SW], FFT-order rows
+    float2 *zn = sm;                                        // [P][N] natural order (aliases strip)
+    float2 *Z = sm + std::max(size_t(N) * SW / 2 + 1, size_t(P) * N);  // [P][S]
+    const int lw = blockIdx.y;
+    const DevLayer L = a.layers[l0 + lw];
+    const ChanInfo ci = a.chans[L.chan];
+    const int R = ci.rows;
+    const int j0 = blockIdx.x * P;
+    const int tid = threadIdx.x;
+    const float *img = resid + L.out_off;
+    // strip: FFT-order row n holds image row (n + H) mod N; column jj is FFT
+    // column j0 + jj (image column j0 + jj + H), column P + jj is FFT column
+    // j0 + jj + H (image column j0 + jj)
+    for (int i = tid; i < N * 2 * P; i += NT) {
+        const int n = i / (2 * P), c = i % (2 * P);
+        const int jj = c < P ? c : c - P;
+        const int j = j0 + jj;
+        float v = 0.f;
+        if (j < H) v = __ldg(img + int64_t((n + H) % N) * N + (c < P ? j + H : j));
+        strip[n * SW + c] = v;
+    }
+    __syncthreads();
+    // step A: z = R_a + i R_b along stride N2, forward twiddles
+    for (int t = tid; t < P * N2; t += NT) {
+        const int jj = t % P, n2 = t / P;
+        float2 x[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const int n = N2 * n1 + n2;
+            x[n1] = make_float2(strip[n * SW + jj], strip[n * SW + P + jj]);
+        }
+        dft<N1, -1>(x);
+        float2 *zp = Z + jj * S + n2;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) zp[N2 * k1] = k1 == 0 ? x[0] : cmulc(x[k1], root_rt<N, -1>(n2 * k1));
+    }
+    __syncthreads();
+    // step B: outputs in natural order to zn (the strip is no longer read)
+    for (int t = tid; t < P * N1; t += NT) {
+        const int jj = t % P, k1 = t / P;
+        const float2 *zp = Z + jj * S + N2 * k1;
+        float2 y[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[n2];
+        dft<N2, -1>(y);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) zn[jj * N + k1 + N1 * k2] = y[k2];
+    }
+    __syncthreads();
+    // unpack the two real columns and keep rows k < R
+    float2 *out = a.scratch + int64_t(lw) * a.r_alloc * N;
+    for (int i = tid; i < R * P; i += NT) {
+        const int k = i / P, jj = i % P, j = j0 + jj;
+        if (j >= H) continue;
+        const float2 za = zn[jj * N + k], zb = zn[jj * N + (N - k) % N];
+        // C_a = (Z[k] + conj Z[N-k]) / 2, C_b = (Z[k] - conj Z[N-k]) / (2 i)
+        out[int64_t(k) * N + j] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+        out[int64_t(k) * N + j + H] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+    }
+}
+
+// Grid: (bands of RB rows, layers in wave).  gamma goes to dvis at vis_off.
+template <int N>
+__global__ void __launch_bounds__(LargeCfg<N>::NT) k_degrid_rows(ImageArgs a, float2 *dvis, int l0) {
+    constexpr int NT = LargeCfg<N>::NT, S = LargeCfg<N>::S, RB = LargeCfg<N>::RB;
+    extern __shared__ float2 sm[];
+    const int lw = blockIdx.y;
+    const DevLayer L = a.layers[l0 + lw];
+    const ChanInfo ci = a.chans[L.chan];
+    const int R = ci.rows;
+    const int r0 = blockIdx.x * RB;
+    const int tid = threadIdx.x;
+    const uint32_t *code = a.codes + ci.code_off;
+    float2 *g = dvis + L.vis_off;
+    if (r0 >= R) return;
+    const int nrows = min(RB, R - r0);
+    const float2 *in = a.scratch + (int64_t(lw) * a.r_alloc + r0) * N;
+    for (int i = tid; i < nrows * N; i += NT) sm[(i / N) * S + (i % N)] = in[i];
+    __syncthreads();
+    rows_fft<N, -1>(sm, S, nrows, tid, NT);
+    const float *w = ci.weighting == 1 ? a.wgt + ci.wgt_off : nullptr;
+    const float scale = 2.f * (((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f);
+    for (int64_t b = tid; b < a.nb; b += NT) {
+        const uint32_t cd = __ldg(code + b);
+        if (cd == kCodeDropped) {
+            if (r0 == 0) g[b] = make_float2(0.f, 0.f);
+            continue;
+        }
+        const int r = int(code_row(cd));
+        if (r < r0 || r >= r0 + nrows) continue;
+        const int c = int(code_col(cd));
+        const float2 h = sm[(r - r0) * S + pos_after_rows<N>(c)];
+        const float wv = scale * (w ? w[r * N + c] : 1.f);
+        g[b] = make_float2(wv * h.x, code_conj(cd) ? -wv * h.y : wv * h.y);
+    }
+}
+
+template <int N>
+Error launch_degrid_n(const ImageArgs &a, const float *resid, float2 *dvis, cudaStream_t st) {
+    if (a.n_layers == 0) return Error{0, ""};
+    using C = DegridCfg<N>;
+    const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
+    if (!a.scratch || a.scratch_bytes < per_layer)
+        return Error{-5, "degrid scratch too small for image size " + std::to_string(N)};
+    const int wave = int(std::min<size_t>(size_t(a.n_layers), std::min<size_t>(65535, a.scratch_bytes / per_layer)));
+    const size_t smem_c = degrid_cols_smem<N>();
+    const size_t smem_r = size_t(LargeCfg<N>::RB) * LargeCfg<N>::S * sizeof(float2);
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_c)));
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_r)));
+    const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
+    const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
+    for (int l0 = 0; l0 < a.n_layers; l0 += wave) {
+        const int cnt = std::min(wave, a.n_layers - l0);
+        k_degrid_cols<N><<<dim3(pchunks, unsigned(cnt)), C::NT, smem_c, st>>>(a, resid, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_degrid_rows<N><<<dim3(bands, unsigned(cnt)), LargeCfg<N>::NT, smem_r, st>>>(a, dvis, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+    }
+    return Error{0, ""};
+}
+
 constexpr size_t kSmallSmemLimit = 200 * 1024;
 
 template <int N>
@@ -755,6 +911,17 @@ size_t image_scratch_per_layer(int n_px, int r_alloc) {
 
 Error launch_image_group(int n_px, const ImageArgs &a, cudaStream_t st) {
 #define X(N_) if (n_px == N_) return launch_image_n<N_>(a, st);
+    BLINK_FOR_EACH_SIZE(X)
+#undef X
+    return Error{-2, "unsupported image size " + std::to_string(n_px)};
+}
+
+size_t degrid_scratch_per_layer(int n_px, int r_alloc) {
+    return size_t(r_alloc) * n_px * sizeof(float2);
+}
+
+Error launch_degrid_group(int n_px, const ImageArgs &a, const float *resid, float2 *dvis, cudaStream_t st) {
+#define X(N_) if (n_px == N_) return launch_degrid_n<N_>(a, resid, dvis, st);
     BLINK_FOR_EACH_SIZE(X)
 #undef X
     return Error{-2, "unsupported image size " + std::to_string(n_px)};

@@ -46,5 +46,16 @@ int supported_sizes(int32_t *out, int cap);
 size_t image_scratch_per_layer(int n_px, int r_alloc);
 Error launch_image_group(int n_px, const ImageArgs &a, cudaStream_t st);
 Error launch_grid_group(int n_px, const ImageArgs &a, cudaStream_t st);
+// Adjoint of the image path: resid (float [N][N] at out_off) -> dvis
+// (complex64 at vis_off).  Needs degrid_scratch_per_layer() bytes per layer.
+size_t degrid_scratch_per_layer(int n_px, int r_alloc);
+Error launch_degrid_group(int n_px, const ImageArgs &a, const float *resid, float2 *dvis, cudaStream_t st);
+
+// Antenna gains (blink_gains.cu): vis = g_i conj(g_j) model per layer, and
+// the per-antenna gradient accumulated over all layers.
+Error launch_apply_gains(const float2 *model, const float2 *gains, const int64_t *vis_off, int n_layers, int n_ant,
+                         int64_t nb, float2 *vis, cudaStream_t st);
+Error launch_gain_grad(const float2 *dvis, const float2 *model, const float2 *gains, const int64_t *vis_off,
+                       int n_layers, int n_ant, float2 *dgains, cudaStream_t st);
 
 }  // namespace blink

@@ -1,0 +1,153 @@
+"""GPU adjoint (blink_degrid, gain gradients, autograd) against the FP64 oracle.
+
+Tolerance: the gradient is an FP32 forward 2-D transform of the image
+gradient followed by a gather, so its error is bounded like the forward
+image's: max |gpu - oracle| <= 1e-5 * max |oracle| per layer (the oracle's
+own adjoint is pinned by FP64 finite differences in test_oracle_adjoint).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    from paper_2405_13478_gb300 import binding, build
+    build.build()
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def layer_cells(xyz, L):
+    u, v = oracle.uv(xyz, L["freq_hz"])
+    return oracle.cells(u, v, L["delta_u"], L["n_px"])
+
+
+def run_degrid(torch, ctx, xyz, layers, resid_list, nb, flags=0):
+    from paper_2405_13478_gb300 import binding
+    layers, total = binding.layer_out_offsets(layers)
+    r = torch.cat([torch.as_tensor(x.reshape(-1), dtype=torch.float32) for x in resid_list]).cuda()
+    dvis = torch.full((len(layers) * nb,), complex(float("nan"), 0), dtype=torch.complex64,
+                      device="cuda")
+    lay = [dict(L, vis_offset=k * nb) for k, L in enumerate(layers)]
+    ctx.degrid(torch.as_tensor(xyz).cuda(), lay, r, dvis, flags)
+    torch.cuda.synchronize()
+    return dvis.cpu().numpy().reshape(len(layers), nb)
+
+
+@pytest.mark.parametrize("n_px", [16, 20, 128, 180, 256, 512, 1024])
+@pytest.mark.parametrize("weighting", [0, 1])
+def test_degrid_matches_oracle(torch, ctx, n_px, weighting):
+    ws = synth.config1(seed=n_px + 7)
+    du = synth.max_uv(ws.ant_xyz, ws.freqs_hz[0]) / (n_px / 2 - 1)
+    if n_px <= 20:
+        du *= 3.0  # also exercise dropped baselines
+    L = dict(n_px=n_px, weighting=weighting, freq_hz=float(ws.freqs_hz[0]), delta_u=du,
+             vis_offset=0)
+    rng = np.random.default_rng(n_px)
+    resid = rng.normal(size=(n_px, n_px))
+    got = run_degrid(torch, ctx, ws.ant_xyz, [L], [resid], ws.n_baselines)[0]
+    ku, kv = layer_cells(ws.ant_xyz, L)
+    want = oracle.degrid(ku, kv, resid.astype(np.float32).astype(np.float64), weighting, "fft")
+    assert np.isfinite(got).all()
+    assert np.abs(got - want).max() <= TOL * np.abs(want).max()
+    assert not got[ku == oracle.DROPPED].any()
+
+
+def test_degrid_station_layers_and_normalize(torch, ctx):
+    ws = synth.config5(seed=3, n_times=1)
+    layers = [dict(n_px=1024, weighting=0, freq_hz=float(f), delta_u=0.5, vis_offset=0)
+              for f in ws.freqs_hz[[0, 7]]]
+    layers += [dict(n_px=180, weighting=1, freq_hz=float(ws.freqs_hz[3]), delta_u=0.5,
+                    vis_offset=0)]
+    rng = np.random.default_rng(5)
+    res = [rng.normal(size=(L["n_px"], L["n_px"])) for L in layers]
+    got = run_degrid(torch, ctx, ws.ant_xyz, layers, res, ws.n_baselines)
+    got_n = run_degrid(torch, ctx, ws.ant_xyz, layers, res, ws.n_baselines, flags=1)
+    for k, L in enumerate(layers):
+        ku, kv = layer_cells(ws.ant_xyz, L)
+        want = oracle.degrid(ku, kv, res[k].astype(np.float32).astype(np.float64),
+                             L["weighting"], "fft")
+        assert np.abs(got[k] - want).max() <= TOL * np.abs(want).max()
+        _, _, wsum = oracle.grid(ku, kv, np.zeros(ku.size, np.complex64), L["n_px"],
+                                 L["weighting"])
+        assert np.abs(got_n[k] * wsum - got[k]).max() <= 1e-6 * np.abs(got[k]).max()
+
+
+def test_adjoint_identity_on_gpu(torch, ctx):
+    from paper_2405_13478_gb300 import binding
+    ws = synth.config2(seed=4, n_times=1)
+    B = ws.n_baselines
+    layers = [dict(n_px=180, weighting=w, freq_hz=float(ws.freqs_hz[c]), delta_u=0.5,
+                   vis_offset=k * B) for k, (c, w) in enumerate(((0, 1), (31, 0)))]
+    layers, total = binding.layer_out_offsets(layers)
+    vis = synth.noise((2 * B,), 1.0, 9, "cpu").cuda()
+    img = torch.empty(total, device="cuda")
+    ctx.image_batch(torch.as_tensor(ws.ant_xyz).cuda(), layers, vis, img)
+    r = torch.randn(total, generator=torch.Generator().manual_seed(3)).cuda()
+    dvis = torch.empty(2 * B, dtype=torch.complex64, device="cuda")
+    ctx.degrid(torch.as_tensor(ws.ant_xyz).cuda(), layers, r, dvis)
+    torch.cuda.synchronize()
+    lhs = float((r.double() * img.double()).sum())
+    rhs = float((vis.to(torch.complex128) * dvis.to(torch.complex128).conj()).real.sum())
+    scale = float((r.double().abs() * img.double().abs()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_autograd_gains_config5_slice(torch, ctx):
+    """Config-5 form: V = g_i conj(g_j) M, loss = sum (image(V) - image(M))^2;
+    gradients w.r.t. V and g from torch.autograd (library kernels) against
+    the CPU reference gradient of the oracle."""
+    from paper_2405_13478_gb300 import autograd, binding
+    ws = synth.config5(seed=11, n_times=1)
+    B, n_ant = ws.n_baselines, ws.n_ant
+    chans = [0, 5]
+    model = torch.as_tensor(synth.model_vis(ws.ant_xyz, ws.freqs_hz[chans], ws.sky)
+                            .astype(np.complex64)).reshape(-1)
+    layers = [dict(n_px=1024, weighting=0, freq_hz=float(ws.freqs_hz[c]), delta_u=0.5,
+                   vis_offset=k * B) for k, c in enumerate(chans)]
+    layers, total = binding.layer_out_offsets(layers)
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    plan = ctx.plan(d_xyz, layers)
+    g = torch.as_tensor(ws.gains.astype(np.complex64)).cuda().requires_grad_(True)
+    m = model.cuda()
+    target = autograd.dirty_images(m, plan, total).detach()
+    vis = autograd.apply_gains(g, m, ctx, n_ant, layers)
+    vis.retain_grad()
+    img = autograd.dirty_images(vis, plan, total)
+    loss = ((img - target) ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    # CPU reference: oracle images, residual, adjoint and chain rule (FP64)
+    mnp = model.numpy()
+    gnp = ws.gains.astype(np.complex64).astype(np.complex128)
+    i, j = np.triu_indices(n_ant, 1)
+    gam_g = np.zeros(n_ant, np.complex128)
+    for k, L in enumerate(layers):
+        mk = mnp[k * B:(k + 1) * B].astype(np.complex128)
+        vk = (gnp[i] * np.conj(gnp[j]) * mk)
+        ku, kv = layer_cells(ws.ant_xyz, L)
+        gi, _, _ = oracle.grid_c128(ku, kv, vk, 1024, 0)
+        gt, _, _ = oracle.grid_c128(ku, kv, mk, 1024, 0)
+        ii, _ = oracle.image_fft(gi)
+        it, _ = oracle.image_fft(gt)
+        gam_v = oracle.degrid(ku, kv, 2 * (ii - it), 0, "fft")
+        got_v = vis.grad.cpu().numpy()[k * B:(k + 1) * B]
+        assert np.abs(got_v - gam_v).max() <= 1e-4 * np.abs(gam_v).max()
+        oracle.gain_grad(n_ant, gam_v, gnp, mk, gam_g)
+    got_g = g.grad.cpu().numpy()
+    assert np.abs(got_g - gam_g).max() <= 1e-4 * np.abs(gam_g).max()
+    plan.close()
