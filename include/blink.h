@@ -68,6 +68,18 @@ typedef enum { BLINK_NATURAL = 0, BLINK_UNIFORM = 1 } blink_weighting;
 
 /* Flags of blink_image_batch / blink_plan_image. */
 #define BLINK_NORMALIZE 0x1u /* divide each image by its summed weight */
+/* Transform of the second pass (along v).  Default: FP32 FFT.  The others
+ * run it as a dense real GEMM on the tensor cores (image sizes that are a
+ * multiple of 256; other sizes keep the FFT), FP32 accumulation:
+ *   BF16 / FP16        one product of rounded operands,
+ *   BF16X3 / FP16X3    split-precision recovery (hi*hi + hi*lo + lo*hi).
+ * Error against the FP64 result is stated per mode in the tests. */
+#define BLINK_TRANSFORM_MASK 0xF0u
+#define BLINK_TRANSFORM_FFT 0x00u
+#define BLINK_TRANSFORM_BF16 0x10u
+#define BLINK_TRANSFORM_BF16X3 0x20u
+#define BLINK_TRANSFORM_FP16 0x30u
+#define BLINK_TRANSFORM_FP16X3 0x40u
 
 /* One image ("layer", Sec. 5.2.4). */
 typedef struct {
@@ -186,6 +198,11 @@ BLINK_API int blink_plan_create(blink_ctx *ctx, const double *d_ant_xyz, int n_a
 BLINK_API int blink_plan_image(blink_plan *plan, const float *d_vis, float *d_images, float *d_wsum,
                      uint32_t flags, void *stream);
 BLINK_API void blink_plan_destroy(blink_plan *plan);
+
+/* Waits for `stream` and returns the plan's device status word: BLINK_OK, or
+ * BLINK_ERR_TIMEOUT if a bounded device-side wait of an earlier launch gave
+ * up (that launch's output is incomplete).  Clears the word. */
+BLINK_API int blink_plan_check(blink_plan *plan, void *stream);
 
 /* Summed weight and kept-baseline count of layer `layer` of a plan (host
  * copies; no device work). */

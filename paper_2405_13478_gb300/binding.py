@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_PKG, "_build", "libblink.so")
 OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE = 0, -1, -2, -3, -4, -5
 NATURAL, UNIFORM = 0, 1
 NORMALIZE = 0x1
+TRANSFORM_FFT, TRANSFORM_BF16, TRANSFORM_BF16X3, TRANSFORM_FP16, TRANSFORM_FP16X3 = (
+    0x00, 0x10, 0x20, 0x30, 0x40)
 DROPPED = -(2 ** 31)
 
 # Symbols declared in include/blink.h (checked by the CPU test suite).
@@ -25,7 +27,7 @@ EXPORTS = (
     "blink_last_error", "blink_cells", "blink_grid", "blink_image_batch", "blink_plan_create",
     "blink_plan_image", "blink_plan_destroy", "blink_plan_layer_info",
     "blink_image_batch_noalloc", "blink_image_batch_host", "blink_degrid", "blink_plan_degrid",
-    "blink_apply_gains", "blink_gain_grad",
+    "blink_apply_gains", "blink_gain_grad", "blink_plan_check",
 )
 
 
@@ -87,6 +89,8 @@ def lib(path: str = LIB_PATH):
     L.blink_apply_gains.argtypes = [P, I, LP, I, P, P, P, P]
     L.blink_gain_grad.restype = I
     L.blink_gain_grad.argtypes = [P, I, LP, I, P, P, P, P, P]
+    L.blink_plan_check.restype = I
+    L.blink_plan_check.argtypes = [P, P]
     L.blink_plan_layer_info.restype = I
     L.blink_plan_layer_info.argtypes = [P, I, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int64)]
@@ -287,6 +291,10 @@ class Plan:
         _check_dev(dimage, dvis_out)
         self.ctx._raise(self.ctx._lib.blink_plan_degrid(self.handle, _ptr(dimage), _ptr(dvis_out),
                                                         int(flags), _stream(stream)))
+
+    def check(self, stream=None):
+        """Synchronise and raise if a bounded device-side wait timed out."""
+        self.ctx._raise(self.ctx._lib.blink_plan_check(self.handle, _stream(stream)))
 
     def layer_info(self, layer: int):
         w = ctypes.c_float()

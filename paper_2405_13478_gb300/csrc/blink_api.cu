@@ -39,6 +39,7 @@ struct blink_plan {
     std::vector<ChanGeom> geoms;
     std::vector<ChanInfo> infos;
     std::vector<int32_t> layer_chan;
+    std::vector<int64_t> layer_out;  // out_offset per layer in group order
     struct Group {
         int n_px;
         int first;
@@ -62,6 +63,9 @@ struct blink_plan {
     unsigned char *d_sched = nullptr;
     float2 *d_dscratch = nullptr;  // adjoint column-transform scratch (allocated on first use)
     size_t dscratch_bytes = 0;
+    float2 *d_gscratch = nullptr;  // tensor-core transform scratch (allocated on first use)
+    size_t gscratch_bytes = 0;
+    int *d_status = nullptr;       // device status word (in the table block)
     cudaStream_t last_stream = nullptr;
 };
 
@@ -151,6 +155,8 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     if (p->d_scratch) cudaFreeAsync(p->d_scratch, st);
     if (p->d_sched) cudaFreeAsync(p->d_sched, st);
     if (p->d_dscratch) cudaFreeAsync(p->d_dscratch, st);
+    if (p->d_gscratch) cudaFreeAsync(p->d_gscratch, st);
+    p->d_gscratch = nullptr;
     p->d_block = nullptr;
     p->d_scratch = nullptr;
     p->d_sched = nullptr;
@@ -237,6 +243,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         const int l = order[size_t(k)];
         dl[size_t(k)] = DevLayer{h_layers[l].vis_offset, h_layers[l].out_offset,
                                  p->layer_chan[size_t(l)], l};
+        p->layer_out.push_back(h_layers[l].out_offset);
         if (p->groups.empty() || p->groups.back().n_px != h_layers[l].n_px)
             p->groups.push_back(blink_plan::Group{h_layers[l].n_px, k, 0, 1, 0, 0, 0});
         p->groups.back().count++;
@@ -249,6 +256,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     const size_t o_codes = off; off = align_up(off + sizeof(uint32_t) * size_t(p->n_chan) * size_t(p->nb), a);
     const size_t o_wgt = off; off = align_up(off + sizeof(float) * size_t(std::max<int64_t>(wgt_total, 1)), a);
     const size_t o_layers = off; off = align_up(off + sizeof(DevLayer) * size_t(std::max(n_layers, 1)), a);
+    const size_t o_status = off; off = align_up(off + sizeof(int), a);
     const size_t o_cells = off;
     if (want_cells) off = align_up(off + sizeof(int2) * size_t(p->n_chan) * size_t(p->nb), a);
     void *blk = nullptr;
@@ -262,6 +270,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     p->d_wgt = reinterpret_cast<float *>(p->d_block + o_wgt);
     p->d_layers = reinterpret_cast<DevLayer *>(p->d_block + o_layers);
     p->d_cells = want_cells ? reinterpret_cast<int2 *>(p->d_block + o_cells) : nullptr;
+    p->d_status = reinterpret_cast<int *>(p->d_block + o_status);
 #define TRY(call)                                                                          \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
@@ -278,6 +287,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         TRY(cudaMemcpyAsync(p->d_layers, dl.data(), sizeof(DevLayer) * dl.size(),
                             cudaMemcpyHostToDevice, st));
     if (p->any_uniform) TRY(cudaMemsetAsync(p->d_wgt, 0, sizeof(float) * size_t(wgt_total), st));
+    TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
     if (sched_total) {
         void *sb = nullptr;
         e = cudaMallocFromPoolAsync(&sb, size_t(sched_total), ctx->pool, st);
@@ -343,6 +353,7 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.sched_ok = g.sched_ok;
     a.max_chunk = g.max_chunk;
     a.max_seg = g.max_seg;
+    a.status = p->d_status;
     return a;
 }
 
@@ -416,14 +427,65 @@ int blink_plan_image(blink_plan *p, const float *d_vis, float *d_images, float *
     if (!p) return BLINK_ERR_INVALID;
     blink_ctx *ctx = p->ctx;
     if (p->n_layers && (!d_vis || !d_images)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
-    if (flags & ~uint32_t(BLINK_NORMALIZE)) return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
+    const uint32_t mode = (flags & BLINK_TRANSFORM_MASK) >> 4;
+    if ((flags & ~uint32_t(BLINK_NORMALIZE | BLINK_TRANSFORM_MASK)) || mode > 4)
+        return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     p->last_stream = st;
+    // groups that take the tensor-core transform: supported size, 16-byte
+    // aligned image rows
+    auto gemm_ok = [&](const blink_plan::Group &grp) {
+        if (!mode || !blink::dftgemm_supported(grp.n_px, grp.r_alloc, mode) ||
+            (reinterpret_cast<uintptr_t>(d_images) & 15))
+            return false;
+        for (int k = grp.first; k < grp.first + grp.count; ++k)
+            if (p->layer_out[size_t(k)] & 3) return false;
+        return true;
+    };
+    if (mode && !p->d_gscratch) {
+        size_t need = 0;
+        for (const auto &grp : p->groups) {
+            if (!gemm_ok(grp)) continue;
+            const size_t per = blink::dftgemm_scratch_per_layer(grp.n_px, grp.r_alloc);
+            const int rp = (grp.r_alloc + 7) / 8 * 8;
+            const size_t fixed = 2 * size_t(grp.n_px) * 2 * rp * 2 + 512;
+            need = std::max(need, fixed + std::max(per, std::min(per * size_t(grp.count), kScratchCap)));
+        }
+        if (need) {
+            void *ptr = nullptr;
+            const cudaError_t e = cudaMallocFromPoolAsync(&ptr, need, ctx->pool, st);
+            if (e != cudaSuccess)
+                return fail(ctx, BLINK_ERR_WORKSPACE, std::string("tensor-core scratch: ") + cudaGetErrorString(e));
+            p->d_gscratch = static_cast<float2 *>(ptr);
+            p->gscratch_bytes = need;
+        }
+    }
     for (const auto &grp : p->groups) {
-        Error e = blink::launch_image_group(grp.n_px, group_args(p, grp, d_vis, d_images, d_wsum, flags), st);
+        blink::ImageArgs a = group_args(p, grp, d_vis, d_images, d_wsum, flags & BLINK_NORMALIZE);
+        Error e;
+        if (gemm_ok(grp)) {
+            a.scratch = p->d_gscratch;
+            a.scratch_bytes = p->gscratch_bytes;
+            e = blink::launch_dftgemm_group(grp.n_px, int(mode), a, st);
+            if (!e.status && d_wsum) e = blink::launch_wsum_copy(a, st);
+        } else {
+            e = blink::launch_image_group(grp.n_px, a, st);
+        }
         if (e.status) return fail(ctx, e);
     }
+    return BLINK_OK;
+}
+
+int blink_plan_check(blink_plan *p, void *stream) {
+    if (!p) return BLINK_ERR_INVALID;
+    DeviceGuard g(p->ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int word = 0;
+    if (cudaMemcpyAsync(&word, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(p->ctx, BLINK_ERR_CUDA, "status read failed");
+    if (word) return fail(p->ctx, word, "a bounded device-side wait gave up");
     return BLINK_OK;
 }
 

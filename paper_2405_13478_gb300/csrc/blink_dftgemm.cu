@@ -1,0 +1,395 @@
+// blink_dftgemm.cu -- pass 2 of the image transform as a dense GEMM on the
+// fifth-generation tensor cores (tcgen05), in BF16 or FP16 with FP32
+// accumulation and optional split-precision recovery.
+//
+// After pass 1 (gridding + inverse DFT of every canonical row along u, the
+// same kernel as the FFT path) a layer holds T[k][p], k < R (support rows),
+// p the FFT-order column.  The real image is
+//   I[y][x] = sum_{k<R} c_k (cos(2 pi k y'/N) Re T[k][p] - sin(2 pi k y'/N) Im T[k][p])
+// with y' = y - N/2, x = (p + N/2) mod N, c_0 = 1 and c_k = 2 (Hermitian
+// symmetry along v; Sec. 4.3 Eq. 6, Sec. 5.2.2).  That is I = A B with
+//   A[y][k] = c_k cos(..) for k < Rp, -c_{k-Rp} sin(..) for Rp <= k < 2 Rp,
+//   B[k][p] = Re T[k][p] (k < Rp), Im T[k - Rp][p] (Rp <= k < 2 Rp),
+// a real GEMM of M = N, N = N, K = 2 Rp (Rp = R rounded up to 8).  A depends
+// only on (N, Rp) and is built once in FP64 with exact integer phase
+// reduction; B is converted per layer.
+//
+// Precision: x = hi + lo with hi = round(x) and lo = round((x - hi) 2^s) 2^-s;
+// the split product keeps A_hi B_hi + A_hi B_lo + A_lo B_hi (the A_lo B_lo
+// term is below FP32 resolution).  FP16 needs range control: every layer's B
+// is scaled by a power of two so its largest entry is below 2^14, and the
+// cross terms (lo scaled by 2^11) go to a second TMEM accumulator.
+//
+// Operands sit in shared memory in the K-major core-matrix layout of the
+// tensor cores (8 rows x 16 bytes per core matrix, no swizzle); global memory
+// holds them already in that layout so each tile arrives with one 1-D TMA
+// bulk copy.  One CTA computes one 128 x 256 output tile: 4 warps, thread 0
+// issues the MMAs, TMEM holds the FP32 accumulators, tcgen05.ld reads them
+// back for the epilogue.  Every wait is bounded; a timeout sets the status
+// word and the CTA still releases its tensor memory.
+#include "blink_common.cuh"
+#include "blink_kernels.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+namespace blink {
+
+namespace {
+
+constexpr int kTileM = 128, kTileN = 256;
+constexpr long kWaitLimit = 1L << 26;
+
+struct DftArgs {
+    const uint16_t *a_hi, *a_lo;  // [N / 128] blocks of 128 x K (tiled)
+    const uint16_t *b_hi, *b_lo;  // [layers][N / 256] blocks of 256 x K (tiled)
+    const int *b_exp;             // per-layer power-of-two scale of B (FP16)
+    const DevLayer *layers;
+    const ChanInfo *chans;
+    float *out;
+    uint32_t flags;
+    int n_px, K;
+    int *status;
+};
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// Element (r, k) of a tile with K columns in the K-major core-matrix layout.
+__host__ __device__ __forceinline__ int tiled(int r, int k, int K) {
+    return ((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = uint64_t((addr >> 4) & 0x3FFF);
+    d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
+    d |= uint64_t(1) << 46;  // descriptor version of this tensor-core generation; no swizzle
+    return d;
+}
+
+template <bool FP16>
+__device__ __forceinline__ uint16_t to_bits(float x) {
+    if constexpr (FP16) {
+        return __half_as_ushort(__float2half_rn(x));
+    } else {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    }
+}
+template <bool FP16>
+__device__ __forceinline__ float from_bits(uint16_t b) {
+    if constexpr (FP16) {
+        return __half2float(__ushort_as_half(b));
+    } else {
+        return __bfloat162float(__ushort_as_bfloat16(b));
+    }
+}
+
+template <bool FP16>
+constexpr int lo_shift() { return FP16 ? 11 : 0; }
+
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
+    for (long it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- operand A
+// A[y][k] for one image size, hi and lo parts, tiled per 128-row block.
+template <bool FP16>
+__global__ void k_dft_table(int N, int Rp, uint16_t *a_hi, uint16_t *a_lo) {
+    const int K = 2 * Rp;
+    const int64_t total = int64_t(N) * K;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int y = int(i / K), k = int(i % K);
+        const int kk = k < Rp ? k : k - Rp;
+        const int64_t m = ((int64_t(kk) * (y - N / 2)) % N + N) % N;  // exact phase index
+        double s, c;
+        sincospi(2.0 * double(m) / double(N), &s, &c);
+        const double ck = kk == 0 ? 1.0 : 2.0;
+        const float x = float(k < Rp ? ck * c : -ck * s);
+        const uint16_t hb = to_bits<FP16>(x);
+        const float lo = (x - from_bits<FP16>(hb)) * float(1 << lo_shift<FP16>());
+        const int64_t o = int64_t(y / kTileM) * kTileM * K + tiled(y % kTileM, k, K);
+        a_hi[o] = hb;
+        a_lo[o] = to_bits<FP16>(lo);
+    }
+}
+
+// ---------------------------------------------------------------- operand B
+// Per layer: T (FP32 complex [r_alloc][N] in scratch) -> B hi/lo tiles.
+// One CTA per layer.  FP16: scale 2^-e with the largest |entry| below 2^14.
+template <bool FP16>
+__global__ void __launch_bounds__(256) k_split(const float2 *__restrict__ T, int r_alloc, int N, int Rp,
+                                               const DevLayer *__restrict__ layers,
+                                               const ChanInfo *__restrict__ chans, int l0, uint16_t *b_hi,
+                                               uint16_t *b_lo, int *b_exp) {
+    const int lw = blockIdx.x;
+    const DevLayer L = layers[l0 + lw];
+    const int R = chans[L.chan].rows;
+    const int K = 2 * Rp;
+    const float2 *t = T + int64_t(lw) * r_alloc * N;
+    float scale = 1.f;
+    if constexpr (FP16) {
+        float m = 0.f;
+        for (int i = threadIdx.x; i < R * N; i += blockDim.x) m = fmaxf(m, fmaxf(fabsf(t[i].x), fabsf(t[i].y)));
+        __shared__ float red[256];
+        red[threadIdx.x] = m;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (int(threadIdx.x) < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
+            __syncthreads();
+        }
+        int e = 0;
+        if (red[0] > 0.f) e = max(ilogbf(red[0]) - 13, -100);
+        if (threadIdx.x == 0) b_exp[lw] = e;
+        scale = ldexpf(1.f, -e);
+    }
+    uint16_t *hi = b_hi + int64_t(lw) * N * K;
+    uint16_t *lo = b_lo + int64_t(lw) * N * K;
+    const float lo_scale = float(1 << lo_shift<FP16>());
+    // one thread per (column p, group of 8 k): 16-byte stores
+    for (int i = threadIdx.x; i < N * (K / 8); i += blockDim.x) {
+        const int p = i % N, k8 = i / N;
+        uint16_t h[8], l[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = 8 * k8 + j;
+            const int r = k < Rp ? k : k - Rp;
+            float x = 0.f;
+            if (r < R) x = (k < Rp ? t[int64_t(r) * N + p].x : t[int64_t(r) * N + p].y) * scale;
+            h[j] = to_bits<FP16>(x);
+            l[j] = to_bits<FP16>((x - from_bits<FP16>(h[j])) * lo_scale);
+        }
+        const int64_t o = int64_t(p / kTileN) * kTileN * K + tiled(p % kTileN, 8 * k8, K);
+        uint4 hv, lv;
+        hv.x = h[0] | (uint32_t(h[1]) << 16); hv.y = h[2] | (uint32_t(h[3]) << 16);
+        hv.z = h[4] | (uint32_t(h[5]) << 16); hv.w = h[6] | (uint32_t(h[7]) << 16);
+        lv.x = l[0] | (uint32_t(l[1]) << 16); lv.y = l[2] | (uint32_t(l[3]) << 16);
+        lv.z = l[4] | (uint32_t(l[5]) << 16); lv.w = l[6] | (uint32_t(l[7]) << 16);
+        *reinterpret_cast<uint4 *>(hi + o) = hv;
+        *reinterpret_cast<uint4 *>(lo + o) = lv;
+    }
+}
+
+// ----------------------------------------------------------------- the GEMM
+template <int NC>
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+// Grid: (N / 128, N / 256, layers of the wave).  128 threads.
+template <bool FP16, int SPLIT>
+__global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0) {
+    constexpr bool CROSS = FP16 && SPLIT == 3;      // separate accumulator for the cross terms
+    constexpr uint32_t NCOL = CROSS ? 512 : 256;    // TMEM columns
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t bar_load, bar_mma;
+    __shared__ uint32_t tmem_base;
+    const int K = d.K, N = d.n_px, H = N / 2;
+    const int mt = blockIdx.x, nt = blockIdx.y, lw = blockIdx.z;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t a_bytes = uint32_t(kTileM) * K * 2, b_bytes = uint32_t(kTileN) * K * 2;
+    unsigned char *sA_hi = sm, *sA_lo = sm + a_bytes;
+    unsigned char *sB_hi = sm + (SPLIT == 3 ? 2 : 1) * a_bytes;
+    unsigned char *sB_lo = sB_hi + b_bytes;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_load)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_mma)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                     "r"(NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        const uint32_t total = (SPLIT == 3 ? 2 : 1) * (a_bytes + b_bytes);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&bar_load)), "r"(total)
+                     : "memory");
+        const int n_tiles = N / kTileN;
+        const uint16_t *ga[2] = {d.a_hi + int64_t(mt) * kTileM * K, d.a_lo + int64_t(mt) * kTileM * K};
+        const int64_t bo = (int64_t(lw) * n_tiles + nt) * kTileN * K;
+        const uint16_t *gb[2] = {d.b_hi + bo, d.b_lo + bo};
+        unsigned char *sa[2] = {sA_hi, sA_lo}, *sb[2] = {sB_hi, sB_lo};
+        for (int h = 0; h < (SPLIT == 3 ? 2 : 1); ++h) {
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    saddr(sa[h])),
+                "l"(ga[h]), "r"(a_bytes), "r"(saddr(&bar_load))
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    saddr(sb[h])),
+                "l"(gb[h]), "r"(b_bytes), "r"(saddr(&bar_load))
+                : "memory");
+        }
+    }
+    const bool loaded = wait_parity(saddr(&bar_load), 0);
+    bool ok = loaded;
+    if (tid == 0 && loaded) {
+        // D = A B^T over K in steps of 16: M = 128, N = 256, both K-major
+        constexpr uint32_t fmt = FP16 ? 0u : 1u;  // 0 FP16, 1 BF16
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(kTileN >> 3) << 17) |
+                               (uint32_t(kTileM >> 4) << 24);
+        const uint32_t sbo = uint32_t(K / 8) * 128;
+        for (int s = 0; s < K / 16; ++s) {
+            const uint64_t ah = smem_desc(saddr(sA_hi) + s * 256, 128, sbo);
+            const uint64_t bh = smem_desc(saddr(sB_hi) + s * 256, 128, sbo);
+            mma_f16(tmem, ah, bh, idesc, s > 0);
+            if constexpr (SPLIT == 3) {
+                const uint64_t al = smem_desc(saddr(sA_lo) + s * 256, 128, sbo);
+                const uint64_t bl = smem_desc(saddr(sB_lo) + s * 256, 128, sbo);
+                const uint32_t tx = CROSS ? tmem + 256 : tmem;
+                mma_f16(tx, ah, bl, idesc, CROSS ? uint32_t(s > 0) : 1u);
+                mma_f16(tx, al, bh, idesc, 1u);
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         saddr(&bar_mma))
+                     : "memory");
+    }
+    if (loaded) ok = wait_parity(saddr(&bar_mma), 0);
+    if (!ok) {
+        if (tid == 0 && d.status) atomicExch(d.status, -4);  // BLINK_ERR_TIMEOUT
+        // let copies or MMAs still in flight finish before the memory goes away
+        wait_parity(saddr(&bar_load), 0);
+        if (loaded) wait_parity(saddr(&bar_mma), 0);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const DevLayer L = d.layers[l0 + lw];
+        const ChanInfo ci = d.chans[L.chan];
+        float scale = ((d.flags & 1u) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
+        if (FP16) scale = ldexpf(scale, d.b_exp[lw]);
+        const float cross = 1.f / float(1 << lo_shift<FP16>());
+        const int y = mt * kTileM + warp * 32 + lane;
+        float *row = d.out + L.out_off + int64_t(y) * N;
+        for (int c0 = 0; c0 < kTileN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32<32>(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+            uint32_t q[32];
+            if constexpr (CROSS) tmem_ld32<32>(tmem + (uint32_t(warp * 32) << 16) + uint32_t(256 + c0), q);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int p0 = nt * kTileN + c0;
+            float *o = row + ((p0 + H) % N);
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                float4 v;
+                float e0 = __uint_as_float(r[j]), e1 = __uint_as_float(r[j + 1]);
+                float e2 = __uint_as_float(r[j + 2]), e3 = __uint_as_float(r[j + 3]);
+                if constexpr (CROSS) {
+                    e0 = fmaf(__uint_as_float(q[j]), cross, e0);
+                    e1 = fmaf(__uint_as_float(q[j + 1]), cross, e1);
+                    e2 = fmaf(__uint_as_float(q[j + 2]), cross, e2);
+                    e3 = fmaf(__uint_as_float(q[j + 3]), cross, e3);
+                }
+                v.x = e0 * scale;
+                v.y = e1 * scale;
+                v.z = e2 * scale;
+                v.w = e3 * scale;
+                __stcs(reinterpret_cast<float4 *>(o + j), v);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
+}
+
+template <bool FP16, int SPLIT>
+Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
+    const int K = 2 * Rp;
+    const size_t a_elems = size_t(N) * K;
+    const size_t t_bytes = size_t(a.r_alloc) * N * sizeof(float2);
+    const size_t b_elems = size_t(N) * K;
+    const size_t per_layer = t_bytes + 2 * b_elems * 2 + 16;
+    const size_t fixed = 2 * a_elems * 2 + 256;
+    if (!a.scratch || a.scratch_bytes < fixed + per_layer)
+        return Error{-5, "tensor-core transform scratch too small"};
+    const int wave = int(std::min<size_t>(size_t(a.n_layers), std::min<size_t>(65535, (a.scratch_bytes - fixed) / per_layer)));
+    unsigned char *base = reinterpret_cast<unsigned char *>(a.scratch);
+    uint16_t *a_hi = reinterpret_cast<uint16_t *>(base);
+    uint16_t *a_lo = a_hi + a_elems;
+    unsigned char *wave_base = base + ((fixed + 255) / 256) * 256;
+    float2 *T = reinterpret_cast<float2 *>(wave_base);
+    uint16_t *b_hi = reinterpret_cast<uint16_t *>(wave_base + size_t(wave) * t_bytes);
+    uint16_t *b_lo = b_hi + size_t(wave) * b_elems;
+    int *b_exp = reinterpret_cast<int *>(b_lo + size_t(wave) * b_elems);
+    k_dft_table<FP16><<<256, 256, 0, st>>>(N, Rp, a_hi, a_lo);
+    BLINK_CUDA_TRY(cudaGetLastError());
+    const size_t smem = size_t(SPLIT == 3 ? 2 : 1) * (size_t(kTileM) + kTileN) * K * 2;
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_dftgemm<FP16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    for (int l0 = 0; l0 < a.n_layers; l0 += wave) {
+        const int cnt = std::min(wave, a.n_layers - l0);
+        ImageArgs ra = a;
+        ra.scratch = T;
+        ra.scratch_bytes = size_t(wave) * t_bytes;
+        Error e = launch_rows_wave(N, ra, l0, cnt, st);
+        if (e.status) return e;
+        k_split<FP16><<<cnt, 256, 0, st>>>(T, a.r_alloc, N, Rp, a.layers, a.chans, l0, b_hi, b_lo, b_exp);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        DftArgs d{a_hi, a_lo, b_hi, b_lo, b_exp, a.layers, a.chans, static_cast<float *>(a.out), a.flags, N, K, a.status};
+        k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / kTileN), unsigned(cnt)), 128, smem, st>>>(d, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+    }
+    return Error{0, ""};
+}
+
+}  // namespace
+
+bool dftgemm_supported(int n_px, int r_alloc, int mode) {
+    const int Rp = (r_alloc + 7) / 8 * 8;
+    const size_t smem = size_t(mode == 2 || mode == 4 ? 2 : 1) * (size_t(kTileM) + kTileN) * 2 * Rp * 2;
+    return n_px >= kTileN && n_px % kTileN == 0 && image_size_supported(n_px) && 2 * Rp <= 256 &&
+           smem <= 227 * 1024;
+}
+
+size_t dftgemm_scratch_per_layer(int n_px, int r_alloc) {
+    const int Rp = (r_alloc + 7) / 8 * 8;
+    return size_t(r_alloc) * n_px * sizeof(float2) + 2 * size_t(n_px) * 2 * Rp * 2 + 16;
+}
+
+Error launch_dftgemm_group(int n_px, int mode, const ImageArgs &a, cudaStream_t st) {
+    if (a.n_layers == 0) return Error{0, ""};
+    if (!dftgemm_supported(n_px, a.r_alloc, mode)) return Error{-2, "tensor-core transform: unsupported size or support"};
+    const int Rp = (a.r_alloc + 7) / 8 * 8;
+    const size_t smem = size_t(mode == 2 || mode == 4 ? 2 : 1) * (size_t(kTileM) + kTileN) * 2 * Rp * 2;
+    if (2 * Rp > 256 || smem > 227 * 1024)
+        return Error{-2, "tensor-core transform: too many support rows for shared memory"};
+    switch (mode) {
+        case 1: return run_mode<false, 1>(n_px, a, Rp, st);
+        case 2: return run_mode<false, 3>(n_px, a, Rp, st);
+        case 3: return run_mode<true, 1>(n_px, a, Rp, st);
+        case 4: return run_mode<true, 3>(n_px, a, Rp, st);
+        default: return Error{-1, "unknown transform mode"};
+    }
+}
+
+}  // namespace blink

@@ -916,6 +916,24 @@ Error launch_image_group(int n_px, const ImageArgs &a, cudaStream_t st) {
     return Error{-2, "unsupported image size " + std::to_string(n_px)};
 }
 
+template <int N>
+Error launch_rows_wave_n(const ImageArgs &a, int l0, int cnt, cudaStream_t st) {
+    using C = LargeCfg<N>;
+    const size_t smem_rows = size_t(C::RB) * C::S * sizeof(float2);
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_rows)));
+    const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
+    k_rows<N><<<dim3(bands, unsigned(cnt)), C::NT, smem_rows, st>>>(a, l0);
+    BLINK_CUDA_TRY(cudaGetLastError());
+    return Error{0, ""};
+}
+
+Error launch_rows_wave(int n_px, const ImageArgs &a, int l0, int cnt, cudaStream_t st) {
+#define X(N_) if (n_px == N_) return launch_rows_wave_n<N_>(a, l0, cnt, st);
+    BLINK_FOR_EACH_SIZE(X)
+#undef X
+    return Error{-2, "unsupported image size " + std::to_string(n_px)};
+}
+
 size_t degrid_scratch_per_layer(int n_px, int r_alloc) {
     return size_t(r_alloc) * n_px * sizeof(float2);
 }

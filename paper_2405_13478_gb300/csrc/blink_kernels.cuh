@@ -37,6 +37,7 @@ struct ImageArgs {
     int sched_ok;               // every channel of the group has a schedule
     int max_chunk;              // largest staging chunk of the group's channels
     int max_seg;                // longest per-chunk schedule segment (entries)
+    int *status;                // device status word (bounded waits report BLINK_ERR_TIMEOUT)
 };
 
 bool image_size_supported(int n_px);
@@ -46,6 +47,18 @@ int supported_sizes(int32_t *out, int cap);
 size_t image_scratch_per_layer(int n_px, int r_alloc);
 Error launch_image_group(int n_px, const ImageArgs &a, cudaStream_t st);
 Error launch_grid_group(int n_px, const ImageArgs &a, cudaStream_t st);
+Error launch_wsum_copy(const ImageArgs &a, cudaStream_t st);
+
+// Pass 1 only (gridding + row transforms) for layers [l0, l0 + cnt) of a
+// group into scratch[l - l0][r][p] (natural order, FP32 complex).
+Error launch_rows_wave(int n_px, const ImageArgs &a, int l0, int cnt, cudaStream_t st);
+
+// Pass 2 as a dense real GEMM on the tensor cores (blink_dftgemm.cu).
+// mode: 1 BF16, 2 BF16 x3 (split-precision), 3 FP16, 4 FP16 x3.
+bool dftgemm_supported(int n_px, int r_alloc, int mode);
+size_t dftgemm_scratch_per_layer(int n_px, int r_alloc);
+Error launch_dftgemm_group(int n_px, int mode, const ImageArgs &a, cudaStream_t st);
+
 // Adjoint of the image path: resid (float [N][N] at out_off) -> dvis
 // (complex64 at vis_off).  Needs degrid_scratch_per_layer() bytes per layer.
 size_t degrid_scratch_per_layer(int n_px, int r_alloc);

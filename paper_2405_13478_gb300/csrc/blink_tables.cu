@@ -333,6 +333,21 @@ __global__ void k_expand_cells(const int2 *__restrict__ cells, const DevLayer *_
         out[int64_t(L.layer) * nb + b] = cells[int64_t(L.chan) * nb + b];
 }
 
+// Summed weight of every layer of a group (used where the image kernels do
+// not write it themselves).
+__global__ void k_wsum(const DevLayer *__restrict__ layers, int n_layers, const ChanInfo *__restrict__ chans,
+                       float *__restrict__ wsum) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < n_layers) wsum[layers[l].layer] = chans[layers[l].chan].wsum;
+}
+
+Error launch_wsum_copy(const ImageArgs &a, cudaStream_t st) {
+    if (!a.wsum_out || a.n_layers == 0) return Error{0, ""};
+    k_wsum<<<(a.n_layers + 255) / 256, 256, 0, st>>>(a.layers, a.n_layers, a.chans, a.wsum_out);
+    BLINK_CUDA_TRY(cudaGetLastError());
+    return Error{0, ""};
+}
+
 Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, const ChanGeom *geom,
                     ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_counts,
                     cudaStream_t st, unsigned char *sched) {
