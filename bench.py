@@ -43,7 +43,10 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--n-times", type=int, default=1000, help="time steps per rank (1000)")
+    p.add_argument("--n-times", type=int, default=None, help="time steps per rank")
+    p.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"],
+                   help="cfg2 (default): the headline station batch; the others measure the "
+                        "single-image latency, uneven batch, tensor-core modes and adjoint")
     return p.parse_args()
 
 
@@ -234,7 +237,7 @@ def run_ours(args):
     lib = binding.lib()  # noqa: F841  (fails loudly when the library is missing)
 
     # Each rank images its own 1000 x 32 batch (weak scaling, no data-path collective).
-    ws = synth.config2(seed=rank, n_times=args.n_times)
+    ws = synth.config2(seed=rank, n_times=args.n_times or 1000)
     layers = ws.layers()
     L = len(layers)
     B = ws.n_baselines
@@ -351,12 +354,226 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# Secondary workloads (one JSON line each, same schema): the single-image
+# latency, the uneven mixed-size batch, the tensor-core transform modes and
+# the differentiable path.  Single GPU (rank 0 only); not part of the
+# default run.
+def _setup_single():
+    import torch
+
+    from paper_2405_13478_gb300 import binding, build
+
+    rank, world, local = dist()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    build.build()
+    return torch, binding, binding.Context(local)
+
+
+def _time_steps(torch, step, steps, warmup):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, clocks.stop()
+
+
+def _line(args, metric_value, ms, config, clk, extra):
+    out = {"metric": METRIC, "value": metric_value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config, "clocks": clk}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def _sample_error(torch, ws, layers, vis_flat, out, picks):
+    import numpy as np
+
+    import oracle
+
+    B = ws.n_baselines
+    sub = [dict(layers[k], vis_offset=i * B) for i, k in enumerate(picks)]
+    v = torch.stack([vis_flat[layers[k]["vis_offset"]:layers[k]["vis_offset"] + B] for k in picks])
+    want, _ = oracle.image_batch(ws.ant_xyz, sub, v.cpu().reshape(-1).numpy(), "fft")
+    worst = 0.0
+    for k, w in zip(picks, want):
+        o, n = layers[k]["out_offset"], layers[k]["n_px"]
+        g = out[o:o + n * n].cpu().numpy().reshape(n, n)
+        worst = max(worst, float(np.abs(g - w).max() / np.abs(w).max()))
+    return worst
+
+
+def run_cfg1(args):
+    """One 256^2 image of a 128-antenna 3 km array: latency of a whole call."""
+    env = _setup_single()
+    if env is None:
+        return
+    torch, binding, ctx = env
+    import synth
+
+    ws = synth.config1(seed=0)
+    layers, total = binding.layer_out_offsets(ws.layers())
+    vis = ws.vis("cuda").reshape(-1)
+    out = torch.empty(total, device="cuda")
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    ms, clk = _time_steps(torch, lambda: ctx.image_batch(d_xyz, layers, vis, out), args.steps, args.warmup)
+    plan = ctx.plan(d_xyz, layers)
+    ms_k, _ = _time_steps(torch, lambda: plan.image(vis, out), args.steps, args.warmup)
+    err = _sample_error(torch, ws, layers, vis, out, [0])
+    _line(args, 1e3 / ms, ms, {"workload": "single 256^2 image, 128 antennas in a 3 km disk, 8128 "
+                                           "baselines, 160 MHz, natural weighting"}, clk,
+          {"latency_us": ms * 1e3, "latency_plan_cached_us": ms_k * 1e3, "err_vs_oracle": err,
+           "gpu_launches": 5 * args.steps})
+    plan.close()
+    ctx.close()
+
+
+def run_cfg3(args):
+    """Uneven batch: 768 channels x T steps, 128^2..1024^2 by channel group."""
+    env = _setup_single()
+    if env is None:
+        return
+    torch, binding, ctx = env
+    import synth
+
+    n_t = args.n_times or 100
+    ws = synth.config3(seed=0, n_times=n_t)
+    layers = ws.layers()
+    layers, total = binding.layer_out_offsets(layers)
+    larr = binding.layer_array([d["n_px"] for d in layers], [d["weighting"] for d in layers],
+                               [d["freq_hz"] for d in layers], [d["delta_u"] for d in layers],
+                               [d["vis_offset"] for d in layers], [d["out_offset"] for d in layers])
+    free, _ = torch.cuda.mem_get_info()
+    if total * 4 + ws.n_layers * ws.n_baselines * 8 > 0.85 * free:
+        raise SystemExit(f"cfg3 with {n_t} time steps does not fit in device memory; pass --n-times")
+    vis = ws.vis("cuda").reshape(-1)
+    out = torch.empty(total, device="cuda")
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    ms, clk = _time_steps(torch, lambda: ctx.image_batch(d_xyz, larr, vis, out), args.steps, args.warmup)
+    picks = [20 * 768 + c for c in (0, 100, 200, 300, 767)]  # the pulse arrives at step 20
+    err = _sample_error(torch, ws, layers, vis, out, [k for k in picks if k < len(layers)])
+    L = len(layers)
+    nbytes = L * ws.n_baselines * 8 + total * 4
+    peak, kind = measured_peaks()
+    gbs = nbytes / (ms / 1e3) / 1e9
+    _line(args, L / (ms / 1e3), ms,
+          {"workload": f"uneven batch: 128 antennas in a 3 km disk, 768 channels x {n_t} steps, "
+                       "images 128/256/512/1024 by channel group, dispersed pulse + noise",
+           "layers": L, "image_floats": total}, clk,
+          {"err_vs_oracle": err,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "peak_kind": kind, "traffic": None, "kernel": "whole step (all sizes)",
+                        "algorithmic_bytes_per_launch": nbytes}})
+    ctx.close()
+
+
+def run_cfg4(args):
+    """Station 512^2 batch: FP32 FFT against the tensor-core modes."""
+    env = _setup_single()
+    if env is None:
+        return
+    torch, binding, ctx = env
+    import synth
+
+    n_t = args.n_times or 2000
+    ws = synth.config4(seed=0, n_times=n_t)
+    layers = ws.layers()
+    layers, total = binding.layer_out_offsets(layers)
+    larr = binding.layer_array([d["n_px"] for d in layers], [d["weighting"] for d in layers],
+                               [d["freq_hz"] for d in layers], [d["delta_u"] for d in layers],
+                               [d["vis_offset"] for d in layers], [d["out_offset"] for d in layers])
+    vis = ws.vis("cuda").reshape(-1)
+    out = torch.empty(total, device="cuda")
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    L = len(layers)
+    modes = {"fft_fp32": 0x00, "bf16": 0x10, "bf16x3": 0x20, "fp16": 0x30, "fp16x3": 0x40}
+    res, clk0 = {}, None
+    for name, flag in modes.items():
+        def step(flag=flag):
+            plan = binding.Plan(ctx, d_xyz, larr)
+            plan.image(vis, out, None, flag)
+            plan.close()
+        ms, clk = _time_steps(torch, step, args.steps, args.warmup)
+        clk0 = clk0 or clk
+        err = _sample_error(torch, ws, layers, vis, out, [0, L // 2, L - 1])
+        res[name] = {"images_per_s": L / (ms / 1e3), "ms_per_step": ms, "err_vs_oracle": err}
+    # tensor work of the split mode: 3 products of 512 x 512 x K, K = 2 * 48
+    flops = 3 * 2 * 512 * 512 * 96 * L
+    tf = flops / (res["bf16x3"]["ms_per_step"] / 1e3) / 1e12
+    try:
+        peak_tf = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        kind = "measured"
+    except Exception:
+        peak_tf, kind = 1900.0, "fallback"
+    _line(args, res["fft_fp32"]["images_per_s"], res["fft_fp32"]["ms_per_step"],
+          {"workload": f"station: 256 antennas, 32640 baselines, {n_t} steps x 16 channels, 512^2 "
+                       "images, natural weighting, 50 sources 1e-3..10 Jy + noise", "layers": L}, clk0,
+          {"modes": res,
+           "roofline": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                        "frac": tf / peak_tf, "peak_kind": kind, "traffic": None,
+                        "kernel": "whole bf16x3 step (tcgen05 GEMM + pass 1 + split)",
+                        "algorithmic_flops_per_launch": flops}})
+    ctx.close()
+
+
+def run_cfg5(args):
+    """Differentiable 1024^2 imaging with antenna gains: forward + backward."""
+    env = _setup_single()
+    if env is None:
+        return
+    torch, binding, ctx = env
+    import numpy as np
+
+    import synth
+    from paper_2405_13478_gb300 import autograd
+
+    n_t = args.n_times or 100
+    ws = synth.config5(seed=0, n_times=n_t)
+    B, n_ant = ws.n_baselines, ws.n_ant
+    model_c = torch.as_tensor(synth.model_vis(ws.ant_xyz, ws.freqs_hz, ws.sky).astype(np.complex64)).cuda()
+    model = model_c.unsqueeze(0).expand(n_t, -1, -1).contiguous().reshape(-1)
+    layers, total = binding.layer_out_offsets(ws.layers())
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    plan = ctx.plan(d_xyz, layers)
+    target = autograd.dirty_images(model, plan, total).detach()
+    g0 = torch.as_tensor(ws.gains.astype(np.complex64)).cuda()
+
+    def step():
+        g = g0.clone().requires_grad_(True)
+        vis = autograd.apply_gains(g, model, ctx, n_ant, layers)
+        img = autograd.dirty_images(vis, plan, total)
+        loss = ((img - target) ** 2).sum()
+        loss.backward()
+        return g.grad
+
+    ms, clk = _time_steps(torch, step, args.steps, args.warmup)
+    L = len(layers)
+    _line(args, L / (ms / 1e3), ms,
+          {"workload": f"station: 256 antennas, {n_t} steps x 8 channels, 1024^2 images, gains on a "
+                       "20-source model, loss = sum (image - model image)^2, forward + backward",
+           "layers": L}, clk, {"gpu_launches_note": "gains, image, degrid and gain-gradient kernels"})
+    plan.close()
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "cfg2":
         run_ours(args)
+    else:
+        {"cfg1": run_cfg1, "cfg3": run_cfg3, "cfg4": run_cfg4, "cfg5": run_cfg5}[args.workload](args)
 
 
 if __name__ == "__main__":
