@@ -460,8 +460,9 @@ def run_cfg3(args):
     out = torch.empty(total, device="cuda")
     d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
     ms, clk = _time_steps(torch, lambda: ctx.image_batch(d_xyz, larr, vis, out), args.steps, args.warmup)
-    picks = [20 * 768 + c for c in (0, 100, 200, 300, 767)]  # the pulse arrives at step 20
-    err = _sample_error(torch, ws, layers, vis, out, [k for k in picks if k < len(layers)])
+    t_s = min(20, n_t - 1)  # the pulse reaches the top channel at step 20
+    picks = [t_s * 768 + c for c in (0, 100, 200, 300, 767)]
+    err = _sample_error(torch, ws, layers, vis, out, picks)
     L = len(layers)
     nbytes = L * ws.n_baselines * 8 + total * 4
     peak, kind = measured_peaks()

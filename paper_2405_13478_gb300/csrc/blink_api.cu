@@ -61,6 +61,7 @@ struct blink_plan {
     float2 *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     unsigned char *d_sched = nullptr;
+    unsigned char *d_csr = nullptr;  // row buckets per channel
     float2 *d_dscratch = nullptr;  // adjoint column-transform scratch (allocated on first use)
     size_t dscratch_bytes = 0;
     float2 *d_gscratch = nullptr;  // tensor-core transform scratch (allocated on first use)
@@ -71,7 +72,7 @@ struct blink_plan {
 
 namespace {
 
-constexpr size_t kScratchCap = size_t(256) << 20;  // bytes of row-transform scratch per plan
+constexpr size_t kScratchCap = size_t(48) << 20;  // bytes of row-transform scratch per plan (L2-sized waves)
 
 // Runs f with ctx->device current and restores the caller's device.
 struct DeviceGuard {
@@ -154,6 +155,8 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     if (p->d_block) cudaFreeAsync(p->d_block, st);
     if (p->d_scratch) cudaFreeAsync(p->d_scratch, st);
     if (p->d_sched) cudaFreeAsync(p->d_sched, st);
+    if (p->d_csr) cudaFreeAsync(p->d_csr, st);
+    p->d_csr = nullptr;
     if (p->d_dscratch) cudaFreeAsync(p->d_dscratch, st);
     if (p->d_gscratch) cudaFreeAsync(p->d_gscratch, st);
     p->d_gscratch = nullptr;
@@ -206,12 +209,15 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     p->infos.assign(size_t(p->n_chan), ChanInfo{});
     int64_t wgt_total = 0;
     int64_t sched_total = 0;
+    int64_t csr_total = 0;
     for (int c = 0; c < p->n_chan; ++c) {
         ChanInfo &ci = p->infos[size_t(c)];
         ci.n_px = p->geoms[size_t(c)].n_px;
         ci.weighting = p->geoms[size_t(c)].weighting;
         ci.code_off = int64_t(c) * p->nb;
         ci.sched_off = -1;
+        ci.csr_off = csr_total;
+        csr_total += blink::CsrLayout(ci.n_px, p->nb).bytes;
         const bool sched = ci.n_px <= kSchedMaxPx;
         if (sched) {
             const int q = int((p->nb + blink::kSchedMaxChunk - 1) / blink::kSchedMaxChunk);
@@ -296,8 +302,17 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         p->d_sched = static_cast<unsigned char *>(sb);
         TRY(cudaMemsetAsync(p->d_sched, 0, size_t(sched_total), st));
     }
+    if (csr_total) {
+        void *cb = nullptr;
+        e = cudaMallocFromPoolAsync(&cb, size_t(csr_total), ctx->pool, st);
+        if (e != cudaSuccess)
+            return fail(ctx, BLINK_ERR_WORKSPACE, std::string("row-bucket allocation: ") + cudaGetErrorString(e));
+        p->d_csr = static_cast<unsigned char *>(cb);
+        TRY(cudaMemsetAsync(p->d_csr, 0, size_t(csr_total), st));
+    }
     Error er = blink::launch_tables(d_ant_xyz, n_ant, p->nb, p->n_chan, p->d_geom, p->d_info,
-                                    p->d_codes, p->d_cells, p->d_wgt, p->any_uniform, st, p->d_sched);
+                                    p->d_codes, p->d_cells, p->d_wgt, p->any_uniform, st, p->d_sched,
+                                    p->d_csr);
     if (er.status) return fail(ctx, er);
     if (p->n_chan)
         TRY(cudaMemcpyAsync(p->infos.data(), p->d_info, sizeof(ChanInfo) * p->infos.size(),
@@ -354,6 +369,7 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.max_chunk = g.max_chunk;
     a.max_seg = g.max_seg;
     a.status = p->d_status;
+    a.csr = p->d_csr;
     return a;
 }
 

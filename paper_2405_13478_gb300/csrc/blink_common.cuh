@@ -41,6 +41,23 @@ struct ChanInfo {
     int64_t sched_off;   // byte offset of this channel's schedule block (-1 if none)
     int32_t max_seg;     // longest per-chunk stream segment (entries)
     int32_t pad2;
+    int64_t csr_off;     // row-bucketed entries of this channel (-1 if none), see CsrLayout
+};
+
+// Kept baselines bucketed by canonical row (large images): row_ptr[r] ..
+// row_ptr[r + 1] index ents = {baseline, packed code}; bucket N/2 holds the
+// dropped baselines.  Order inside a bucket is arbitrary.
+struct CsrLayout {
+    int64_t row_ptr, cursor, ents, bytes;
+    __host__ __device__ CsrLayout(int n_px, int64_t nb) {
+        auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
+        const int64_t nbk = n_px / 2 + 2;
+        int64_t o = 0;
+        row_ptr = o; o = up(o + 4 * nbk);
+        cursor = o; o = up(o + 4 * nbk);
+        ents = o; o = up(o + 8 * nb);
+        bytes = o;
+    }
 };
 
 // Register-accumulation gridding schedule (one block per channel).

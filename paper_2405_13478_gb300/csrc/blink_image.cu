@@ -31,21 +31,43 @@ namespace {
 
 constexpr int kNormalize = 1;
 
+// Layers per wave of the two-kernel paths: the row-transform scratch of a
+// wave stays within a budget that fits in L2 (so the second kernel reads it
+// from L2), within the scratch buffer and within a grid dimension.
+constexpr size_t kL2WaveBytes = size_t(48) << 20;
+inline int wave_size(int n_layers, size_t scratch_bytes, size_t per_layer) {
+    size_t w = std::min(scratch_bytes / per_layer, std::max<size_t>(1, kL2WaveBytes / per_layer));
+    w = std::min<size_t>(w, 65535);
+    return int(std::min<size_t>(size_t(n_layers), std::max<size_t>(w, 1)));
+}
+
 __device__ __forceinline__ float2 ld_stream(const float2 *p) { return __ldcs(p); }
+
+// Row layout of the two-kernel (large image) path in shared memory.  When
+// the four-step split has N2 a multiple of 32, consecutive frequencies of a
+// transformed row sit 32 elements apart (N2 (p mod N1) + p / N1) and would hit
+// one bank; one padding element per 32 (phys(q) = q + q / 32) spreads them.
+template <int N>
+struct RowLayout {
+    static constexpr bool pad = Plan<N>::N2 % 32 == 0;
+    static constexpr int S = pad ? N + N / 32 + 1 : N + 1;  // odd row stride
+    __device__ __forceinline__ static int phys(int q) { return pad ? q + (q >> 5) : q; }
+};
 
 // Weight the canonical cells and complete row 0.  G has row stride S.
 // Cells outside the canonical half are zero on entry.
-template <int N>
+template <int N, bool PAD = false>
 __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begin, int r_end,
                                                     const ChanInfo &ci, const float *wgt, int tid,
                                                     int nt) {
+    auto ph = [](int q) { return PAD ? RowLayout<N>::phys(q) : q; };
     constexpr int H = N / 2;
     const float *w = ci.weighting == 1 ? wgt + ci.wgt_off : nullptr;
     if (w) {
         const int first = max(r_begin, 1);
         for (int idx = tid; idx < (r_end - first) * N; idx += nt) {
             const int r = first + idx / N, c = idx % N;
-            float2 &g = G[(r - r_begin) * S + c];
+            float2 &g = G[(r - r_begin) * S + ph(c)];
             const float wv = w[r * N + c];
             g.x *= wv;
             g.y *= wv;
@@ -54,15 +76,15 @@ __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begi
     if (r_begin == 0) {
         for (int c = tid; c < H; c += nt) {
             const float wv = w ? w[c] : 1.f;
-            float2 g = G[c];
+            float2 g = G[ph(c)];
             if (c == 0) {
                 // origin: V and conj(V) of every baseline there
-                G[0] = make_float2(2.f * g.x * wv, 0.f);
+                G[ph(0)] = make_float2(2.f * g.x * wv, 0.f);
             } else {
                 g.x *= wv;
                 g.y *= wv;
-                G[c] = g;
-                G[N - c] = make_float2(g.x, -g.y);
+                G[ph(c)] = g;
+                G[ph(N - c)] = make_float2(g.x, -g.y);
             }
         }
     }
@@ -70,33 +92,34 @@ __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begi
 
 // Pass 1 on rows [0, nrows) of G (row stride S): N-point inverse DFT of each
 // row in place.  Output frequency p ends at position N2 * (p % N1) + p / N1.
-template <int N, int SIGN = +1>
+template <int N, int SIGN = +1, bool PAD = false>
 __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+    auto ph = [](int q) { return PAD ? RowLayout<N>::phys(q) : q; };
     // step A: N1-point transforms along stride N2, then twiddle W_N^(n2 k1)
     for (int t = tid; t < nrows * N2; t += nt) {
         const int r = t % nrows, n2 = t / nrows;
-        float2 *row = G + r * S + n2;
+        float2 *row = G + r * S;
         float2 x[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) x[n1] = row[N2 * n1];
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = row[ph(N2 * n1 + n2)];
         dft<N1, SIGN>(x);
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmulc(x[k1], root_rt<N, SIGN>(n2 * k1));
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) row[N2 * k1] = x[k1];
+        for (int k1 = 0; k1 < N1; ++k1) row[ph(N2 * k1 + n2)] = x[k1];
     }
     __syncthreads();
     // step B: N2-point transforms on contiguous runs, result kept in place
     for (int t = tid; t < nrows * N1; t += nt) {
         const int r = t % nrows, k1 = t / nrows;
-        float2 *run = G + r * S + N2 * k1;
+        float2 *run = G + r * S;
         float2 y[N2];
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) y[n2] = run[n2];
+        for (int n2 = 0; n2 < N2; ++n2) y[n2] = run[ph(N2 * k1 + n2)];
         dft<N2, SIGN>(y);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) run[k2] = y[k2];
+        for (int k2 = 0; k2 < N2; ++k2) run[ph(N2 * k1 + k2)] = y[k2];
     }
     __syncthreads();
 }
@@ -172,7 +195,7 @@ __device__ __forceinline__ void cols_step_b(const float2 *Z, int S, int j0, floa
 }
 
 // Grid the canonical rows [r0, r0 + nrows) of one layer into G (stride S).
-template <int NT>
+template <int NT, int N>
 __device__ __forceinline__ void grid_rows(float2 *G, int S, int r0, int nrows, const uint32_t *code,
                                           const float2 *vis, int64_t nb, int tid) {
     for (int64_t b = tid; b < nb; b += NT) {
@@ -182,7 +205,7 @@ __device__ __forceinline__ void grid_rows(float2 *G, int S, int r0, int nrows, c
         if (r < 0 || r >= nrows) continue;
         float2 v = ld_stream(vis + b);
         if (code_conj(cd)) v.y = -v.y;
-        float2 *cell = G + r * S + code_col(cd);
+        float2 *cell = G + r * S + RowLayout<N>::phys(int(code_col(cd)));
         atomicAdd(&cell->x, v.x);
         atomicAdd(&cell->y, v.y);
     }
@@ -551,7 +574,7 @@ size_t small_smem(int r_alloc) {
 template <int N>
 struct LargeCfg {
     static constexpr int NT = 256;
-    static constexpr int S = N + 1;
+    static constexpr int S = RowLayout<N>::S;
     static constexpr int RB = std::max(1, std::min(32, int(65536 / (S * sizeof(float2)))));
     static constexpr int P = std::max(1, std::min(32, NT / Plan<N>::N1));
 };
@@ -572,15 +595,32 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_rows(ImageArgs a, int l0) {
     const int tid = threadIdx.x;
     for (int i = tid; i < nrows * S; i += NT) sm[i] = make_float2(0.f, 0.f);
     __syncthreads();
-    grid_rows<NT>(sm, S, r0, nrows, a.codes + ci.code_off, a.vis + L.vis_off, a.nb, tid);
+    if (a.csr && ci.csr_off >= 0) {
+        // only this band's baselines, from the row buckets
+        const CsrLayout cl(N, a.nb);
+        const int32_t *ptr = reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr);
+        const uint2 *ents = reinterpret_cast<const uint2 *>(a.csr + ci.csr_off + cl.ents);
+        const float2 *vis = a.vis + L.vis_off;
+        const int e1 = ptr[r0 + nrows];
+        for (int e = ptr[r0] + tid; e < e1; e += NT) {
+            const uint2 en = __ldg(ents + e);
+            float2 v = __ldg(vis + en.x);
+            if (code_conj(en.y)) v.y = -v.y;
+            float2 *cell = sm + (int(code_row(en.y)) - r0) * S + RowLayout<N>::phys(int(code_col(en.y)));
+            atomicAdd(&cell->x, v.x);
+            atomicAdd(&cell->y, v.y);
+        }
+    } else {
+        grid_rows<NT, N>(sm, S, r0, nrows, a.codes + ci.code_off, a.vis + L.vis_off, a.nb, tid);
+    }
     __syncthreads();
-    weight_and_complete<N>(sm, S, r0, r0 + nrows, ci, a.wgt, tid, NT);
+    weight_and_complete<N, true>(sm, S, r0, r0 + nrows, ci, a.wgt, tid, NT);
     __syncthreads();
-    rows_fft<N>(sm, S, nrows, tid, NT);
+    rows_fft<N, +1, true>(sm, S, nrows, tid, NT);
     float2 *out = a.scratch + (int64_t(lw) * a.r_alloc + r0) * N;
     for (int i = tid; i < nrows * N; i += NT) {
         const int r = i / N, p = i % N;
-        out[int64_t(r) * N + p] = sm[r * S + pos_after_rows<N>(p)];
+        out[int64_t(r) * N + p] = sm[r * S + RowLayout<N>::phys(pos_after_rows<N>(p))];
     }
 }
 
@@ -782,11 +822,27 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_degrid_rows(ImageArgs a, fl
     if (r0 >= R) return;
     const int nrows = min(RB, R - r0);
     const float2 *in = a.scratch + (int64_t(lw) * a.r_alloc + r0) * N;
-    for (int i = tid; i < nrows * N; i += NT) sm[(i / N) * S + (i % N)] = in[i];
+    for (int i = tid; i < nrows * N; i += NT) sm[(i / N) * S + RowLayout<N>::phys(i % N)] = in[i];
     __syncthreads();
-    rows_fft<N, -1>(sm, S, nrows, tid, NT);
+    rows_fft<N, -1, true>(sm, S, nrows, tid, NT);
     const float *w = ci.weighting == 1 ? a.wgt + ci.wgt_off : nullptr;
     const float scale = 2.f * (((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f);
+    if (a.csr && ci.csr_off >= 0) {
+        const CsrLayout cl(N, a.nb);
+        const int32_t *ptr = reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr);
+        const uint2 *ents = reinterpret_cast<const uint2 *>(a.csr + ci.csr_off + cl.ents);
+        if (r0 == 0)  // dropped baselines (last bucket) get a zero gradient
+            for (int e = ptr[N / 2] + tid; e < ptr[N / 2 + 1]; e += NT) g[__ldg(ents + e).x] = make_float2(0.f, 0.f);
+        const int e1 = ptr[r0 + nrows];
+        for (int e = ptr[r0] + tid; e < e1; e += NT) {
+            const uint2 en = __ldg(ents + e);
+            const int r = int(code_row(en.y)), c = int(code_col(en.y));
+            const float2 h = sm[(r - r0) * S + RowLayout<N>::phys(pos_after_rows<N>(c))];
+            const float wv = scale * (w ? w[r * N + c] : 1.f);
+            g[en.x] = make_float2(wv * h.x, code_conj(en.y) ? -wv * h.y : wv * h.y);
+        }
+        return;
+    }
     for (int64_t b = tid; b < a.nb; b += NT) {
         const uint32_t cd = __ldg(code + b);
         if (cd == kCodeDropped) {
@@ -796,7 +852,7 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_degrid_rows(ImageArgs a, fl
         const int r = int(code_row(cd));
         if (r < r0 || r >= r0 + nrows) continue;
         const int c = int(code_col(cd));
-        const float2 h = sm[(r - r0) * S + pos_after_rows<N>(c)];
+        const float2 h = sm[(r - r0) * S + RowLayout<N>::phys(pos_after_rows<N>(c))];
         const float wv = scale * (w ? w[r * N + c] : 1.f);
         g[b] = make_float2(wv * h.x, code_conj(cd) ? -wv * h.y : wv * h.y);
     }
@@ -809,7 +865,7 @@ Error launch_degrid_n(const ImageArgs &a, const float *resid, float2 *dvis, cuda
     const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
     if (!a.scratch || a.scratch_bytes < per_layer)
         return Error{-5, "degrid scratch too small for image size " + std::to_string(N)};
-    const int wave = int(std::min<size_t>(size_t(a.n_layers), std::min<size_t>(65535, a.scratch_bytes / per_layer)));
+    const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer);
     const size_t smem_c = degrid_cols_smem<N>();
     const size_t smem_r = size_t(LargeCfg<N>::RB) * LargeCfg<N>::S * sizeof(float2);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_c)));
@@ -861,7 +917,7 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
     if (!a.scratch || a.scratch_bytes < per_layer)
         return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
-    const int wave = int(std::min<size_t>(size_t(a.n_layers), std::min<size_t>(65535, a.scratch_bytes / per_layer)));
+    const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer);
     const size_t smem_rows = size_t(C::RB) * C::S * sizeof(float2);
     const size_t smem_cols = size_t(C::P) * C::S * sizeof(float2);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,

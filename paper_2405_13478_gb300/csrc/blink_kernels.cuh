@@ -14,7 +14,7 @@ namespace blink {
 // zeroed, for channels imaged by the register-accumulation gridding.
 Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, const ChanGeom *geom,
                     ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_counts,
-                    cudaStream_t st, unsigned char *sched = nullptr);
+                    cudaStream_t st, unsigned char *sched = nullptr, unsigned char *csr = nullptr);
 Error launch_expand_cells(const int2 *cells, const DevLayer *layers, int n_layers, int64_t nb,
                           int2 *out, cudaStream_t st);
 
@@ -38,6 +38,7 @@ struct ImageArgs {
     int max_chunk;              // largest staging chunk of the group's channels
     int max_seg;                // longest per-chunk schedule segment (entries)
     int *status;                // device status word (bounded waits report BLINK_ERR_TIMEOUT)
+    const unsigned char *csr;   // row buckets of large-image channels (or null)
 };
 
 bool image_size_supported(int n_px);

@@ -42,7 +42,8 @@ __device__ __forceinline__ bool axis_cell(double w, double delta_u, int n_px, in
 __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t nb,
                         const ChanGeom *__restrict__ geom, ChanInfo *__restrict__ info,
                         uint32_t *__restrict__ codes, int2 *__restrict__ cells,
-                        int32_t *__restrict__ counts, unsigned char *__restrict__ sched) {
+                        int32_t *__restrict__ counts, unsigned char *__restrict__ sched,
+                        unsigned char *__restrict__ csr) {
     const int ch = blockIdx.y;
     const ChanGeom g = geom[ch];
     const ChanInfo ci0 = info[ch];
@@ -92,6 +93,11 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
         }
         codes[code_off + b] = code;
         if (cells) cells[ch * nb + b] = make_int2(ku, kv);
+        if (csr && ci0.csr_off >= 0) {  // bucket sizes (stored one slot up for the scan)
+            const CsrLayout cl(n, nb);
+            int32_t *cnt_r = reinterpret_cast<int32_t *>(csr + ci0.csr_off + cl.row_ptr);
+            atomicAdd(cnt_r + 1 + (code == kCodeDropped ? n / 2 : int(code_row(code))), 1);
+        }
     }
     // warp reductions, then one atomic per warp
     const unsigned full = 0xFFFFFFFFu;
@@ -322,6 +328,38 @@ __global__ void k_sched_sort(const ChanInfo *__restrict__ info, unsigned char *_
     }
 }
 
+// Row buckets, step 2 (one CTA per channel): inclusive scan of the bucket
+// sizes into row_ptr and a copy into the fill cursors.
+__global__ void k_csr_scan(const ChanInfo *__restrict__ info, unsigned char *__restrict__ csr, int64_t nb) {
+    const ChanInfo ci = info[blockIdx.x];
+    if (ci.csr_off < 0) return;
+    const CsrLayout cl(ci.n_px, nb);
+    int32_t *ptr = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.row_ptr);
+    int32_t *cur = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.cursor);
+    const int nbk = ci.n_px / 2 + 1;
+    if (threadIdx.x == 0) {
+        for (int r = 1; r <= nbk; ++r) ptr[r] += ptr[r - 1];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r <= nbk; r += blockDim.x) cur[r] = ptr[r];
+}
+
+// Row buckets, step 3: place every baseline in its bucket.
+__global__ void k_csr_fill(const ChanInfo *__restrict__ info, const uint32_t *__restrict__ codes,
+                           unsigned char *__restrict__ csr, int64_t nb) {
+    const ChanInfo ci = info[blockIdx.y];
+    if (ci.csr_off < 0) return;
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const CsrLayout cl(ci.n_px, nb);
+    int32_t *cur = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.cursor);
+    uint2 *ents = reinterpret_cast<uint2 *>(csr + ci.csr_off + cl.ents);
+    const uint32_t code = codes[ci.code_off + b];
+    const int bucket = code == kCodeDropped ? ci.n_px / 2 : int(code_row(code));
+    const int pos = atomicAdd(cur + bucket, 1);
+    ents[pos] = make_uint2(uint32_t(b), code);
+}
+
 // Per-layer copy of the per-channel signed cells (blink_cells).
 __global__ void k_expand_cells(const int2 *__restrict__ cells, const DevLayer *__restrict__ layers,
                                int n_layers, int64_t nb, int2 *__restrict__ out) {
@@ -350,12 +388,12 @@ Error launch_wsum_copy(const ImageArgs &a, cudaStream_t st) {
 
 Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, const ChanGeom *geom,
                     ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_counts,
-                    cudaStream_t st, unsigned char *sched) {
+                    cudaStream_t st, unsigned char *sched, unsigned char *csr) {
     if (n_chan == 0) return Error{0, ""};
     const int tpb = 256;
     dim3 grid(unsigned((nb + tpb - 1) / tpb), unsigned(n_chan));
     k_cells<<<grid, tpb, 0, st>>>(ant_xyz, n_ant, nb, geom, info, codes, cells,
-                                  any_counts ? reinterpret_cast<int32_t *>(wgt) : nullptr, sched);
+                                  any_counts ? reinterpret_cast<int32_t *>(wgt) : nullptr, sched, csr);
     BLINK_CUDA_TRY(cudaGetLastError());
     if (sched) {
         k_sched_slots<<<n_chan, 1024, 0, st>>>(info, wgt, sched, nb);
@@ -365,6 +403,12 @@ Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, co
         k_sched_entries<<<grid, tpb, 0, st>>>(info, codes, sched, nb);
         BLINK_CUDA_TRY(cudaGetLastError());
         k_sched_sort<<<dim3(32, unsigned(n_chan)), 256, 0, st>>>(info, sched, nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+    }
+    if (csr) {
+        k_csr_scan<<<n_chan, 32, 0, st>>>(info, csr, nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_csr_fill<<<grid, tpb, 0, st>>>(info, codes, csr, nb);
         BLINK_CUDA_TRY(cudaGetLastError());
     }
     k_finalize<<<n_chan, 512, 0, st>>>(info, wgt);
