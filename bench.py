@@ -464,6 +464,17 @@ def run_cfg3(args):
     picks = [t_s * 768 + c for c in (0, 100, 200, 300, 767)]
     err = _sample_error(torch, ws, layers, vis, out, picks)
     L = len(layers)
+    # the same batch through a reused plan: default kernels, autotuned kernels,
+    # and the autotuned launches replayed as one CUDA graph
+    plan = ctx.plan(d_xyz, larr)
+    ms_plan, _ = _time_steps(torch, lambda: plan.image(vis, out), args.steps, args.warmup)
+    plan.autotune(vis, out)
+    ms_tuned, _ = _time_steps(torch, lambda: plan.image(vis, out), args.steps, args.warmup)
+    plan.capture(vis, out)
+    ms_graph, _ = _time_steps(torch, lambda: plan.replay(), args.steps, args.warmup)
+    err_graph = _sample_error(torch, ws, layers, vis, out, picks)
+    tuning = plan.tuning()
+    plan.close()
     nbytes = L * ws.n_baselines * 8 + total * 4
     peak, kind = measured_peaks()
     gbs = nbytes / (ms / 1e3) / 1e9
@@ -472,6 +483,14 @@ def run_cfg3(args):
                        "images 128/256/512/1024 by channel group, dispersed pulse + noise",
            "layers": L, "image_floats": total}, clk,
           {"err_vs_oracle": err,
+           "variants": {"planned": {"images_per_s": L / (ms_plan / 1e3), "ms_per_step": ms_plan},
+                        "autotuned": {"images_per_s": L / (ms_tuned / 1e3), "ms_per_step": ms_tuned},
+                        "autotuned_graph": {"images_per_s": L / (ms_graph / 1e3), "ms_per_step": ms_graph,
+                                            "err_vs_oracle": err_graph,
+                                            "hbm_frac": nbytes / (ms_graph / 1e3) / 1e9 / peak},
+                        "tuning": [{"n_px": n, "path": ["default", "scheduled fused", "atomic fused",
+                                                        "two-kernel"][p_], "wave_bytes": w}
+                                   for n, p_, w in tuning]},
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                         "peak_kind": kind, "traffic": None, "kernel": "whole step (all sizes)",
                         "algorithmic_bytes_per_launch": nbytes}})

@@ -199,6 +199,32 @@ BLINK_API int blink_plan_image(blink_plan *plan, const float *d_vis, float *d_im
                      uint32_t flags, void *stream);
 BLINK_API void blink_plan_destroy(blink_plan *plan);
 
+/* Autotuner: for every image size of the plan, times the candidate kernel
+ * configurations on the given data (the atomic-free scheduled fused kernel,
+ * the shared-atomic fused kernel, the two-kernel path with wave budgets of
+ * 12, 24, 48 and 96 MB of row-transform scratch) and keeps the fastest for
+ * later calls.  Synchronises `stream`; writes images as a side effect.
+ * blink_plan_tuning reports the choice for size group `group` (groups are the
+ * plan's distinct sizes in increasing order; path 1 scheduled fused, 2
+ * atomic fused, 3 two-kernel). */
+BLINK_API int blink_plan_autotune(blink_plan *plan, const float *d_vis, float *d_images, void *stream);
+BLINK_API int blink_plan_tuning(const blink_plan *plan, int group, int *n_px, int *path, int64_t *wave_bytes);
+/* Sets a size group's kernel choice by hand (e.g. a tuning kept from an
+ * earlier run): path 0 default, 1 scheduled fused (sizes <= 256 whose
+ * schedule fits), 2 atomic fused (sizes <= 256), 3 two-kernel (any size);
+ * wave_bytes 0 = default L2-sized waves.  BLINK_ERR_INVALID for a path the
+ * group cannot take; the plan is unchanged then. */
+BLINK_API int blink_plan_set_tuning(blink_plan *plan, int group, int path, int64_t wave_bytes);
+
+/* CUDA graph of the plan's image launches: blink_plan_capture runs
+ * blink_plan_image once on `stream` (allocating whatever it needs), then
+ * records the same launches, bound to these pointers and flags, into a graph
+ * owned by the plan (replacing any earlier one).  blink_plan_replay launches
+ * the whole batch -- every image size -- as that one graph on `stream`. */
+BLINK_API int blink_plan_capture(blink_plan *plan, const float *d_vis, float *d_images, float *d_wsum,
+                                 uint32_t flags, void *stream);
+BLINK_API int blink_plan_replay(blink_plan *plan, void *stream);
+
 /* Waits for `stream` and returns the plan's device status word: BLINK_OK, or
  * BLINK_ERR_TIMEOUT if a bounded device-side wait of an earlier launch gave
  * up (that launch's output is incomplete).  Clears the word. */

@@ -27,7 +27,8 @@ EXPORTS = (
     "blink_last_error", "blink_cells", "blink_grid", "blink_image_batch", "blink_plan_create",
     "blink_plan_image", "blink_plan_destroy", "blink_plan_layer_info",
     "blink_image_batch_noalloc", "blink_image_batch_host", "blink_degrid", "blink_plan_degrid",
-    "blink_apply_gains", "blink_gain_grad", "blink_plan_check",
+    "blink_apply_gains", "blink_gain_grad", "blink_plan_check", "blink_plan_autotune",
+    "blink_plan_tuning", "blink_plan_set_tuning", "blink_plan_capture", "blink_plan_replay",
 )
 
 
@@ -89,6 +90,17 @@ def lib(path: str = LIB_PATH):
     L.blink_apply_gains.argtypes = [P, I, LP, I, P, P, P, P]
     L.blink_gain_grad.restype = I
     L.blink_gain_grad.argtypes = [P, I, LP, I, P, P, P, P, P]
+    L.blink_plan_autotune.restype = I
+    L.blink_plan_autotune.argtypes = [P, P, P, P]
+    L.blink_plan_tuning.restype = I
+    L.blink_plan_tuning.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int64)]
+    L.blink_plan_set_tuning.restype = I
+    L.blink_plan_set_tuning.argtypes = [P, I, I, ctypes.c_int64]
+    L.blink_plan_capture.restype = I
+    L.blink_plan_capture.argtypes = [P, P, P, P, ctypes.c_uint32, P]
+    L.blink_plan_replay.restype = I
+    L.blink_plan_replay.argtypes = [P, P]
     L.blink_plan_check.restype = I
     L.blink_plan_check.argtypes = [P, P]
     L.blink_plan_layer_info.restype = I
@@ -291,6 +303,39 @@ class Plan:
         _check_dev(dimage, dvis_out)
         self.ctx._raise(self.ctx._lib.blink_plan_degrid(self.handle, _ptr(dimage), _ptr(dvis_out),
                                                         int(flags), _stream(stream)))
+
+    def autotune(self, vis, images_out, stream=None):
+        """Time the candidate kernel configurations per image size, keep the fastest."""
+        _check_dev(vis, images_out)
+        self.ctx._raise(self.ctx._lib.blink_plan_autotune(self.handle, _ptr(vis), _ptr(images_out),
+                                                          _stream(stream)))
+
+    def tuning(self):
+        """[(n_px, path, wave_bytes)] chosen per size group."""
+        out, g = [], 0
+        while True:
+            n, pth, wb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+            if self.ctx._lib.blink_plan_tuning(self.handle, g, ctypes.byref(n), ctypes.byref(pth),
+                                               ctypes.byref(wb)) != OK:
+                return out
+            out.append((n.value, pth.value, wb.value))
+            g += 1
+
+    def set_tuning(self, group, path, wave_bytes=0):
+        """Force size group `group` onto kernel path 0-3 (see blink_plan_set_tuning)."""
+        self.ctx._raise(self.ctx._lib.blink_plan_set_tuning(self.handle, int(group), int(path),
+                                                            int(wave_bytes)))
+
+    def capture(self, vis, images_out, wsum_out=None, flags=0, stream=None):
+        """Record the batch's launches into a CUDA graph bound to these buffers."""
+        _check_dev(vis, images_out, wsum_out)
+        self.ctx._raise(self.ctx._lib.blink_plan_capture(self.handle, _ptr(vis), _ptr(images_out),
+                                                         _ptr(wsum_out), int(flags),
+                                                         _stream(stream)))
+
+    def replay(self, stream=None):
+        """Launch the captured graph (the whole batch, every image size)."""
+        self.ctx._raise(self.ctx._lib.blink_plan_replay(self.handle, _stream(stream)))
 
     def check(self, stream=None):
         """Synchronise and raise if a bounded device-side wait timed out."""

@@ -48,6 +48,8 @@ struct blink_plan {
         int sched_ok;   // every channel of the group has a gridding schedule
         int max_chunk;  // largest staging chunk among those channels
         int max_seg;    // longest per-chunk schedule segment among them
+        int force_path = 0;       // autotuned kernel choice (0 = default)
+        size_t wave_budget = 0;   // autotuned wave size of the two-kernel path
     };
     std::vector<Group> groups;
     // device memory (one pool allocation for the tables, one for scratch)
@@ -68,6 +70,8 @@ struct blink_plan {
     size_t gscratch_bytes = 0;
     int *d_status = nullptr;       // device status word (in the table block)
     cudaStream_t last_stream = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    cudaGraphExec_t graph = nullptr;     // captured image launches (blink_plan_capture)
 };
 
 namespace {
@@ -251,7 +255,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
                                  p->layer_chan[size_t(l)], l};
         p->layer_out.push_back(h_layers[l].out_offset);
         if (p->groups.empty() || p->groups.back().n_px != h_layers[l].n_px)
-            p->groups.push_back(blink_plan::Group{h_layers[l].n_px, k, 0, 1, 0, 0, 0});
+            p->groups.push_back(blink_plan::Group{h_layers[l].n_px, k, 0, 1, 0, 0, 0, 0, 0});
         p->groups.back().count++;
     }
     // one device block for every table
@@ -370,6 +374,8 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.max_seg = g.max_seg;
     a.status = p->d_status;
     a.csr = p->d_csr;
+    a.force_path = g.force_path;
+    a.wave_budget = g.wave_budget;
     return a;
 }
 
@@ -438,6 +444,26 @@ int blink_plan_create(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const 
     return BLINK_OK;
 }
 
+// Row-transform scratch for every group that may take the two-kernel path
+// (needed before autotuning or graph capture, which must not allocate).
+static int ensure_rows_scratch(blink_plan *p, cudaStream_t st) {
+    size_t need = 0;
+    for (const auto &grp : p->groups) {
+        const size_t per = blink::image_rows_scratch_per_layer(grp.n_px, grp.r_alloc);
+        need = std::max(need, std::max(per, std::min(per * size_t(grp.count), kScratchCap)));
+    }
+    if (need <= p->scratch_bytes) return BLINK_OK;
+    if (p->d_scratch) cudaFreeAsync(p->d_scratch, st);
+    p->d_scratch = nullptr;
+    p->scratch_bytes = 0;
+    void *ptr = nullptr;
+    const cudaError_t e = cudaMallocFromPoolAsync(&ptr, need, p->ctx->pool, st);
+    if (e != cudaSuccess) return fail(p->ctx, BLINK_ERR_WORKSPACE, "scratch allocation failed");
+    p->d_scratch = static_cast<float2 *>(ptr);
+    p->scratch_bytes = need;
+    return BLINK_OK;
+}
+
 int blink_plan_image(blink_plan *p, const float *d_vis, float *d_images, float *d_wsum, uint32_t flags,
                      void *stream) {
     if (!p) return BLINK_ERR_INVALID;
@@ -477,6 +503,12 @@ int blink_plan_image(blink_plan *p, const float *d_vis, float *d_images, float *
             p->gscratch_bytes = need;
         }
     }
+    for (const auto &grp : p->groups)
+        if (grp.force_path == 3) {
+            const int rc = ensure_rows_scratch(p, st);
+            if (rc) return rc;
+            break;
+        }
     for (const auto &grp : p->groups) {
         blink::ImageArgs a = group_args(p, grp, d_vis, d_images, d_wsum, flags & BLINK_NORMALIZE);
         Error e;
@@ -509,9 +541,138 @@ void blink_plan_destroy(blink_plan *p) {
     if (!p) return;
     {
         DeviceGuard g(p->ctx->device);
+        if (p->graph) cudaGraphExecDestroy(p->graph);
         free_plan_memory(p, p->last_stream);
+        if (p->cap_stream) {
+            cudaStreamSynchronize(p->last_stream);
+            cudaStreamDestroy(p->cap_stream);
+        }
     }
     delete p;
+}
+
+int blink_plan_autotune(blink_plan *p, const float *d_vis, float *d_images, void *stream) {
+    if (!p) return BLINK_ERR_INVALID;
+    blink_ctx *ctx = p->ctx;
+    if (p->n_layers && (!d_vis || !d_images)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    p->last_stream = st;
+    int rc = ensure_rows_scratch(p, st);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(ctx, BLINK_ERR_CUDA, "event creation failed");
+    struct Cand {
+        int path;
+        size_t budget;
+    };
+    for (auto &grp : p->groups) {
+        std::vector<Cand> cands;
+        if (blink::image_small_path(grp.n_px, grp.r_alloc)) {
+            if (grp.sched_ok) cands.push_back({1, 0});
+            cands.push_back({2, 0});
+        }
+        for (size_t mb : {12, 24, 48, 96}) cands.push_back({3, mb << 20});
+        float best = 1e30f;
+        Cand pick = cands.front();
+        for (const Cand &c : cands) {
+            grp.force_path = c.path;
+            grp.wave_budget = c.budget;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && !rc; ++rep) {  // first run warms up
+                blink::ImageArgs a = group_args(p, grp, d_vis, d_images, nullptr, 0);
+                cudaEventRecord(e0, st);
+                Error e = blink::launch_image_group(grp.n_px, a, st);
+                cudaEventRecord(e1, st);
+                if (e.status) rc = fail(ctx, e);
+                else if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ctx, BLINK_ERR_CUDA, "autotune timing failed");
+                else cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                pick = c;
+            }
+        }
+        grp.force_path = pick.path;
+        grp.wave_budget = pick.budget;
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) ctx->err.clear();
+    return rc;
+}
+
+int blink_plan_tuning(const blink_plan *p, int group, int *n_px, int *path, int64_t *wave_bytes) {
+    if (!p || group < 0 || group >= int(p->groups.size())) return BLINK_ERR_INVALID;
+    const auto &grp = p->groups[size_t(group)];
+    if (n_px) *n_px = grp.n_px;
+    if (path) *path = grp.force_path;
+    if (wave_bytes) *wave_bytes = int64_t(grp.wave_budget);
+    return BLINK_OK;
+}
+
+int blink_plan_set_tuning(blink_plan *p, int group, int path, int64_t wave_bytes) {
+    if (!p) return BLINK_ERR_INVALID;
+    if (group < 0 || group >= int(p->groups.size()))
+        return fail(p->ctx, BLINK_ERR_INVALID, "size group out of range");
+    auto &grp = p->groups[size_t(group)];
+    const bool small = blink::image_small_path(grp.n_px, grp.r_alloc);
+    if (path < 0 || path > 3 || wave_bytes < 0 || (path == 1 && !(small && grp.sched_ok)) ||
+        (path == 2 && !small))
+        return fail(p->ctx, BLINK_ERR_INVALID, "kernel path not available for this size group");
+    grp.force_path = path;
+    grp.wave_budget = size_t(wave_bytes);
+    return BLINK_OK;
+}
+
+int blink_plan_capture(blink_plan *p, const float *d_vis, float *d_images, float *d_wsum, uint32_t flags,
+                       void *stream) {
+    if (!p) return BLINK_ERR_INVALID;
+    blink_ctx *ctx = p->ctx;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // every allocation happens before capture
+    int rc = ensure_rows_scratch(p, st);
+    if (rc) return rc;
+    rc = blink_plan_image(p, d_vis, d_images, d_wsum, flags, stream);  // also allocates lazily
+    if (rc) return rc;
+    if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ctx, BLINK_ERR_CUDA, "capture stream creation failed");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(ctx, BLINK_ERR_CUDA, "synchronise failed");
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(ctx, BLINK_ERR_CUDA, "begin capture failed");
+    const cudaStream_t keep = p->last_stream;
+    rc = blink_plan_image(p, d_vis, d_images, d_wsum, flags, p->cap_stream);
+    p->last_stream = keep;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ec != cudaSuccess || !graph) return fail(ctx, BLINK_ERR_CUDA, "end capture failed");
+    const cudaError_t ei = cudaGraphInstantiate(&p->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(ctx, BLINK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    ctx->err.clear();
+    return BLINK_OK;
+}
+
+int blink_plan_replay(blink_plan *p, void *stream) {
+    if (!p) return BLINK_ERR_INVALID;
+    if (!p->graph) return fail(p->ctx, BLINK_ERR_INVALID, "no captured graph (call blink_plan_capture)");
+    DeviceGuard g(p->ctx->device);
+    const cudaError_t e = cudaGraphLaunch(p->graph, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(p->ctx, BLINK_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    p->last_stream = static_cast<cudaStream_t>(stream);
+    return BLINK_OK;
 }
 
 int blink_plan_degrid(blink_plan *p, const float *d_dimage, float *d_dvis, uint32_t flags, void *stream) {

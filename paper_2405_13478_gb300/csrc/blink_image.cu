@@ -35,8 +35,9 @@ constexpr int kNormalize = 1;
 // wave stays within a budget that fits in L2 (so the second kernel reads it
 // from L2), within the scratch buffer and within a grid dimension.
 constexpr size_t kL2WaveBytes = size_t(48) << 20;
-inline int wave_size(int n_layers, size_t scratch_bytes, size_t per_layer) {
-    size_t w = std::min(scratch_bytes / per_layer, std::max<size_t>(1, kL2WaveBytes / per_layer));
+inline int wave_size(int n_layers, size_t scratch_bytes, size_t per_layer, size_t budget = 0) {
+    const size_t b = budget ? budget : kL2WaveBytes;
+    size_t w = std::min(scratch_bytes / per_layer, std::max<size_t>(1, b / per_layer));
     w = std::min<size_t>(w, 65535);
     return int(std::min<size_t>(size_t(n_layers), std::max<size_t>(w, 1)));
 }
@@ -897,9 +898,9 @@ template <int N>
 Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     if (a.n_layers == 0) return Error{0, ""};
     if constexpr (N <= 256) {
-      if (use_small<N>(a.r_alloc)) {
+      if (a.force_path != 3 && use_small<N>(a.r_alloc)) {
         size_t smem = small_smem<N>(a.r_alloc);
-        const bool sched = a.sched && a.sched_ok;
+        const bool sched = a.sched && a.sched_ok && a.force_path != 2;
         if (sched) smem = std::max(smem, size_t(StageLayout(a.max_chunk, a.max_seg, kSchedSlots).bytes));
         auto kern = sched ? k_image_sched<N> : k_image_small<N>;
         BLINK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -917,7 +918,7 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
     if (!a.scratch || a.scratch_bytes < per_layer)
         return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
-    const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer);
+    const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer, a.wave_budget);
     const size_t smem_rows = size_t(C::RB) * C::S * sizeof(float2);
     const size_t smem_cols = size_t(C::P) * C::S * sizeof(float2);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -957,6 +958,15 @@ int supported_sizes(int32_t *out, int cap) {
 #undef X
     return k;
 }
+
+bool image_small_path(int n_px, int r_alloc) {
+#define X(N_) if (n_px == N_) return use_small<N_>(r_alloc);
+    BLINK_FOR_EACH_SIZE(X)
+#undef X
+    return false;
+}
+
+size_t image_rows_scratch_per_layer(int n_px, int r_alloc) { return size_t(r_alloc) * n_px * sizeof(float2); }
 
 size_t image_scratch_per_layer(int n_px, int r_alloc) {
 #define X(N_) if (n_px == N_) return scratch_per_layer_n<N_>(r_alloc);

@@ -39,6 +39,8 @@ struct ImageArgs {
     int max_seg;                // longest per-chunk schedule segment (entries)
     int *status;                // device status word (bounded waits report BLINK_ERR_TIMEOUT)
     const unsigned char *csr;   // row buckets of large-image channels (or null)
+    int force_path;             // 0 default, 1 scheduled fused, 2 atomic fused, 3 two-kernel
+    size_t wave_budget;         // row-transform scratch per wave (0 = default, L2-sized)
 };
 
 bool image_size_supported(int n_px);
@@ -46,6 +48,10 @@ int supported_sizes(int32_t *out, int cap);
 // Bytes of row-transform scratch one layer of size n_px with r_alloc rows needs
 // on the large-image path (0 if the fused single-CTA path takes the group).
 size_t image_scratch_per_layer(int n_px, int r_alloc);
+// Whether the fused single-CTA kernels can take a group, and the scratch a
+// layer needs on the two-kernel path regardless of that choice.
+bool image_small_path(int n_px, int r_alloc);
+size_t image_rows_scratch_per_layer(int n_px, int r_alloc);
 Error launch_image_group(int n_px, const ImageArgs &a, cudaStream_t st);
 Error launch_grid_group(int n_px, const ImageArgs &a, cudaStream_t st);
 Error launch_wsum_copy(const ImageArgs &a, cudaStream_t st);
