@@ -88,6 +88,11 @@ def _load():
         lib.orc_gain_grad.restype = None
         lib.orc_gain_grad.argtypes = [ctypes.c_int, D, D, D, D]
         lib.orc_image_batch.restype = ctypes.c_int
+        lib.orc_apply_gains.argtypes = [ctypes.c_int, D, F, D]
+        lib.orc_apply_gains.restype = None
+        lib.orc_image_batch_ex.argtypes = [D, ctypes.c_int, ctypes.c_int, I32, I32, D, D, I64, I64,
+                                           F, D, ctypes.c_int64, D, D, D, ctypes.c_int,
+                                           ctypes.c_int]
         lib.orc_image_batch.argtypes = [D, ctypes.c_int, ctypes.c_int, I32, I32, D, D, I64, I64,
                                         F, D, D, ctypes.c_int, ctypes.c_int]
         _lib = lib
@@ -175,12 +180,26 @@ def fft1d(x: np.ndarray, sign: int) -> np.ndarray:
     return out
 
 
-def image_batch(ant_xyz, layers, vis, mode: str = "fft", n_threads: int = 0):
+def apply_gains(n_ant: int, gains, vis):
+    """V'_ij = g_i conj(g_j) V_ij for the pairs (i < j), in complex128."""
+    g = np.ascontiguousarray(gains, np.complex128)
+    v = np.ascontiguousarray(vis, np.complex64).reshape(-1)
+    out = np.empty(v.size, np.complex128)
+    _load().orc_apply_gains(int(n_ant), _p(g.view(np.float64), ctypes.c_double),
+                            _p(v.view(np.float32), ctypes.c_float),
+                            _p(out.view(np.float64), ctypes.c_double))
+    return out
+
+
+def image_batch(ant_xyz, layers, vis, mode: str = "fft", n_threads: int = 0, gains=None,
+                gain_stride: int = 0, ref=None):
     """Whole path over many layers.
 
     ``layers`` is a sequence of dicts with keys n_px, weighting, freq_hz,
-    delta_u, vis_offset (complex elements into ``vis``).  Returns
-    (list of float64 images, wsum array).
+    delta_u, vis_offset (complex elements into ``vis``).  Optional: ``gains``
+    (complex, layer l uses the row starting at l * gain_stride) applied to the
+    visibilities, and ``ref`` (flat, packed like the returned images)
+    subtracted from the images.  Returns (list of float64 images, wsum array).
     """
     xyz = np.ascontiguousarray(ant_xyz, np.float64)
     vis = np.ascontiguousarray(vis, np.complex64).reshape(-1)
@@ -194,12 +213,28 @@ def image_batch(ant_xyz, layers, vis, mode: str = "fft", n_threads: int = 0):
     oo = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
     out = np.empty(int(sizes.sum()), np.float64)
     ws = np.zeros(L, np.float64)
-    st = _load().orc_image_batch(
-        _p(xyz, ctypes.c_double), xyz.shape[0], L, _p(npx, ctypes.c_int32),
-        _p(wt, ctypes.c_int32), _p(fr, ctypes.c_double), _p(du, ctypes.c_double),
-        _p(vo, ctypes.c_int64), _p(oo, ctypes.c_int64), _p(vis.view(np.float32), ctypes.c_float),
-        _p(out, ctypes.c_double), _p(ws, ctypes.c_double), 1 if mode == "direct" else 0,
-        int(n_threads))
+    if gains is None and ref is None:
+        st = _load().orc_image_batch(
+            _p(xyz, ctypes.c_double), xyz.shape[0], L, _p(npx, ctypes.c_int32),
+            _p(wt, ctypes.c_int32), _p(fr, ctypes.c_double), _p(du, ctypes.c_double),
+            _p(vo, ctypes.c_int64), _p(oo, ctypes.c_int64),
+            _p(vis.view(np.float32), ctypes.c_float), _p(out, ctypes.c_double),
+            _p(ws, ctypes.c_double), 1 if mode == "direct" else 0, int(n_threads))
+    else:
+        g = None if gains is None else np.ascontiguousarray(gains, np.complex128).reshape(-1)
+        r = None if ref is None else np.ascontiguousarray(ref, np.float64).reshape(-1)
+        if r is not None and r.size < out.size:
+            raise ValueError("reference images smaller than the output")
+        if g is not None and g.size < (L - 1) * int(gain_stride) + xyz.shape[0]:
+            raise ValueError("gain rows smaller than the layers need")
+        st = _load().orc_image_batch_ex(
+            _p(xyz, ctypes.c_double), xyz.shape[0], L, _p(npx, ctypes.c_int32),
+            _p(wt, ctypes.c_int32), _p(fr, ctypes.c_double), _p(du, ctypes.c_double),
+            _p(vo, ctypes.c_int64), _p(oo, ctypes.c_int64),
+            _p(vis.view(np.float32), ctypes.c_float),
+            None if g is None else _p(g.view(np.float64), ctypes.c_double), int(gain_stride),
+            None if r is None else _p(r, ctypes.c_double), _p(out, ctypes.c_double),
+            _p(ws, ctypes.c_double), 1 if mode == "direct" else 0, int(n_threads))
     if st != 0:
         raise ValueError(f"orc_image_batch failed ({st})")
     imgs = [out[oo[i]:oo[i] + sizes[i]].reshape(npx[i], npx[i]) for i in range(L)]

@@ -473,16 +473,61 @@ void orc_gain_grad(int n_ant, const double *gamma_v, const double *gains, const 
     }
 }
 
+/* ----------------------------------- calibration gains (Sec. 4.2, step ii) */
+/* Antenna-based complex gains applied after correlation: the visibility of
+ * the pair (i < j) becomes g_i conj(g_j) V_ij.  gains: [n_ant] complex128;
+ * vis: [B] complex64; out: [B] complex128 (re, im interleaved).  To remove a
+ * calibration solution pass its reciprocal gains. */
+void orc_apply_gains(int n_ant, const double *gains, const float *vis, double *out) {
+    int64_t b = 0;
+    for (int i = 0; i < n_ant; ++i) {
+        const double ar = gains[2 * i], ai = gains[2 * i + 1];
+        for (int j = i + 1; j < n_ant; ++j, ++b) {
+            const double cr = gains[2 * j], ci = gains[2 * j + 1];
+            /* g_i conj(g_j) = (ar + i ai)(cr - i ci) */
+            const double pr = ar * cr + ai * ci;
+            const double pi = ai * cr - ar * ci;
+            const double vr = vis[2 * b], vi = vis[2 * b + 1];
+            out[2 * b] = pr * vr - pi * vi;
+            out[2 * b + 1] = pr * vi + pi * vr;
+        }
+    }
+}
+
 /* --------------------------------------------------- whole path, batched */
 /* One layer = one (time step, channel) image (Sec. 5.2.4).  Layer l reads
  * B = n_ant(n_ant-1)/2 complex64 visibilities at vis + 2*vis_off[l] and writes
  * n_px[l]^2 doubles at images + out_off[l]; wsum[l] gets the summed weight.
  * mode 0: FFT route, mode 1: direct route.  n_threads <= 0: all cores.
  * Returns 0 or the first non-zero layer status. */
+int orc_image_batch_ex(const double *ant_xyz, int n_ant, int n_layers, const int32_t *n_px,
+                       const int32_t *weighting, const double *freq_hz, const double *delta_u,
+                       const int64_t *vis_off, const int64_t *out_off, const float *vis,
+                       const double *gains, int64_t gain_stride, const double *ref,
+                       double *images, double *wsum, int mode, int n_threads);
+
 int orc_image_batch(const double *ant_xyz, int n_ant, int n_layers, const int32_t *n_px,
                     const int32_t *weighting, const double *freq_hz, const double *delta_u,
                     const int64_t *vis_off, const int64_t *out_off, const float *vis,
                     double *images, double *wsum, int mode, int n_threads) {
+    return orc_image_batch_ex(ant_xyz, n_ant, n_layers, n_px, weighting, freq_hz, delta_u, vis_off,
+                              out_off, vis, NULL, 0, NULL, images, wsum, mode, n_threads);
+}
+
+/* The same with the two optional steps around the imager that transient
+ * searches use:
+ *   gains (may be NULL): layer l's visibilities are first multiplied by
+ *     g_i conj(g_j) with the gain row gains + 2 * l * gain_stride (complex128,
+ *     [n_ant]); gain_stride 0 = one row for every layer (Sec. 4.2, step ii);
+ *   ref (may be NULL): a reference image is subtracted from each dirty image,
+ *     image = dirty - ref, ref read at the layer's out_off like the output
+ *     (Sec. 2 and Sec. 4.3 after Eq. 6: side-lobes of a transient search are
+ *     removed by subtracting a reference image of the same field). */
+int orc_image_batch_ex(const double *ant_xyz, int n_ant, int n_layers, const int32_t *n_px,
+                       const int32_t *weighting, const double *freq_hz, const double *delta_u,
+                       const int64_t *vis_off, const int64_t *out_off, const float *vis,
+                       const double *gains, int64_t gain_stride, const double *ref,
+                       double *images, double *wsum, int mode, int n_threads) {
     const int64_t nb = orc_n_baselines(n_ant);
     int status = 0;
 #ifdef _OPENMP
@@ -496,18 +541,29 @@ int orc_image_batch(const double *ant_xyz, int n_ant, int n_layers, const int32_
         int32_t *ku = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
         int32_t *kv = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
         double *g = (double *)malloc(sizeof(double) * 2 * (size_t)n * n);
-        int st = (!u || !v || !ku || !kv || !g) ? -1 : 0;
+        double *vg = gains ? (double *)malloc(sizeof(double) * 2 * (size_t)nb) : NULL;
+        int st = (!u || !v || !ku || !kv || !g || (gains && !vg)) ? -1 : 0;
         if (!st) {
             orc_uv(ant_xyz, n_ant, freq_hz[l], u, v);
             orc_cells(u, v, nb, delta_u[l], n, ku, kv);
-            st = orc_grid(ku, kv, vis + 2 * vis_off[l], nb, n, weighting[l], g, NULL, &wsum[l]);
+            if (gains) {
+                orc_apply_gains(n_ant, gains + 2 * gain_stride * l, vis + 2 * vis_off[l], vg);
+                st = orc_grid_c128(ku, kv, vg, nb, n, weighting[l], g, NULL, &wsum[l]);
+            } else {
+                st = orc_grid(ku, kv, vis + 2 * vis_off[l], nb, n, weighting[l], g, NULL, &wsum[l]);
+            }
         }
         if (!st) {
             double mi = 0.0;
             st = mode == 1 ? orc_image_direct(g, n, images + out_off[l], &mi)
                            : orc_image_fft(g, n, images + out_off[l], &mi);
         }
-        free(u); free(v); free(ku); free(kv); free(g);
+        if (!st && ref) {
+            double *img = images + out_off[l];
+            const double *rf = ref + out_off[l];
+            for (int64_t p = 0; p < (int64_t)n * n; ++p) img[p] -= rf[p];
+        }
+        free(u); free(v); free(ku); free(kv); free(g); free(vg);
         if (st) {
 #ifdef _OPENMP
 #pragma omp critical

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_adjoint as adj
+from tests import test_oracle_epilogue as epi
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "blink_oracle.c")
@@ -60,6 +61,14 @@ MUTANTS = {
     # gain chain rule without the conjugate on the second antenna's term
     "gain_grad_conjugate": ("gamma_g[2 * j + 1] += gr * ui - gi * ur;",
                             "gamma_g[2 * j + 1] += gr * ui + gi * ur;"),
+    # gain product with the conjugate on the first antenna: conj(g_i) g_j
+    "gain_conjugate_swapped": ("const double pi = ai * cr - ar * ci;", "const double pi = ar * ci - ai * cr;"),
+    # reference image added instead of subtracted
+    "reference_added": ("for (int64_t p = 0; p < (int64_t)n * n; ++p) img[p] -= rf[p];",
+                        "for (int64_t p = 0; p < (int64_t)n * n; ++p) img[p] += rf[p];"),
+    # every layer reads the first gain row
+    "gain_stride_ignored": ("orc_apply_gains(n_ant, gains + 2 * gain_stride * l,",
+                            "orc_apply_gains(n_ant, gains,"),
 }
 
 PINS = [
@@ -78,6 +87,10 @@ PINS = [
     lambda: adj.test_adjoint_dot_product_identity(0, "fft"),
     lambda: adj.test_visibility_gradient_matches_finite_differences(1),
     adj.test_gain_gradient_matches_finite_differences,
+    lambda: epi.test_phase_ramp_gains_move_a_source(0),
+    lambda: epi.test_gains_match_bruteforce_direct_sum(1),
+    epi.test_gain_rows_follow_the_stride,
+    epi.test_reference_subtraction_is_dirty_minus_reference,
 ]
 
 
@@ -103,7 +116,8 @@ def test_pins_catch_mutant(name, workdir, monkeypatch):
     mlib = ctypes.CDLL(so_path)
     for fn in ("orc_version", "orc_n_baselines", "orc_uv", "orc_cells", "orc_grid",
                "orc_image_direct", "orc_image_fft", "orc_fft1d", "orc_image_batch",
-               "orc_grid_c128", "orc_degrid_direct", "orc_degrid_fft", "orc_gain_grad"):
+               "orc_grid_c128", "orc_degrid_direct", "orc_degrid_fft", "orc_gain_grad",
+               "orc_apply_gains", "orc_image_batch_ex"):
         getattr(mlib, fn).restype = getattr(real, fn).restype
         getattr(mlib, fn).argtypes = getattr(real, fn).argtypes
     monkeypatch.setattr(oracle, "_lib", mlib)
