@@ -91,8 +91,8 @@ def _load():
         lib.orc_apply_gains.argtypes = [ctypes.c_int, D, F, D]
         lib.orc_apply_gains.restype = None
         lib.orc_image_batch_ex.argtypes = [D, ctypes.c_int, ctypes.c_int, I32, I32, D, D, I64, I64,
-                                           F, D, ctypes.c_int64, D, D, D, ctypes.c_int,
-                                           ctypes.c_int]
+                                           F, D, ctypes.c_int64, ctypes.c_int64, D, D, D,
+                                           ctypes.c_int, ctypes.c_int]
         lib.orc_image_batch.argtypes = [D, ctypes.c_int, ctypes.c_int, I32, I32, D, D, I64, I64,
                                         F, D, D, ctypes.c_int, ctypes.c_int]
         _lib = lib
@@ -192,13 +192,13 @@ def apply_gains(n_ant: int, gains, vis):
 
 
 def image_batch(ant_xyz, layers, vis, mode: str = "fft", n_threads: int = 0, gains=None,
-                gain_stride: int = 0, ref=None):
+                gain_stride: int = 0, ref=None, gain_period: int = 0):
     """Whole path over many layers.
 
     ``layers`` is a sequence of dicts with keys n_px, weighting, freq_hz,
     delta_u, vis_offset (complex elements into ``vis``).  Optional: ``gains``
-    (complex, layer l uses the row starting at l * gain_stride) applied to the
-    visibilities, and ``ref`` (flat, packed like the returned images)
+    (complex, layer l uses the row starting at r * gain_stride, r = l mod
+    gain_period, or r = l when gain_period is 0) applied to the visibilities, and ``ref`` (flat, packed like the returned images)
     subtracted from the images.  Returns (list of float64 images, wsum array).
     """
     xyz = np.ascontiguousarray(ant_xyz, np.float64)
@@ -225,7 +225,8 @@ def image_batch(ant_xyz, layers, vis, mode: str = "fft", n_threads: int = 0, gai
         r = None if ref is None else np.ascontiguousarray(ref, np.float64).reshape(-1)
         if r is not None and r.size < out.size:
             raise ValueError("reference images smaller than the output")
-        if g is not None and g.size < (L - 1) * int(gain_stride) + xyz.shape[0]:
+        rows = min(L, int(gain_period)) if gain_period > 0 else L
+        if g is not None and g.size < (rows - 1) * int(gain_stride) + xyz.shape[0]:
             raise ValueError("gain rows smaller than the layers need")
         st = _load().orc_image_batch_ex(
             _p(xyz, ctypes.c_double), xyz.shape[0], L, _p(npx, ctypes.c_int32),
@@ -233,7 +234,7 @@ def image_batch(ant_xyz, layers, vis, mode: str = "fft", n_threads: int = 0, gai
             _p(vo, ctypes.c_int64), _p(oo, ctypes.c_int64),
             _p(vis.view(np.float32), ctypes.c_float),
             None if g is None else _p(g.view(np.float64), ctypes.c_double), int(gain_stride),
-            None if r is None else _p(r, ctypes.c_double), _p(out, ctypes.c_double),
+            int(gain_period), None if r is None else _p(r, ctypes.c_double), _p(out, ctypes.c_double),
             _p(ws, ctypes.c_double), 1 if mode == "direct" else 0, int(n_threads))
     if st != 0:
         raise ValueError(f"orc_image_batch failed ({st})")

@@ -503,22 +503,25 @@ void orc_apply_gains(int n_ant, const double *gains, const float *vis, double *o
 int orc_image_batch_ex(const double *ant_xyz, int n_ant, int n_layers, const int32_t *n_px,
                        const int32_t *weighting, const double *freq_hz, const double *delta_u,
                        const int64_t *vis_off, const int64_t *out_off, const float *vis,
-                       const double *gains, int64_t gain_stride, const double *ref,
-                       double *images, double *wsum, int mode, int n_threads);
+                       const double *gains, int64_t gain_stride, int64_t gain_period,
+                       const double *ref, double *images, double *wsum, int mode, int n_threads);
 
 int orc_image_batch(const double *ant_xyz, int n_ant, int n_layers, const int32_t *n_px,
                     const int32_t *weighting, const double *freq_hz, const double *delta_u,
                     const int64_t *vis_off, const int64_t *out_off, const float *vis,
                     double *images, double *wsum, int mode, int n_threads) {
     return orc_image_batch_ex(ant_xyz, n_ant, n_layers, n_px, weighting, freq_hz, delta_u, vis_off,
-                              out_off, vis, NULL, 0, NULL, images, wsum, mode, n_threads);
+                              out_off, vis, NULL, 0, 0, NULL, images, wsum, mode, n_threads);
 }
 
 /* The same with the two optional steps around the imager that transient
  * searches use:
  *   gains (may be NULL): layer l's visibilities are first multiplied by
- *     g_i conj(g_j) with the gain row gains + 2 * l * gain_stride (complex128,
- *     [n_ant]); gain_stride 0 = one row for every layer (Sec. 4.2, step ii);
+ *     g_i conj(g_j) with the gain row gains + 2 * r * gain_stride, r = l mod
+ *     gain_period (r = l when gain_period <= 0), complex128 [n_ant];
+ *     gain_stride 0 = one row for every layer; gain_period = number of
+ *     channels gives per-channel gains for time-major layers (Sec. 4.2,
+ *     step ii);
  *   ref (may be NULL): a reference image is subtracted from each dirty image,
  *     image = dirty - ref, ref read at the layer's out_off like the output
  *     (Sec. 2 and Sec. 4.3 after Eq. 6: side-lobes of a transient search are
@@ -526,8 +529,8 @@ int orc_image_batch(const double *ant_xyz, int n_ant, int n_layers, const int32_
 int orc_image_batch_ex(const double *ant_xyz, int n_ant, int n_layers, const int32_t *n_px,
                        const int32_t *weighting, const double *freq_hz, const double *delta_u,
                        const int64_t *vis_off, const int64_t *out_off, const float *vis,
-                       const double *gains, int64_t gain_stride, const double *ref,
-                       double *images, double *wsum, int mode, int n_threads) {
+                       const double *gains, int64_t gain_stride, int64_t gain_period,
+                       const double *ref, double *images, double *wsum, int mode, int n_threads) {
     const int64_t nb = orc_n_baselines(n_ant);
     int status = 0;
 #ifdef _OPENMP
@@ -547,7 +550,8 @@ int orc_image_batch_ex(const double *ant_xyz, int n_ant, int n_layers, const int
             orc_uv(ant_xyz, n_ant, freq_hz[l], u, v);
             orc_cells(u, v, nb, delta_u[l], n, ku, kv);
             if (gains) {
-                orc_apply_gains(n_ant, gains + 2 * gain_stride * l, vis + 2 * vis_off[l], vg);
+                const int64_t row = gain_period > 0 ? l % gain_period : l;
+                orc_apply_gains(n_ant, gains + 2 * gain_stride * row, vis + 2 * vis_off[l], vg);
                 st = orc_grid_c128(ku, kv, vg, nb, n, weighting[l], g, NULL, &wsum[l]);
             } else {
                 st = orc_grid(ku, kv, vis + 2 * vis_off[l], nb, n, weighting[l], g, NULL, &wsum[l]);

@@ -112,6 +112,12 @@ def test_gain_rows_follow_the_stride():
     (first,), _ = oracle.image_batch(xyz, [dict(lay[2], vis_offset=0)], vis[2 * nb:],
                                      gains=rows[0])
     assert np.array_equal(shared[2], first)
+    # period 2: layer 2 wraps around to row 0 (all three rows passed, so a
+    # wrong row index reads valid memory)
+    per, _ = oracle.image_batch(xyz, lay, vis, gains=rows.reshape(-1), gain_stride=8,
+                                gain_period=2)
+    assert np.array_equal(per[2], first)
+    assert np.array_equal(per[1], together[1])
 
 
 def test_reference_subtraction_is_dirty_minus_reference():

@@ -67,8 +67,11 @@ MUTANTS = {
     "reference_added": ("for (int64_t p = 0; p < (int64_t)n * n; ++p) img[p] -= rf[p];",
                         "for (int64_t p = 0; p < (int64_t)n * n; ++p) img[p] += rf[p];"),
     # every layer reads the first gain row
-    "gain_stride_ignored": ("orc_apply_gains(n_ant, gains + 2 * gain_stride * l,",
+    "gain_stride_ignored": ("orc_apply_gains(n_ant, gains + 2 * gain_stride * row,",
                             "orc_apply_gains(n_ant, gains,"),
+    # gain period ignored (rows run on past the period)
+    "gain_period_ignored": ("const int64_t row = gain_period > 0 ? l % gain_period : l;",
+                            "const int64_t row = l;"),
 }
 
 PINS = [
