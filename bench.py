@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "dirty images/s and Gvis/s gridded on 1 GB300, % roofline, error vs FP64 oracle"
 UNIT = "images/s"
-KERNEL = "k_image_sched<180>"
+KERNEL = "k_image_sched<180, false>"
 CSRC = os.path.join(ROOT, "paper_2405_13478_gb300", "csrc")
 
 
@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the plan-reuse and fused-epilogue timings of the default workload")
     p.add_argument("--n-times", type=int, default=None, help="time steps per rank")
     p.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"],
                    help="cfg2 (default): the headline station batch; the others measure the "
@@ -77,7 +79,7 @@ def measured_peaks():
 def ncu_traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None if there is none for the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "k_image_small_180_traffic.json")
+    path = os.path.join(ROOT, "profiles", "k_image_sched_180_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -180,6 +182,79 @@ def sampled_error(ctx, ws, d_xyz, vis, images, layers, n=8):
         g = images[o:o + 180 * 180].cpu().numpy().reshape(180, 180)
         worst = max(worst, float(np.abs(g - w).max() / np.abs(w).max()))
     return worst
+
+
+def epilogue_variants(torch, binding, ctx, ws, d_xyz, larr, vis, images, wsum, layers, steps,
+                      warmup):
+    """The same batch through one reused plan: the plain transform, and the
+    fused epilogue (per-channel antenna gains applied at gridding, a
+    reference image subtracted at the store) as a difference-imaging search
+    would run it.  Returns (dict, error of the epilogue vs the oracle)."""
+    import numpy as np
+
+    import oracle
+
+    C, B = ws.n_chan, ws.n_baselines
+    stream = torch.cuda.current_stream()
+    plan = binding.Plan(ctx, d_xyz, larr)
+    rng = np.random.default_rng(3)
+    g = (np.abs(rng.normal(1.0, 0.1, (C, ws.n_ant)))
+         * np.exp(1j * rng.uniform(-np.pi, np.pi, (C, ws.n_ant)))).astype(np.complex64)
+    d_g = torch.as_tensor(g.reshape(-1)).cuda()
+    ref = torch.empty_like(images)
+    plan.image(vis, ref)                                  # reference = dirty images of the batch
+    ref.mul_(0.5)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    L = len(layers)
+    ms_plain = timed(lambda: plan.image(vis, images, wsum))
+    ms_gains = timed(lambda: plan.image(vis, images, wsum, gains=d_g, gain_stride=ws.n_ant,
+                                        gain_period=C))
+    ms_ref = timed(lambda: plan.image(vis, images, wsum, ref=ref))
+    ms_epi = timed(lambda: plan.image(vis, images, wsum, gains=d_g, gain_stride=ws.n_ant,
+                                      gain_period=C, ref=ref))
+    # sampled error of the epilogue against the oracle
+    pick = [0, L // 2 + 7, L - 1]
+    sub = [dict(layers[k], vis_offset=i * B) for i, k in enumerate(pick)]
+    v = torch.stack([vis[layers[k]["vis_offset"]:layers[k]["vis_offset"] + B] for k in pick])
+    n2 = 180 * 180
+    r = torch.stack([ref[layers[k]["out_offset"]:layers[k]["out_offset"] + n2] for k in pick])
+    rows = np.stack([g[k % C] for k in pick]).astype(np.complex128)
+    want, _ = oracle.image_batch(ws.ant_xyz, sub, v.cpu().reshape(-1).numpy(), "fft",
+                                 gains=rows.reshape(-1), gain_stride=ws.n_ant,
+                                 ref=r.cpu().double().reshape(-1).numpy())
+    worst = 0.0
+    for k, w, rr in zip(pick, want, r.cpu().numpy()):
+        o = layers[k]["out_offset"]
+        got = images[o:o + n2].cpu().numpy().reshape(180, 180)
+        worst = max(worst, float(np.abs(got - w).max() / (np.abs(w).max() + np.abs(rr).max())))
+    plan.close()
+    del ref
+    bytes_plain = B * 8 + n2 * 4
+    bytes_epi = bytes_plain + n2 * 4                      # + reference read
+    return {"plan_reused": {"images_per_s": L / (ms_plain / 1e3), "ms_per_step": ms_plain,
+                            "hbm_gbs": L * bytes_plain / (ms_plain / 1e3) / 1e9},
+            "epilogue_gains": {"images_per_s": L / (ms_gains / 1e3), "ms_per_step": ms_gains},
+            "epilogue_ref": {"images_per_s": L / (ms_ref / 1e3), "ms_per_step": ms_ref,
+                             "hbm_gbs": L * bytes_epi / (ms_ref / 1e3) / 1e9},
+            "epilogue_gains_ref": {"images_per_s": L / (ms_epi / 1e3), "ms_per_step": ms_epi,
+                                   "hbm_gbs": L * bytes_epi / (ms_epi / 1e3) / 1e9,
+                                   "algorithmic_bytes_per_image": bytes_epi,
+                                   "err_vs_oracle": worst,
+                                   "what": "per-channel antenna gains (32 rows, period 32) "
+                                           "applied at gridding + reference image subtracted "
+                                           "at the store"}}
 
 
 def run_reference(args):
@@ -290,6 +365,10 @@ def run_ours(args):
         ms = float(t.item())
     value = world * L * args.steps / (ms / 1e3)
     err = sampled_error(ctx, ws, d_xyz, vis, images, layers) if rank == 0 else None
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = epilogue_variants(torch, binding, ctx, ws, d_xyz, larr, vis, images, wsum,
+                                     layers, args.steps, args.warmup)
 
     # e2e: the host-buffer entry point (pinned host memory), copies inside the
     # timed region, overlapped with the kernels by the library's pipeline
@@ -336,6 +415,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world} (independent layers, no collective)"},
             "gvis_per_s": value * B / 1e9,
             "err_vs_oracle": err,
+            "variants": variants,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": (tr * L) if tr is not None else None,
@@ -346,7 +426,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d_bytes,
                     "d2h_bytes_per_step": int(images.numel() * 4 + wsum.numel() * 4)},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 7 * args.steps,  # 6 table kernels + 1 fused image kernel per step
         }
         print(json.dumps(out), flush=True)
     ctx.close()

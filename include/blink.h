@@ -197,6 +197,39 @@ BLINK_API int blink_plan_create(blink_ctx *ctx, const double *d_ant_xyz, int n_a
                       const blink_layer *h_layers, int n_layers, blink_plan **out, void *stream);
 BLINK_API int blink_plan_image(blink_plan *plan, const float *d_vis, float *d_images, float *d_wsum,
                      uint32_t flags, void *stream);
+
+/* Fused epilogue of blink_plan_image_ex / blink_plan_capture (every field may
+ * be NULL / 0; a NULL blink_epilogue pointer means none):
+ *   d_gains      complex64 (re, im) antenna gains, device memory.  Layer l
+ *                (index into the plan's layer array) uses the n_ant gains at
+ *                d_gains + 2 * r * gain_stride floats, r = l mod gain_period
+ *                (r = l when gain_period is 0); each visibility of the
+ *                pair (i < j) is multiplied by g_i conj(g_j) as it is loaded
+ *                for gridding (calibration applied after correlation,
+ *                Sec. 4.2 step ii; pass reciprocal gains to remove a
+ *                solution).  Needs n_ant < 65536.
+ *   gain_stride  complex elements between consecutive gain rows; 0 = one
+ *                row for every layer.  Must be >= 0.
+ *   gain_period  0, or the number of gain rows that repeat over the layers:
+ *                with time-major layers, gain_period = channels gives
+ *                per-channel gains constant over time.  Must be >= 0.
+ *   d_ref        float32 reference images, device memory, addressed like
+ *                d_images (layer l at out_offset).  The output becomes the
+ *                dirty image minus the reference, subtracted as the image is
+ *                stored (Sec. 2 and Sec. 4.3 after Eq. 6: side-lobes of a
+ *                transient search removed by subtracting a reference image of
+ *                the same field).  With BLINK_NORMALIZE the dirty image is
+ *                normalised first.  d_ref must not overlap the output
+ *                extent (BLINK_ERR_INVALID). */
+typedef struct {
+    const float *d_gains;
+    int64_t gain_stride;
+    int64_t gain_period;
+    const float *d_ref;
+} blink_epilogue;
+
+BLINK_API int blink_plan_image_ex(blink_plan *plan, const float *d_vis, float *d_images, float *d_wsum,
+                                  uint32_t flags, const blink_epilogue *epi, void *stream);
 BLINK_API void blink_plan_destroy(blink_plan *plan);
 
 /* Autotuner: for every image size of the plan, times the candidate kernel
@@ -217,12 +250,12 @@ BLINK_API int blink_plan_tuning(const blink_plan *plan, int group, int *n_px, in
 BLINK_API int blink_plan_set_tuning(blink_plan *plan, int group, int path, int64_t wave_bytes);
 
 /* CUDA graph of the plan's image launches: blink_plan_capture runs
- * blink_plan_image once on `stream` (allocating whatever it needs), then
+ * blink_plan_image_ex once on `stream` (allocating whatever it needs), then
  * records the same launches, bound to these pointers and flags, into a graph
  * owned by the plan (replacing any earlier one).  blink_plan_replay launches
  * the whole batch -- every image size -- as that one graph on `stream`. */
 BLINK_API int blink_plan_capture(blink_plan *plan, const float *d_vis, float *d_images, float *d_wsum,
-                                 uint32_t flags, void *stream);
+                                 uint32_t flags, const blink_epilogue *epi, void *stream);
 BLINK_API int blink_plan_replay(blink_plan *plan, void *stream);
 
 /* Waits for `stream` and returns the plan's device status word: BLINK_OK, or

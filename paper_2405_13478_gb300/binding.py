@@ -29,6 +29,7 @@ EXPORTS = (
     "blink_image_batch_noalloc", "blink_image_batch_host", "blink_degrid", "blink_plan_degrid",
     "blink_apply_gains", "blink_gain_grad", "blink_plan_check", "blink_plan_autotune",
     "blink_plan_tuning", "blink_plan_set_tuning", "blink_plan_capture", "blink_plan_replay",
+    "blink_plan_image_ex",
 )
 
 
@@ -42,6 +43,35 @@ class Layer(ctypes.Structure):
     _fields_ = [("n_px", ctypes.c_int32), ("weighting", ctypes.c_int32),
                 ("freq_hz", ctypes.c_double), ("delta_u", ctypes.c_double),
                 ("vis_offset", ctypes.c_int64), ("out_offset", ctypes.c_int64)]
+
+
+class Epilogue(ctypes.Structure):
+    """blink_epilogue: gains applied at gridding, reference image subtracted."""
+    _fields_ = [("d_gains", ctypes.c_void_p), ("gain_stride", ctypes.c_int64),
+                ("gain_period", ctypes.c_int64), ("d_ref", ctypes.c_void_p)]
+
+
+def _epilogue(gains, gain_stride, ref, gain_period=0):
+    """A blink_epilogue for the optional tensors (None when both are absent)."""
+    if gains is None and ref is None:
+        return None
+    _check_dev(gains, ref)
+    if gains is not None and gains.dtype != _complex64():
+        raise ValueError("gains must be complex64")
+    if ref is not None and ref.dtype != _float32():
+        raise ValueError("reference images must be float32")
+    return Epilogue(0 if gains is None else gains.data_ptr(), int(gain_stride), int(gain_period),
+                    0 if ref is None else ref.data_ptr())
+
+
+def _complex64():
+    import torch
+    return torch.complex64
+
+
+def _float32():
+    import torch
+    return torch.float32
 
 
 _lib = None
@@ -78,6 +108,8 @@ def lib(path: str = LIB_PATH):
     L.blink_plan_create.argtypes = [P, P, I, LP, I, ctypes.POINTER(P), P]
     L.blink_plan_image.restype = I
     L.blink_plan_image.argtypes = [P, P, P, P, ctypes.c_uint32, P]
+    L.blink_plan_image_ex.restype = I
+    L.blink_plan_image_ex.argtypes = [P, P, P, P, ctypes.c_uint32, ctypes.POINTER(Epilogue), P]
     L.blink_plan_destroy.restype = None
     L.blink_plan_destroy.argtypes = [P]
     L.blink_image_batch_host.restype = I
@@ -98,7 +130,7 @@ def lib(path: str = LIB_PATH):
     L.blink_plan_set_tuning.restype = I
     L.blink_plan_set_tuning.argtypes = [P, I, I, ctypes.c_int64]
     L.blink_plan_capture.restype = I
-    L.blink_plan_capture.argtypes = [P, P, P, P, ctypes.c_uint32, P]
+    L.blink_plan_capture.argtypes = [P, P, P, P, ctypes.c_uint32, ctypes.POINTER(Epilogue), P]
     L.blink_plan_replay.restype = I
     L.blink_plan_replay.argtypes = [P, P]
     L.blink_plan_check.restype = I
@@ -293,11 +325,22 @@ class Plan:
                                               len(layers), ctypes.byref(h), _stream(stream)))
         self.handle = h
 
-    def image(self, vis, images_out, wsum_out=None, flags=0, stream=None):
+    def image(self, vis, images_out, wsum_out=None, flags=0, stream=None, gains=None,
+              gain_stride=0, ref=None, gain_period=0):
+        """Dirty images of the plan's layers.  Optional fused epilogue: ``gains``
+        (complex64, layer l uses the row at r * gain_stride, r = l mod
+        gain_period or l) applied to the visibilities, ``ref`` (float32, laid
+        out like ``images_out``) subtracted from the images."""
         _check_dev(vis, images_out, wsum_out)
-        self.ctx._raise(self.ctx._lib.blink_plan_image(self.handle, _ptr(vis), _ptr(images_out),
-                                                       _ptr(wsum_out), int(flags),
-                                                       _stream(stream)))
+        epi = _epilogue(gains, gain_stride, ref, gain_period)
+        if epi is None:
+            st = self.ctx._lib.blink_plan_image(self.handle, _ptr(vis), _ptr(images_out),
+                                                _ptr(wsum_out), int(flags), _stream(stream))
+        else:
+            st = self.ctx._lib.blink_plan_image_ex(self.handle, _ptr(vis), _ptr(images_out),
+                                                   _ptr(wsum_out), int(flags), ctypes.byref(epi),
+                                                   _stream(stream))
+        self.ctx._raise(st)
 
     def degrid(self, dimage, dvis_out, flags=0, stream=None):
         _check_dev(dimage, dvis_out)
@@ -326,12 +369,15 @@ class Plan:
         self.ctx._raise(self.ctx._lib.blink_plan_set_tuning(self.handle, int(group), int(path),
                                                             int(wave_bytes)))
 
-    def capture(self, vis, images_out, wsum_out=None, flags=0, stream=None):
-        """Record the batch's launches into a CUDA graph bound to these buffers."""
+    def capture(self, vis, images_out, wsum_out=None, flags=0, stream=None, gains=None,
+                gain_stride=0, ref=None, gain_period=0):
+        """Record the batch's launches (with the optional epilogue) into a CUDA
+        graph bound to these buffers."""
         _check_dev(vis, images_out, wsum_out)
-        self.ctx._raise(self.ctx._lib.blink_plan_capture(self.handle, _ptr(vis), _ptr(images_out),
-                                                         _ptr(wsum_out), int(flags),
-                                                         _stream(stream)))
+        epi = _epilogue(gains, gain_stride, ref, gain_period)
+        self.ctx._raise(self.ctx._lib.blink_plan_capture(
+            self.handle, _ptr(vis), _ptr(images_out), _ptr(wsum_out), int(flags),
+            None if epi is None else ctypes.byref(epi), _stream(stream)))
 
     def replay(self, stream=None):
         """Launch the captured graph (the whole batch, every image size)."""

@@ -69,6 +69,9 @@ struct blink_plan {
     float2 *d_gscratch = nullptr;  // tensor-core transform scratch (allocated on first use)
     size_t gscratch_bytes = 0;
     int *d_status = nullptr;       // device status word (in the table block)
+    int64_t out_extent = 0;        // max over layers of out_offset + n_px^2
+    float2 *d_gprod = nullptr;     // gain-product table of the fused epilogue (on first use)
+    size_t gprod_bytes = 0;
     cudaStream_t last_stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaGraphExec_t graph = nullptr;     // captured image launches (blink_plan_capture)
@@ -76,7 +79,10 @@ struct blink_plan {
 
 namespace {
 
-constexpr size_t kScratchCap = size_t(48) << 20;  // bytes of row-transform scratch per plan (L2-sized waves)
+constexpr size_t kScratchCap = size_t(48) << 20;
+// Largest gain-product table (distinct gain rows x baselines x 8 bytes) the
+// fused epilogue builds; above it the kernels form g_i conj(g_j) per entry.
+constexpr size_t kGainTableCap = size_t(256) << 20;  // bytes of row-transform scratch per plan (L2-sized waves)
 
 // Runs f with ctx->device current and restores the caller's device.
 struct DeviceGuard {
@@ -164,6 +170,9 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     if (p->d_dscratch) cudaFreeAsync(p->d_dscratch, st);
     if (p->d_gscratch) cudaFreeAsync(p->d_gscratch, st);
     p->d_gscratch = nullptr;
+    if (p->d_gprod) cudaFreeAsync(p->d_gprod, st);
+    p->d_gprod = nullptr;
+    p->gprod_bytes = 0;
     p->d_block = nullptr;
     p->d_scratch = nullptr;
     p->d_sched = nullptr;
@@ -180,6 +189,8 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     p->ctx = ctx;
     p->n_ant = n_ant;
     p->nb = int64_t(n_ant) * (n_ant - 1) / 2;
+    for (int l = 0; l < n_layers; ++l)
+        p->out_extent = std::max(p->out_extent, h_layers[l].out_offset + int64_t(h_layers[l].n_px) * h_layers[l].n_px);
     p->n_layers = n_layers;
     p->last_stream = st;
     // distinct channels
@@ -220,8 +231,14 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         ci.weighting = p->geoms[size_t(c)].weighting;
         ci.code_off = int64_t(c) * p->nb;
         ci.sched_off = -1;
-        ci.csr_off = csr_total;
-        csr_total += blink::CsrLayout(ci.n_px, p->nb).bytes;
+        // row buckets only where a full-extent image can miss the fused kernel
+        // (sizes whose whole support always fits it never need them)
+        if (!blink::image_small_path(ci.n_px, ci.n_px / 2 + 1)) {
+            ci.csr_off = csr_total;
+            csr_total += blink::CsrLayout(ci.n_px, p->nb).bytes;
+        } else {
+            ci.csr_off = -1;
+        }
         const bool sched = ci.n_px <= kSchedMaxPx;
         if (sched) {
             const int q = int((p->nb + blink::kSchedMaxChunk - 1) / blink::kSchedMaxChunk);
@@ -374,6 +391,7 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.max_seg = g.max_seg;
     a.status = p->d_status;
     a.csr = p->d_csr;
+    a.n_ant = p->n_ant;
     a.force_path = g.force_path;
     a.wave_budget = g.wave_budget;
     return a;
@@ -466,20 +484,62 @@ static int ensure_rows_scratch(blink_plan *p, cudaStream_t st) {
 
 int blink_plan_image(blink_plan *p, const float *d_vis, float *d_images, float *d_wsum, uint32_t flags,
                      void *stream) {
+    return blink_plan_image_ex(p, d_vis, d_images, d_wsum, flags, nullptr, stream);
+}
+
+int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, float *d_wsum, uint32_t flags,
+                        const blink_epilogue *epi, void *stream) {
     if (!p) return BLINK_ERR_INVALID;
     blink_ctx *ctx = p->ctx;
     if (p->n_layers && (!d_vis || !d_images)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
     const uint32_t mode = (flags & BLINK_TRANSFORM_MASK) >> 4;
     if ((flags & ~uint32_t(BLINK_NORMALIZE | BLINK_TRANSFORM_MASK)) || mode > 4)
         return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
+    const float *d_gains = epi ? epi->d_gains : nullptr;
+    const float *d_ref = epi ? epi->d_ref : nullptr;
+    if (epi && (epi->gain_stride < 0 || epi->gain_period < 0))
+        return fail(ctx, BLINK_ERR_INVALID, "gain_stride and gain_period must be >= 0");
+    if (d_gains && p->n_ant >= 65536) return fail(ctx, BLINK_ERR_UNSUPPORTED, "gains need fewer than 65536 antennas");
+    if (d_ref) {
+        // the kernels read the reference and write the output through
+        // non-aliasing (restrict) pointers: the two extents must not overlap
+        const uintptr_t r0 = reinterpret_cast<uintptr_t>(d_ref), i0 = reinterpret_cast<uintptr_t>(d_images);
+        const uintptr_t ext = uintptr_t(p->out_extent) * sizeof(float);
+        if (r0 < i0 + ext && i0 < r0 + ext)
+            return fail(ctx, BLINK_ERR_INVALID, "reference images overlap the output");
+    }
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     p->last_stream = st;
+    // gain products g_i conj(g_j) once per distinct gain row, when they fit
+    const float2 *gprod = nullptr;
+    if (d_gains && p->nb > 0) {
+        const int64_t rows = epi->gain_stride == 0 ? 1
+                             : (epi->gain_period > 0 ? std::min<int64_t>(epi->gain_period, p->n_layers)
+                                                     : int64_t(p->n_layers));
+        const size_t bytes = size_t(rows) * size_t(p->nb) * sizeof(float2);
+        if (rows > 0 && bytes <= kGainTableCap) {
+            if (bytes > p->gprod_bytes) {
+                if (p->d_gprod) cudaFreeAsync(p->d_gprod, st);
+                p->d_gprod = nullptr;
+                p->gprod_bytes = 0;
+                void *ptr = nullptr;
+                if (cudaMallocFromPoolAsync(&ptr, bytes, ctx->pool, st) != cudaSuccess)
+                    return fail(ctx, BLINK_ERR_WORKSPACE, "gain-product table allocation failed");
+                p->d_gprod = static_cast<float2 *>(ptr);
+                p->gprod_bytes = bytes;
+            }
+            Error e = blink::launch_gain_products(reinterpret_cast<const float2 *>(d_gains), epi->gain_stride,
+                                                  int(rows), p->n_ant, p->nb, p->d_gprod, st);
+            if (e.status) return fail(ctx, e);
+            gprod = p->d_gprod;
+        }
+    }
     // groups that take the tensor-core transform: supported size, 16-byte
-    // aligned image rows
+    // aligned image rows (and reference rows)
     auto gemm_ok = [&](const blink_plan::Group &grp) {
         if (!mode || !blink::dftgemm_supported(grp.n_px, grp.r_alloc, mode) ||
-            (reinterpret_cast<uintptr_t>(d_images) & 15))
+            ((reinterpret_cast<uintptr_t>(d_images) | reinterpret_cast<uintptr_t>(d_ref)) & 15))
             return false;
         for (int k = grp.first; k < grp.first + grp.count; ++k)
             if (p->layer_out[size_t(k)] & 3) return false;
@@ -511,6 +571,11 @@ int blink_plan_image(blink_plan *p, const float *d_vis, float *d_images, float *
         }
     for (const auto &grp : p->groups) {
         blink::ImageArgs a = group_args(p, grp, d_vis, d_images, d_wsum, flags & BLINK_NORMALIZE);
+        a.gains = reinterpret_cast<const float2 *>(d_gains);
+        a.gain_stride = epi ? epi->gain_stride : 0;
+        a.gain_period = epi ? epi->gain_period : 0;
+        a.gprod = gprod;
+        a.ref = d_ref;
         Error e;
         if (gemm_ok(grp)) {
             a.scratch = p->d_gscratch;
@@ -629,7 +694,7 @@ int blink_plan_set_tuning(blink_plan *p, int group, int path, int64_t wave_bytes
 }
 
 int blink_plan_capture(blink_plan *p, const float *d_vis, float *d_images, float *d_wsum, uint32_t flags,
-                       void *stream) {
+                       const blink_epilogue *epi, void *stream) {
     if (!p) return BLINK_ERR_INVALID;
     blink_ctx *ctx = p->ctx;
     DeviceGuard g(ctx->device);
@@ -637,7 +702,7 @@ int blink_plan_capture(blink_plan *p, const float *d_vis, float *d_images, float
     // every allocation happens before capture
     int rc = ensure_rows_scratch(p, st);
     if (rc) return rc;
-    rc = blink_plan_image(p, d_vis, d_images, d_wsum, flags, stream);  // also allocates lazily
+    rc = blink_plan_image_ex(p, d_vis, d_images, d_wsum, flags, epi, stream);  // also allocates lazily
     if (rc) return rc;
     if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return fail(ctx, BLINK_ERR_CUDA, "capture stream creation failed");
@@ -649,7 +714,7 @@ int blink_plan_capture(blink_plan *p, const float *d_vis, float *d_images, float
     if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return fail(ctx, BLINK_ERR_CUDA, "begin capture failed");
     const cudaStream_t keep = p->last_stream;
-    rc = blink_plan_image(p, d_vis, d_images, d_wsum, flags, p->cap_stream);
+    rc = blink_plan_image_ex(p, d_vis, d_images, d_wsum, flags, epi, p->cap_stream);
     p->last_stream = keep;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &graph);

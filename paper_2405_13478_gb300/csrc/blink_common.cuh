@@ -6,6 +6,13 @@
 
 #include <string>
 
+// Supported image sizes (N_px): products of small radices whose four-step
+// split N = N1 * N2 has register-sized codelets.  Every per-size dispatch in
+// the library expands this list.
+#define BLINK_FOR_EACH_SIZE(X) \
+    X(16) X(20) X(24) X(32) X(36) X(48) X(64) X(96) X(120) X(128) X(160) X(180) X(192) X(256) \
+    X(360) X(384) X(512) X(768) X(1024)
+
 namespace blink {
 
 constexpr double kSpeedOfLight = 299792458.0;  // m/s (SI definition)

@@ -52,6 +52,7 @@ struct DftArgs {
     uint32_t flags;
     int n_px, K;
     int *status;
+    const float *ref;             // reference images (fused epilogue) or null
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -202,7 +203,8 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t da, uint64_t db,
 
 // Grid: (N / 128, N / 256, layers of the wave).  128 threads.
 template <bool FP16, int SPLIT>
-__global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0) {
+__global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__restrict__ out,
+                                                    const float *__restrict__ ref) {
     constexpr bool CROSS = FP16 && SPLIT == 3;      // separate accumulator for the cross terms
     constexpr uint32_t NCOL = CROSS ? 512 : 256;    // TMEM columns
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0) {
         if (FP16) scale = ldexpf(scale, d.b_exp[lw]);
         const float cross = 1.f / float(1 << lo_shift<FP16>());
         const int y = mt * kTileM + warp * 32 + lane;
-        float *row = d.out + L.out_off + int64_t(y) * N;
+        float *row = out + L.out_off + int64_t(y) * N;
         for (int c0 = 0; c0 < kTileN; c0 += 32) {
             uint32_t r[32];
             tmem_ld32<32>(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
@@ -314,6 +316,13 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0) {
                 v.y = e1 * scale;
                 v.z = e2 * scale;
                 v.w = e3 * scale;
+                if (ref) {  // fused epilogue: dirty - reference
+                    const float4 rf = __ldcs(reinterpret_cast<const float4 *>(ref + (o - out) + j));
+                    v.x -= rf.x;
+                    v.y -= rf.y;
+                    v.z -= rf.z;
+                    v.w -= rf.w;
+                }
                 __stcs(reinterpret_cast<float4 *>(o + j), v);
             }
         }
@@ -355,8 +364,10 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
         if (e.status) return e;
         k_split<FP16><<<cnt, 256, 0, st>>>(T, a.r_alloc, N, Rp, a.layers, a.chans, l0, b_hi, b_lo, b_exp);
         BLINK_CUDA_TRY(cudaGetLastError());
-        DftArgs d{a_hi, a_lo, b_hi, b_lo, b_exp, a.layers, a.chans, static_cast<float *>(a.out), a.flags, N, K, a.status};
-        k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / kTileN), unsigned(cnt)), 128, smem, st>>>(d, l0);
+        DftArgs d{a_hi, a_lo, b_hi, b_lo, b_exp, a.layers, a.chans, static_cast<float *>(a.out), a.flags, N, K, a.status,
+                  a.ref};
+        k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / kTileN), unsigned(cnt)), 128, smem, st>>>(
+            d, l0, d.out, d.ref);
         BLINK_CUDA_TRY(cudaGetLastError());
     }
     return Error{0, ""};

@@ -286,8 +286,4 @@ BLINK_PLAN(768, 24, 32)
 BLINK_PLAN(1024, 32, 32)
 #undef BLINK_PLAN
 
-#define BLINK_FOR_EACH_SIZE(X) \
-    X(16) X(20) X(24) X(32) X(36) X(48) X(64) X(96) X(120) X(128) X(160) X(180) X(192) X(256) \
-    X(360) X(384) X(512) X(768) X(1024)
-
 }  // namespace blink

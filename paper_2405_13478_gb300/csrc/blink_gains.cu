@@ -9,27 +9,13 @@
 // summed over all layers.
 #include "blink_common.cuh"
 #include "blink_kernels.cuh"
+#include "blink_pairs.cuh"
 
 #include <algorithm>
 
 namespace blink {
 
 namespace {
-
-__device__ __forceinline__ int64_t pair_index(int i, int j, int n_ant) {  // i < j
-    return int64_t(i) * n_ant - int64_t(i) * (i + 1) / 2 + (j - i - 1);
-}
-
-__device__ __forceinline__ void pair_of_b(int64_t b, int n_ant, int &i, int &j) {
-    const double twon1 = 2.0 * n_ant - 1.0;
-    int r = int((twon1 - sqrt(fmax(twon1 * twon1 - 8.0 * double(b), 0.0))) * 0.5);
-    r = max(0, min(r, n_ant - 2));
-    auto start = [n_ant](int64_t row) { return row * (2 * int64_t(n_ant) - row - 1) / 2; };
-    while (r > 0 && start(r) > b) --r;
-    while (r < n_ant - 2 && start(r + 1) <= b) ++r;
-    i = r;
-    j = int(b - start(r)) + r + 1;
-}
 
 // Grid: (ceil(B / 256), layers).
 __global__ void k_apply_gains(const float2 *__restrict__ model, const float2 *__restrict__ gains,
@@ -38,12 +24,24 @@ __global__ void k_apply_gains(const float2 *__restrict__ model, const float2 *__
     const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     int i, j;
-    pair_of_b(b, n_ant, i, j);
+    baseline_pair(b, n_ant, i, j);
     const int64_t o = vis_off[blockIdx.y] + b;
     const float2 m = model[o], gi = gains[i], gj = gains[j];
     // g_i conj(g_j)
     const float2 p = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
     vis[o] = make_float2(p.x * m.x - p.y * m.y, p.x * m.y + p.y * m.x);
+}
+
+// Grid: (ceil(B / 256), rows).  Gain-product table of the fused epilogue.
+__global__ void k_gain_products(const float2 *__restrict__ gains, int64_t stride, int n_ant, int64_t nb,
+                                float2 *__restrict__ out) {
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int i, j;
+    baseline_pair(b, n_ant, i, j);
+    const float2 *g = gains + int64_t(blockIdx.y) * stride;
+    const float2 gi = g[i], gj = g[j];
+    out[int64_t(blockIdx.y) * nb + b] = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
 }
 
 // One CTA per antenna; FP64 accumulation, fixed-order block reduction.
@@ -60,14 +58,14 @@ __global__ void __launch_bounds__(256) k_gain_grad(const float2 *__restrict__ dv
         const int64_t o = vis_off[l];
         const float2 gj = gains[j];
         if (j > i) {
-            const int64_t b = o + pair_index(i, j, n_ant);
+            const int64_t b = o + baseline_index(i, j, n_ant);
             const float2 gv = dvis[b], m = model[b];
             const double tr = double(gj.x) * m.x + double(gj.y) * m.y;  // g_j conj(M)
             const double ti = double(gj.y) * m.x - double(gj.x) * m.y;
             re += gv.x * tr - gv.y * ti;
             im += gv.x * ti + gv.y * tr;
         } else {
-            const int64_t b = o + pair_index(j, i, n_ant);
+            const int64_t b = o + baseline_index(j, i, n_ant);
             const float2 gv = dvis[b], m = model[b];
             const double ur = double(gj.x) * m.x - double(gj.y) * m.y;  // g_j M
             const double ui = double(gj.x) * m.y + double(gj.y) * m.x;
@@ -90,6 +88,18 @@ __global__ void __launch_bounds__(256) k_gain_grad(const float2 *__restrict__ dv
 }
 
 }  // namespace
+
+Error launch_gain_products(const float2 *gains, int64_t stride, int rows, int n_ant, int64_t nb, float2 *out,
+                           cudaStream_t st) {
+    if (rows <= 0 || nb <= 0) return Error{0, ""};
+    for (int r0 = 0; r0 < rows; r0 += 65535) {
+        const int cnt = std::min(65535, rows - r0);
+        k_gain_products<<<dim3(unsigned((nb + 255) / 256), unsigned(cnt)), 256, 0, st>>>(
+            gains + int64_t(r0) * stride, stride, n_ant, nb, out + int64_t(r0) * nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+    }
+    return Error{0, ""};
+}
 
 Error launch_apply_gains(const float2 *model, const float2 *gains, const int64_t *vis_off, int n_layers, int n_ant,
                          int64_t nb, float2 *vis, cudaStream_t st) {

@@ -41,6 +41,25 @@ struct ImageArgs {
     const unsigned char *csr;   // row buckets of large-image channels (or null)
     int force_path;             // 0 default, 1 scheduled fused, 2 atomic fused, 3 two-kernel
     size_t wave_budget;         // row-transform scratch per wave (0 = default, L2-sized)
+    // fused epilogue (all null/0 when unused)
+    const float2 *gains;        // antenna gains; layer l uses row (l mod gain_period, or l)
+    int64_t gain_stride;        // complex elements between gain rows
+    int64_t gain_period;        // 0 = no wrap
+    int n_ant;                  // antennas (baseline b <-> pair, for the gains)
+    const float2 *gprod;        // gain products g_i conj(g_j) [gain rows][nb], or null
+                                // (then the kernels form them from `gains`)
+    const float *ref;           // reference images, addressed like the output
+};
+
+// Per-size launchers (defined in blink_image_impl.cuh, instantiated once per
+// size in the blink_image_<sizes>.cu units).
+template <int N>
+struct SizeOps {
+    static Error image(const ImageArgs &a, cudaStream_t st);
+    static Error rows_wave(const ImageArgs &a, int l0, int cnt, cudaStream_t st);
+    static Error degrid(const ImageArgs &a, const float *resid, float2 *dvis, cudaStream_t st);
+    static bool small(int r_alloc);
+    static size_t scratch_per_layer(int r_alloc);
 };
 
 bool image_size_supported(int n_px);
@@ -73,6 +92,9 @@ Error launch_degrid_group(int n_px, const ImageArgs &a, const float *resid, floa
 
 // Antenna gains (blink_gains.cu): vis = g_i conj(g_j) model per layer, and
 // the per-antenna gradient accumulated over all layers.
+// out[r][b] = g_i conj(g_j) of gain row r (gains + r * stride), r < rows.
+Error launch_gain_products(const float2 *gains, int64_t stride, int rows, int n_ant, int64_t nb, float2 *out,
+                           cudaStream_t st);
 Error launch_apply_gains(const float2 *model, const float2 *gains, const int64_t *vis_off, int n_layers, int n_ant,
                          int64_t nb, float2 *vis, cudaStream_t st);
 Error launch_gain_grad(const float2 *dvis, const float2 *model, const float2 *gains, const int64_t *vis_off,

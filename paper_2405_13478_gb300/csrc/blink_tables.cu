@@ -5,24 +5,11 @@
 // channel shares its cells and weights.
 #include "blink_common.cuh"
 #include "blink_kernels.cuh"
+#include "blink_pairs.cuh"
 
 #include <algorithm>
 
 namespace blink {
-
-// Antenna pair (i < j) of lexicographic baseline index b; exact integer
-// result after a float estimate of the row.
-__device__ __forceinline__ void pair_of(int64_t b, int n_ant, int &i, int &j) {
-    const double twon1 = 2.0 * n_ant - 1.0;
-    const float disc = float(twon1 * twon1 - 8.0 * double(b));
-    int r = int((float(twon1) - sqrtf(fmaxf(disc, 0.f))) * 0.5f);
-    r = max(0, min(r, n_ant - 2));
-    auto start = [n_ant](int64_t row) { return row * (2 * int64_t(n_ant) - row - 1) / 2; };
-    while (r > 0 && start(r) > b) --r;
-    while (r < n_ant - 2 && start(r + 1) <= b) ++r;
-    i = r;
-    j = int(b - start(r)) + r + 1;
-}
 
 // One axis of a2: k = round half away from zero of (w / delta_u); false if the
 // baseline leaves the grid (|k| > N/2 - 1) or is not finite.
@@ -64,7 +51,7 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
     int row = -1, kabs = 0, kept = 0;
     if (b < nb) {
         int i, j;
-        pair_of(b, n_ant, i, j);
+        baseline_pair(b, n_ant, i, j);
         const double dx = __dsub_rn(ant_xyz[3 * j + 0], ant_xyz[3 * i + 0]);
         const double dy = __dsub_rn(ant_xyz[3 * j + 1], ant_xyz[3 * i + 1]);
         const double u = __ddiv_rn(dx, lambda);
