@@ -7,8 +7,8 @@ station (32640 baselines) in a 38 m disk, 1000 time steps x 32 channels over
 sigma = 1 noise -- 32000 dirty images per step.
 
 One step = one pass of the whole path over the batch through the C ABI:
-a1-a2 + weight tables (plan build, one host sync), a3-a7 (gridding + FFT
-kernels), plan release.  Inputs are device resident when the timed region
+uv, cells and weight tables (plan build, one host sync), then the gridding +
+FFT kernels, then the plan release.  Inputs are device resident when the timed region
 starts; `e2e` repeats the measurement with host buffers and the host<->device
 copies inside the timed region.  Prints one JSON line on rank 0.
 
@@ -46,8 +46,8 @@ def parse():
     p.add_argument("--no-variants", action="store_true",
                    help="skip the plan-reuse and fused-epilogue timings of the default workload")
     p.add_argument("--n-times", type=int, default=None, help="time steps per rank")
-    p.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"],
-                   help="cfg2 (default): the headline station batch; the others measure the "
+    p.add_argument("--workload", default="station", choices=["single", "station", "uneven", "station512", "gains"],
+                   help="station (default): the headline station batch; the others measure the "
                         "single-image latency, uneven batch, tensor-core modes and adjoint")
     return p.parse_args()
 
@@ -263,7 +263,7 @@ def run_reference(args):
     rank, world, _ = dist()
     if rank != 0:
         return
-    ws = synth.config2(seed=0, n_times=20)
+    ws = synth.station_batch(seed=0, n_times=20)
     import oracle
 
     cores = os.cpu_count() or 1
@@ -312,7 +312,7 @@ def run_ours(args):
     lib = binding.lib()  # noqa: F841  (fails loudly when the library is missing)
 
     # Each rank images its own 1000 x 32 batch (weak scaling, no data-path collective).
-    ws = synth.config2(seed=rank, n_times=args.n_times or 1000)
+    ws = synth.station_batch(seed=rank, n_times=args.n_times or 1000)
     layers = ws.layers()
     L = len(layers)
     B = ws.n_baselines
@@ -329,10 +329,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
-        plan = binding.Plan(ctx, d_xyz, larr)     # a1-a2 + tables (one host sync)
+        plan = binding.Plan(ctx, d_xyz, larr)     # uv, cells, weight tables (one host sync)
         if ev:
             ev[0].record(stream)
-        plan.image(vis, images, wsum)              # a3-a7
+        plan.image(vis, images, wsum)              # gridding + transform
         if ev:
             ev[1].record(stream)
         plan.close()
@@ -394,7 +394,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(synth.config2(seed=0, n_times=20))
+        cpu = cpu_baseline(synth.station_batch(seed=0, n_times=20))
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
@@ -493,7 +493,7 @@ def _sample_error(torch, ws, layers, vis_flat, out, picks):
     return worst
 
 
-def run_cfg1(args):
+def run_single(args):
     """One 256^2 image of a 128-antenna 3 km array: latency of a whole call."""
     env = _setup_single()
     if env is None:
@@ -501,7 +501,7 @@ def run_cfg1(args):
     torch, binding, ctx = env
     import synth
 
-    ws = synth.config1(seed=0)
+    ws = synth.single_image(seed=0)
     layers, total = binding.layer_out_offsets(ws.layers())
     vis = ws.vis("cuda").reshape(-1)
     out = torch.empty(total, device="cuda")
@@ -518,7 +518,7 @@ def run_cfg1(args):
     ctx.close()
 
 
-def run_cfg3(args):
+def run_uneven(args):
     """Uneven batch: 768 channels x T steps, 128^2..1024^2 by channel group."""
     env = _setup_single()
     if env is None:
@@ -527,7 +527,7 @@ def run_cfg3(args):
     import synth
 
     n_t = args.n_times or 100
-    ws = synth.config3(seed=0, n_times=n_t)
+    ws = synth.uneven_batch(seed=0, n_times=n_t)
     layers = ws.layers()
     layers, total = binding.layer_out_offsets(layers)
     larr = binding.layer_array([d["n_px"] for d in layers], [d["weighting"] for d in layers],
@@ -535,7 +535,7 @@ def run_cfg3(args):
                                [d["vis_offset"] for d in layers], [d["out_offset"] for d in layers])
     free, _ = torch.cuda.mem_get_info()
     if total * 4 + ws.n_layers * ws.n_baselines * 8 > 0.85 * free:
-        raise SystemExit(f"cfg3 with {n_t} time steps does not fit in device memory; pass --n-times")
+        raise SystemExit(f"uneven with {n_t} time steps does not fit in device memory; pass --n-times")
     vis = ws.vis("cuda").reshape(-1)
     out = torch.empty(total, device="cuda")
     d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
@@ -577,7 +577,7 @@ def run_cfg3(args):
     ctx.close()
 
 
-def run_cfg4(args):
+def run_station512(args):
     """Station 512^2 batch: FP32 FFT against the tensor-core modes."""
     env = _setup_single()
     if env is None:
@@ -586,7 +586,7 @@ def run_cfg4(args):
     import synth
 
     n_t = args.n_times or 2000
-    ws = synth.config4(seed=0, n_times=n_t)
+    ws = synth.station_512(seed=0, n_times=n_t)
     layers = ws.layers()
     layers, total = binding.layer_out_offsets(layers)
     larr = binding.layer_array([d["n_px"] for d in layers], [d["weighting"] for d in layers],
@@ -626,7 +626,7 @@ def run_cfg4(args):
     ctx.close()
 
 
-def run_cfg5(args):
+def run_gains(args):
     """Differentiable 1024^2 imaging with antenna gains: forward + backward."""
     env = _setup_single()
     if env is None:
@@ -638,7 +638,7 @@ def run_cfg5(args):
     from paper_2405_13478_gb300 import autograd
 
     n_t = args.n_times or 100
-    ws = synth.config5(seed=0, n_times=n_t)
+    ws = synth.station_gains(seed=0, n_times=n_t)
     B, n_ant = ws.n_baselines, ws.n_ant
     model_c = torch.as_tensor(synth.model_vis(ws.ant_xyz, ws.freqs_hz, ws.sky).astype(np.complex64)).cuda()
     model = model_c.unsqueeze(0).expand(n_t, -1, -1).contiguous().reshape(-1)
@@ -670,10 +670,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "cfg2":
+    elif args.workload == "station":
         run_ours(args)
     else:
-        {"cfg1": run_cfg1, "cfg3": run_cfg3, "cfg4": run_cfg4, "cfg5": run_cfg5}[args.workload](args)
+        {"single": run_single, "uneven": run_uneven, "station512": run_station512, "gains": run_gains}[args.workload](args)
 
 
 if __name__ == "__main__":

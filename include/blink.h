@@ -4,16 +4,16 @@
  * The library turns batches of complex visibilities into dirty images, one
  * image per (time step, frequency channel) "layer" (Sokolowski et al.,
  * arXiv 2405.13478, Sec. 5.2.4).  For every layer it
- *   a1  computes each baseline's (u,v) in wavelengths from the antenna
+ *   (1) computes each baseline's (u,v) in wavelengths from the antenna
  *       positions and the layer frequency, in FP64 (Sec. 5.2.1 step 1; the
  *       Fig. 7 listing; w is dropped for a coplanar zenith-phased array,
  *       Sec. 4.3 Eqs. 4-5);
- *   a2  assigns the grid cell k = round-half-away(u / delta_u), zero spatial
+ *   (2) assigns the grid cell k = round-half-away(u / delta_u), zero spatial
  *       frequency in the centre bin, keeping |k_u|,|k_v| <= N/2-1 (Sec. 4.4.1
  *       Eq. 9; Sec. 5.2.1 step 1);
- *   a3  grids V at k and conj(V) at -k (Sec. 5.2.1 steps 2-3);
- *   a4  applies natural or uniform (1/count) weighting (Sec. 4.4.2);
- *   a5-a7  inverse 2-D FFT with FFT shifts and real part (Sec. 4.3 Eq. 6,
+ *   (3) grids V at k and conj(V) at -k (Sec. 5.2.1 steps 2-3);
+ *   (4) applies natural or uniform (1/count) weighting (Sec. 4.4.2);
+ *   (5) runs the inverse 2-D FFT with FFT shifts and real part (Sec. 4.3 Eq. 6,
  *       Sec. 5.2.2), unnormalised: a unit source at the phase centre gives a
  *       centre pixel equal to the summed weight.
  *
@@ -113,16 +113,16 @@ BLINK_API void blink_ctx_destroy(blink_ctx *ctx);
  * to the context and stays valid until its next call. */
 BLINK_API const char *blink_last_error(const blink_ctx *ctx);
 
-/* ------------------------------------------------------------ a1-a2 only */
+/* ------------------------------------------------- cell indices only */
 /* Cell indices of every baseline of every layer, bit-exact FP64 rounding
- * (a1-a2).  d_cells: int32 [n_layers][B][2] = (k_u, k_v) per baseline, or
+ * (steps 1-2).  d_cells: int32 [n_layers][B][2] = (k_u, k_v) per baseline, or
  * (INT32_MIN, INT32_MIN) when the baseline falls outside |k| <= N/2-1 and is
  * not gridded.  vis_offset/out_offset of h_layers are ignored. */
 BLINK_API int blink_cells(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
                 int n_layers, int32_t *d_cells, void *stream);
 
-/* ------------------------------------------------------------ a1-a4 grid */
-/* Gridded, weighted visibilities of every layer (a1-a4), Hermitian-complete:
+/* ------------------------------------------------------------- grids */
+/* Gridded, weighted visibilities of every layer (steps 1-4), Hermitian-complete:
  * d_grid + out_offset holds complex64 [N][N] with zero spatial frequency at
  * (N/2, N/2) (Sec. 5.2.1 step 1).  d_wsum (float32 [n_layers], may be NULL)
  * receives each layer's summed weight.  d_vis holds the complex64 visibilities
@@ -131,8 +131,8 @@ BLINK_API int blink_cells(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, co
 BLINK_API int blink_grid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
                int n_layers, const float *d_vis, float *d_grid, float *d_wsum, void *stream);
 
-/* ----------------------------------------------------- a1-a7 dirty images */
-/* Dirty images of every layer (a1-a7): d_images + out_offset receives the
+/* ------------------------------------------------------- dirty images */
+/* Dirty images of every layer (steps 1-5): d_images + out_offset receives the
  * float32 [N][N] FFT-shifted real image, unnormalised unless flags has
  * BLINK_NORMALIZE.  d_wsum (float32 [n_layers], may be NULL) receives the
  * summed weights.  Layers of different sizes may be mixed.
@@ -188,7 +188,7 @@ BLINK_API int blink_image_batch_host(blink_ctx *ctx, const double *h_ant_xyz, in
                                      float *h_images, float *h_wsum, uint32_t flags, void *stream);
 
 /* ------------------------------------------------------------------ plans */
-/* A plan fixes the array and the layer descriptors, runs a1-a2 and the
+/* A plan fixes the array and the layer descriptors, runs steps 1-2 and the
  * weighting tables once (on `stream`, which it synchronises once), and keeps
  * them on the device.  blink_plan_image then only launches the gridding and
  * FFT kernels: it is asynchronous and may be captured in a CUDA graph.  The
@@ -274,7 +274,7 @@ BLINK_API int blink_plan_layer_info(const blink_plan *plan, int layer, float *ws
  * and forbids allocation (and its unpredictable latency) afterwards, or a
  * host framework whose own allocator already owns the whole device.
  *
- * Same result as blink_image_batch (a1-a7 on every layer), but it allocates
+ * Same result as blink_image_batch (steps 1-5 on every layer), but it allocates
  * nothing: no cudaMalloc, no cudaFree, no memory pool, no context.  All of
  * its scratch -- channel tables, layer descriptors and the row-transform
  * buffer of large images -- lives in one static device array of

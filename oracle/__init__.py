@@ -243,7 +243,7 @@ def image_batch(ant_xyz, layers, vis, mode: str = "fft", n_threads: int = 0, gai
 
 
 def image(ant_xyz, freq_hz, delta_u, n_px, weighting, vis, mode: str = "fft"):
-    """Convenience: one layer through a1..a7; returns (image, wsum, max|Im|)."""
+    """Convenience: one layer through the whole path; returns (image, wsum, max|Im|)."""
     u, v = uv(ant_xyz, freq_hz)
     ku, kv = cells(u, v, delta_u, n_px)
     g, _, ws = grid(ku, kv, vis, n_px, weighting)

@@ -8,25 +8,25 @@
  *
  * What it computes (paper: Sokolowski et al., "BLINK", arXiv 2405.13478):
  *
- *   a1  baseline (u,v) in wavelengths: difference of antenna positions divided
+ *   (1) baseline (u,v) in wavelengths: difference of antenna positions divided
  *       by lambda = c / nu, in FP64 (Sec. 5.2.1 step 1; the Fig. 7 listing
  *       computes the wavelength from the channel frequency in double).  The
  *       array is coplanar and phased at zenith, so w is dropped (Sec. 4.3,
  *       Eqs. 4-5).
- *   a2  grid cell: k = round(u / delta_u) with delta_u = 1/(N_px dx)
+ *   (2) grid cell: k = round(u / delta_u) with delta_u = 1/(N_px dx)
  *       (Sec. 4.4.1, Eq. 9); cells are indexed so that the centre bin is zero
  *       spatial frequency (Sec. 5.2.1 step 1).
- *   a3  gridding: every visibility is added to its cell and its Hermitian
+ *   (3) gridding: every visibility is added to its cell and its Hermitian
  *       conjugate to the mirrored cell, with a per-cell counter
  *       (Sec. 5.2.1 steps 2-3; the correlation matrix holds both V_ij and
  *       V_ji = conj(V_ij)).
- *   a4  weighting: natural = plain sum; uniform = each cell divided by its
+ *   (4) weighting: natural = plain sum; uniform = each cell divided by its
  *       count (Sec. 4.4.2; Sec. 5.2.1, weighting applied after gridding).
- *   a5-a7  dirty image = real part of the inverse 2-D Fourier transform of the
+ *   (5) dirty image = real part of the inverse 2-D Fourier transform of the
  *       gridded visibilities, with the FFT shifts that put the phase centre in
  *       the middle of the image (Sec. 4.3, Eq. 6; Sec. 5.2.2).
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - u = x_j - x_i for the pair (i < j), baselines in lexicographic order;
  *   - round half away from zero (C lround), so cell(-u) = -cell(u);
  *   - a cell is kept iff |k_u| <= N/2-1 and |k_v| <= N/2-1 (the -N/2 bin has
@@ -37,14 +37,14 @@
  *     weight;
  *   - image row y <-> m (v axis), column x <-> l (u axis), centre (N/2, N/2).
  *
- * Two independent evaluations of a5-a7 are provided: orc_image_direct (the
+ * Two independent evaluations of step 5 are provided: orc_image_direct (the
  * double sum of the definition over occupied cells, with exact integer phase
  * reduction) and orc_image_fft (an FP64 mixed-radix FFT, the way the paper
  * computes it).  Both are pinned in tests/ against closed forms, brute force
  * and numpy.fft.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC.
- * -ffp-contract=off keeps every a1/a2 operation a single IEEE rounding.
+ * -ffp-contract=off keeps every step 1-2 operation a single IEEE rounding.
  */
 #include <math.h>
 #include <stdint.h>
@@ -64,7 +64,7 @@ int64_t orc_n_baselines(int n_ant) {
     return (int64_t)n_ant * (int64_t)(n_ant - 1) / 2;
 }
 
-/* ---------------------------------------------------------------- a1: (u,v) */
+/* ----------------------------------------------------------- 1: (u,v) */
 /* ant_xyz: [n_ant][3] metres; u, v: [B] wavelengths, b over pairs (i<j). */
 void orc_uv(const double *ant_xyz, int n_ant, double freq_hz, double *u, double *v) {
     const double lambda = ORC_C_LIGHT / freq_hz;
@@ -80,7 +80,7 @@ void orc_uv(const double *ant_xyz, int n_ant, double freq_hz, double *u, double 
     }
 }
 
-/* ---------------------------------------------------------------- a2: cells */
+/* ----------------------------------------------------------- 2: cells */
 /* One axis: k = round-half-away(t), t = w / delta_u; returns 0 if dropped. */
 static int orc_axis_cell(double w, double delta_u, int n_px, int32_t *k) {
     const double t = w / delta_u;
@@ -111,7 +111,7 @@ int64_t orc_cells(const double *u, const double *v, int64_t nb, double delta_u, 
     return kept;
 }
 
-/* ------------------------------------------------------------ a3-a4: grid */
+/* ------------------------------------------------------- 3-4: grid */
 /* vis: [B] complex64 (re, im interleaved floats).
  * grid: [N][N] complex128 (re, im interleaved doubles), row y = k_v + N/2,
  *       column x = k_u + N/2 (zero spatial frequency in the centre bin).
@@ -190,7 +190,7 @@ static double *orc_twiddles(int n) {
     return tw;
 }
 
-/* ----------------------------------------------- a5-a7: direct definition */
+/* ------------------------------------------ 5: direct definition */
 /* image[py][px] = Re sum_k G[k] exp(+2 pi i (k_u (px - N/2) + k_v (py - N/2)) / N)
  * summed over every non-zero cell; the phase is reduced modulo N in integers
  * before the table lookup, so no large-argument trigonometry is involved.
@@ -299,7 +299,7 @@ int orc_fft1d(const double *in, int n, int sign, double *out) {
     return 0;
 }
 
-/* ------------------------------------------------- a5-a7: FFT with shifts */
+/* -------------------------------------------- 5: FFT with shifts */
 /* ifftshift (centre bin -> index 0), unnormalised inverse 2-D FFT, fftshift
  * (index 0 -> centre pixel), real part (Sec. 5.2.2). */
 int orc_image_fft(const double *grid, int n_px, double *image, double *max_abs_imag) {
@@ -351,8 +351,8 @@ int orc_image_fft(const double *grid, int n_px, double *image, double *max_abs_i
  * Sec. 5.2.1; w_b = 1 natural, 1/n(cell) uniform).  With R = dL/dI, the
  * gradient in the convention dL/dRe V + i dL/dIm V is
  *     gamma_b = 2 w_b H[k_b],  H[k] = sum_p R[p] exp(-2 pi i k.(p - N/2) / N),
- * and zero for baselines that are not gridded.  This reading of the
- * "differentiation" extension is listed in the design doc. */
+ * and zero for baselines that are not gridded (the paper does not
+ * differentiate the imager; this is the adjoint of the map above). */
 static int orc_entry_weights(const int32_t *ku, const int32_t *kv, int64_t nb, int n_px,
                              int weighting, double *w) {
     const int h = n_px / 2;

@@ -239,14 +239,14 @@ class Context:
             raise BlinkError(st, self._lib.blink_last_error(self.handle).decode())
 
     def cells(self, ant_xyz, layers, cells_out, stream=None):
-        """a1-a2: int32 [n_layers][B][2] cell indices."""
+        """Cell indices: int32 [n_layers][B][2]."""
         _check_dev(ant_xyz, cells_out)
         arr = make_layers(layers)
         self._raise(self._lib.blink_cells(self.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
                                           len(layers), _ptr(cells_out), _stream(stream)))
 
     def grid(self, ant_xyz, layers, vis, grid_out, wsum_out=None, stream=None):
-        """a1-a4: complex64 Hermitian-complete grids (DC at N/2, N/2)."""
+        """Gridded, weighted visibilities: complex64 Hermitian-complete grids (DC at N/2, N/2)."""
         _check_dev(ant_xyz, vis, grid_out, wsum_out)
         arr = make_layers(layers)
         self._raise(self._lib.blink_grid(self.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
@@ -254,7 +254,7 @@ class Context:
                                          _stream(stream)))
 
     def image_batch(self, ant_xyz, layers, vis, images_out, wsum_out=None, flags=0, stream=None):
-        """a1-a7: float32 dirty images."""
+        """Float32 dirty images (the whole path)."""
         _check_dev(ant_xyz, vis, images_out, wsum_out)
         arr = make_layers(layers)
         self._raise(self._lib.blink_image_batch(self.handle, _ptr(ant_xyz), ant_xyz.shape[0], arr,
@@ -263,7 +263,7 @@ class Context:
 
     def image_batch_host(self, ant_xyz, layers, vis, images_out, wsum_out=None, flags=0,
                          stream=None):
-        """a1-a7 with host-resident inputs and outputs (numpy arrays or CPU
+        """The whole path with host-resident inputs and outputs (numpy arrays or CPU
         tensors; pinned memory gives full copy bandwidth)."""
         import numpy as np
 
@@ -313,7 +313,7 @@ class Context:
 
 
 class Plan:
-    """Tables built once (a1-a2, weights); image() launches a3-a7 only."""
+    """Tables built once (uv, cells, weights); image() launches gridding + transform only."""
 
     def __init__(self, ctx: Context, ant_xyz, layers, stream=None):
         _check_dev(ant_xyz)

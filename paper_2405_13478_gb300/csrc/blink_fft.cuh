@@ -1,6 +1,6 @@
 // blink_fft.cuh -- in-register DFT codelets and four-step size plans.
 //
-// The inverse 2-D transform of a5-a7 (Sec. 5.2.2) is done as two batches of
+// The inverse 2-D transform of the imager (Sec. 5.2.2) is done as two batches of
 // 1-D transforms.  A 1-D transform of length N = N1 * N2 is split four-step
 // (Cooley-Tukey with one twiddle stage): N2 transforms of length N1 along
 // stride N2, a twiddle multiply by W_N^(n2 k1), then N1 transforms of length

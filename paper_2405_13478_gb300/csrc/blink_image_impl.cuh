@@ -262,7 +262,7 @@ __device__ __forceinline__ void grid_rows(float2 *G, int S, int r0, int nrows, c
 }
 
 // ------------------------------------------------------------- small path
-// One CTA per layer; every step of a1..a7 after the tables happens in shared
+// One CTA per layer; every step after the tables happens in shared
 // memory.  Thread layout: 16-lane groups.  In the four-step A steps a lane is
 // n2 (its twiddles W_N^(n2 k1) live in registers for the whole kernel) and a
 // group is a row (pass 1) or a column pair (pass 2); in pass-1 step B a lane

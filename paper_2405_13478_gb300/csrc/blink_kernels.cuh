@@ -5,7 +5,7 @@
 
 namespace blink {
 
-// a1-a2 and weighting tables for n_chan channels (blink_tables.cu).
+// uv, cells and weighting tables for n_chan channels (blink_tables.cu).
 // info[] must hold n_px, weighting, code_off, wgt_off, the schedule fields
 // and zeroed accumulators; channels with wgt_off >= 0 must have (N/2)*N
 // zeroed int32 counts at wgt + wgt_off (they become 1/n weights for uniform

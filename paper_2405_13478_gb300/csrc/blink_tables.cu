@@ -1,4 +1,4 @@
-// blink_tables.cu -- a1/a2 (baseline uv, grid cell) and the weighting tables.
+// blink_tables.cu -- baseline uv, grid cell and the weighting tables.
 //
 // One table set per channel: a coplanar, zenith-phased array has (u,v) that
 // do not change with time (Sec. 4.3, Eqs. 4-5), so every time step of a
@@ -11,7 +11,7 @@
 
 namespace blink {
 
-// One axis of a2: k = round half away from zero of (w / delta_u); false if the
+// One axis of the cell assignment: k = round half away from zero of (w / delta_u); false if the
 // baseline leaves the grid (|k| > N/2 - 1) or is not finite.
 __device__ __forceinline__ bool axis_cell(double w, double delta_u, int n_px, int &k) {
     const double t = __ddiv_rn(w, delta_u);
@@ -23,7 +23,7 @@ __device__ __forceinline__ bool axis_cell(double w, double delta_u, int n_px, in
     return true;
 }
 
-// a1 + a2 for every (channel, baseline).  Grid: (ceil(B / blockDim), n_chan).
+// uv and cell for every (channel, baseline).  Grid: (ceil(B / blockDim), n_chan).
 // Writes the packed canonical cell, optionally the signed cell pair, counts
 // the entries of uniform-weighted channels and reduces the support bounds.
 __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t nb,

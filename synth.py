@@ -220,26 +220,26 @@ def _du_fill(ant_xyz, f_top, n_px):
     return max_uv(ant_xyz, f_top) / (n_px / 2 - 1)
 
 
-def config1(seed=0) -> Workload:
+def single_image(seed=0) -> Workload:
     """One 256^2 natural-weighted image of a 128-antenna 3 km array at 160 MHz."""
     xyz = antennas_disk(128, 3000.0, seed)
     f = np.array([160e6])
     n = np.array([256])
     sky = sky_box(3, 0.5, [1.0, 0.5, 0.2], seed)
-    return Workload("cfg1_single_256", xyz, f, 1, n,
+    return Workload("single_image_256", xyz, f, 1, n,
                     np.array([_du_fill(xyz, f.max(), 256)]), NATURAL, 0.1, sky, seed)
 
 
-def config2(seed=0, n_times=1000) -> Workload:
+def station_batch(seed=0, n_times=1000) -> Workload:
     """Station, 1000 steps x 32 channels, 180^2 all-sky, uniform weighting."""
     xyz = antennas_disk(256, 38.0, seed)
     f = _uniform_channels(150e6, 180e6, 32)
     sky = sky_disk_loguniform(20, 1.0, 1.0, 10.0, seed)
-    return Workload("cfg2_station_180", xyz, f, n_times, np.full(32, 180),
+    return Workload("station_batch_180", xyz, f, n_times, np.full(32, 180),
                     np.full(32, 0.5), UNIFORM, 1.0, sky, seed)
 
 
-def config3(seed=0, n_times=100) -> Workload:
+def uneven_batch(seed=0, n_times=100) -> Workload:
     """128-antenna 3 km array, 768 channels, sizes 128..1024 by channel group."""
     xyz = antennas_disk(128, 3000.0, seed)
     f = _uniform_channels(150e6, 180e6, 768)
@@ -247,21 +247,21 @@ def config3(seed=0, n_times=100) -> Workload:
     du = np.array([_du_fill(xyz, f.max(), int(n)) for n in sizes])
     sky = sky_box(1, 0.5, [5.0], seed)
     pulse = dict(flux=5.0, dm=100.0, t0=20, dt_s=0.1)
-    w = Workload("cfg3_uneven_pulse", xyz, f, n_times, sizes, du, NATURAL, 1.0, sky, seed,
+    w = Workload("uneven_batch_pulse", xyz, f, n_times, sizes, du, NATURAL, 1.0, sky, seed,
                  pulse=pulse)
     return w
 
 
-def config4(seed=0, n_times=2000) -> Workload:
+def station_512(seed=0, n_times=2000) -> Workload:
     """Station, 512^2 images, 2000 steps x 16 channels, 50 sources over 1e-3..10 Jy."""
     xyz = antennas_disk(256, 38.0, seed)
     f = _uniform_channels(150e6, 180e6, 16)
     sky = sky_disk_loguniform(50, 1.0, 1e-3, 10.0, seed)
-    return Workload("cfg4_station_512", xyz, f, n_times, np.full(16, 512), np.full(16, 0.5),
+    return Workload("station_512", xyz, f, n_times, np.full(16, 512), np.full(16, 0.5),
                     NATURAL, 0.1, sky, seed)
 
 
-def config5(seed=0, n_times=100) -> Workload:
+def station_gains(seed=0, n_times=100) -> Workload:
     """Station, 1024^2 images, 100 steps x 8 channels, gain-corrupted model."""
     xyz = antennas_disk(256, 38.0, seed)
     f = _uniform_channels(150e6, 180e6, 8)
@@ -270,8 +270,9 @@ def config5(seed=0, n_times=100) -> Workload:
     amp = np.abs(rng.normal(1.0, 0.1, 256))
     ph = rng.uniform(-math.pi, math.pi, 256)
     g = amp * np.exp(1j * ph)
-    return Workload("cfg5_station_1024_gains", xyz, f, n_times, np.full(8, 1024),
+    return Workload("station_gains_1024", xyz, f, n_times, np.full(8, 1024),
                     np.full(8, 0.5), NATURAL, 0.0, sky, seed, gains=g)
 
 
-CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
+WORKLOADS = {"single_image": single_image, "station_batch": station_batch,
+             "uneven_batch": uneven_batch, "station_512": station_512, "station_gains": station_gains}

@@ -51,7 +51,7 @@ def run_degrid(torch, ctx, xyz, layers, resid_list, nb, flags=0):
 @pytest.mark.parametrize("n_px", [16, 20, 128, 180, 256, 512, 1024])
 @pytest.mark.parametrize("weighting", [0, 1])
 def test_degrid_matches_oracle(torch, ctx, n_px, weighting):
-    ws = synth.config1(seed=n_px + 7)
+    ws = synth.single_image(seed=n_px + 7)
     du = synth.max_uv(ws.ant_xyz, ws.freqs_hz[0]) / (n_px / 2 - 1)
     if n_px <= 20:
         du *= 3.0  # also exercise dropped baselines
@@ -68,7 +68,7 @@ def test_degrid_matches_oracle(torch, ctx, n_px, weighting):
 
 
 def test_degrid_station_layers_and_normalize(torch, ctx):
-    ws = synth.config5(seed=3, n_times=1)
+    ws = synth.station_gains(seed=3, n_times=1)
     layers = [dict(n_px=1024, weighting=0, freq_hz=float(f), delta_u=0.5, vis_offset=0)
               for f in ws.freqs_hz[[0, 7]]]
     layers += [dict(n_px=180, weighting=1, freq_hz=float(ws.freqs_hz[3]), delta_u=0.5,
@@ -89,7 +89,7 @@ def test_degrid_station_layers_and_normalize(torch, ctx):
 
 def test_adjoint_identity_on_gpu(torch, ctx):
     from paper_2405_13478_gb300 import binding
-    ws = synth.config2(seed=4, n_times=1)
+    ws = synth.station_batch(seed=4, n_times=1)
     B = ws.n_baselines
     layers = [dict(n_px=180, weighting=w, freq_hz=float(ws.freqs_hz[c]), delta_u=0.5,
                    vis_offset=k * B) for k, (c, w) in enumerate(((0, 1), (31, 0)))]
@@ -107,12 +107,12 @@ def test_adjoint_identity_on_gpu(torch, ctx):
     assert abs(lhs - rhs) <= 1e-5 * scale
 
 
-def test_autograd_gains_config5_slice(torch, ctx):
-    """Config-5 form: V = g_i conj(g_j) M, loss = sum (image(V) - image(M))^2;
+def test_autograd_gains_station_gains_slice(torch, ctx):
+    """station-gains form: V = g_i conj(g_j) M, loss = sum (image(V) - image(M))^2;
     gradients w.r.t. V and g from torch.autograd (library kernels) against
     the CPU reference gradient of the oracle."""
     from paper_2405_13478_gb300 import autograd, binding
-    ws = synth.config5(seed=11, n_times=1)
+    ws = synth.station_gains(seed=11, n_times=1)
     B, n_ant = ws.n_baselines, ws.n_ant
     chans = [0, 5]
     model = torch.as_tensor(synth.model_vis(ws.ant_xyz, ws.freqs_hz[chans], ws.sky)

@@ -26,7 +26,7 @@ def env():
     from paper_2405_13478_gb300 import binding, build
     build.build()
     ctx = binding.Context(0)
-    ws = synth.config4(seed=17, n_times=3)
+    ws = synth.station_512(seed=17, n_times=3)
     chans = [0, 7, 15]
     vis = ws.vis("cpu")[:, chans, :].contiguous()
     layers = []

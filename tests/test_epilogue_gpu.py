@@ -46,7 +46,7 @@ def check(got_flat, want, ref_flat, layers, tol=TOL, what=""):
 
 
 def station_case(seed, sizes, weighting=1):
-    ws = synth.config2(seed=seed, n_times=1)
+    ws = synth.station_batch(seed=seed, n_times=1)
     nb = ws.n_baselines
     layers = []
     for k, n in enumerate(sizes):
@@ -102,7 +102,7 @@ def test_gains_and_reference_large_sizes(torch, ctx):
     """Two-kernel path (512, 1024); shared gains (stride 0), natural weighting."""
     flags = 0
     from paper_2405_13478_gb300 import binding
-    ws = synth.config3(seed=12, n_times=30)
+    ws = synth.uneven_batch(seed=12, n_times=30)
     chans = [200, 300, 210]   # 512, 1024, 512
     vis = ws.vis("cpu", times=[20])[0, chans, :].contiguous()
     layers = [dict(n_px=int(ws.n_px[c]), weighting=0, freq_hz=float(ws.freqs_hz[c]),
@@ -192,7 +192,7 @@ def test_gains_and_reference_tensor_core_transform(torch, ctx, flags, tol):
     """Station 512^2 layers through the DFT-GEMM (BF16x3, FP16): the reference
     is subtracted in the TMEM epilogue, the gains in the row pass."""
     from paper_2405_13478_gb300 import binding
-    ws = synth.config4(seed=5, n_times=1)
+    ws = synth.station_512(seed=5, n_times=1)
     chans = [0, 9, 15]
     vis = ws.vis("cpu", times=[0])[0, chans, :].contiguous()
     layers = [dict(n_px=512, weighting=0, freq_hz=float(ws.freqs_hz[c]), delta_u=0.5,
@@ -211,7 +211,7 @@ def test_per_channel_gains_with_period(torch, ctx):
     """Time-major layers (2 steps x 3 channels) with one gain row per channel:
     gain_period = 3 wraps the rows over the time steps."""
     from paper_2405_13478_gb300 import binding
-    ws = synth.config2(seed=37, n_times=2)
+    ws = synth.station_batch(seed=37, n_times=2)
     chans = [0, 11, 31]
     vis = ws.vis("cpu", times=[0, 1])[:, chans, :].contiguous().reshape(-1)
     layers = [dict(n_px=180, weighting=1, freq_hz=float(ws.freqs_hz[c]), delta_u=0.5,

@@ -60,8 +60,8 @@ def assert_close(got, want, what=""):
 
 
 def small_size_workload(seed):
-    """A station of config-2 shape imaged at every small size, both weightings."""
-    ws = synth.config2(seed=seed, n_times=2)
+    """A station of station-batch shape imaged at every small size, both weightings."""
+    ws = synth.station_batch(seed=seed, n_times=2)
     sizes = [16, 20, 64, 128, 180, 256]
     layers = []
     for k, n in enumerate(sizes):
@@ -102,7 +102,7 @@ def test_every_kernel_path_matches_oracle_small_sizes(torch, ctx, path):
 
 @pytest.mark.parametrize("wave_mb", [1, 12, 96])
 def test_wave_budgets_match_oracle_large_sizes(torch, ctx, wave_mb):
-    ws = synth.config3(seed=8, n_times=30)
+    ws = synth.uneven_batch(seed=8, n_times=30)
     layers, total, vis = mixed_layers(ws, [20, 21], [200, 300, 767])   # 512, 1024, 1024
     plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
     for g, _ in enumerate(plan.tuning()):
@@ -117,7 +117,7 @@ def test_wave_budgets_match_oracle_large_sizes(torch, ctx, wave_mb):
 
 def test_unavailable_paths_are_rejected(torch, ctx):
     from paper_2405_13478_gb300 import binding
-    ws = synth.config3(seed=8, n_times=30)
+    ws = synth.uneven_batch(seed=8, n_times=30)
     layers, total, vis = mixed_layers(ws, [20], [0, 300])   # 128, 1024
     plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
     assert [t[0] for t in plan.tuning()] == [128, 1024]
@@ -130,7 +130,7 @@ def test_unavailable_paths_are_rejected(torch, ctx):
 
 
 def test_autotune_choice_keeps_parity(torch, ctx):
-    ws = synth.config3(seed=9, n_times=30)
+    ws = synth.uneven_batch(seed=9, n_times=30)
     layers, total, vis = mixed_layers(ws, [20, 25], [0, 100, 200, 300, 767])
     plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
     d_vis = vis.reshape(-1).cuda()
@@ -149,7 +149,7 @@ def test_autotune_choice_keeps_parity(torch, ctx):
 
 @pytest.mark.parametrize("flags", [0, 1])
 def test_graph_replay_tracks_new_visibilities(torch, ctx, flags):
-    ws = synth.config3(seed=10, n_times=30)
+    ws = synth.uneven_batch(seed=10, n_times=30)
     layers, total, vis_a = mixed_layers(ws, [20], [0, 100, 200, 300])
     _, _, vis_b = mixed_layers(ws, [25], [0, 100, 200, 300])
     plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
@@ -174,7 +174,7 @@ def test_graph_replay_tracks_new_visibilities(torch, ctx, flags):
 
 def test_graph_of_tensor_core_mode(torch, ctx):
     from paper_2405_13478_gb300 import binding
-    ws = synth.config4(seed=3, n_times=1)
+    ws = synth.station_512(seed=3, n_times=1)
     layers = [dict(n_px=512, weighting=0, freq_hz=float(ws.freqs_hz[c]), delta_u=0.5,
                    vis_offset=c * ws.n_baselines) for c in range(4)]
     layers, total = binding.layer_out_offsets(layers)
@@ -195,7 +195,7 @@ def test_graph_of_tensor_core_mode(torch, ctx):
 
 def test_replay_without_capture_is_an_error(torch, ctx):
     from paper_2405_13478_gb300 import binding
-    ws = synth.config1(seed=1)
+    ws = synth.single_image(seed=1)
     layers = [dict(n_px=256, weighting=0, freq_hz=float(ws.freqs_hz[0]),
                    delta_u=float(ws.delta_u[0]), vis_offset=0)]
     plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)

@@ -105,7 +105,7 @@ def test_visibility_gradient_matches_finite_differences(weighting):
 
 
 def test_gain_gradient_matches_finite_differences():
-    # V_ij = g_i conj(g_j) M_ij; loss = sum (image - model image)^2 (config-5 form)
+    # V_ij = g_i conj(g_j) M_ij; loss = sum (image - model image)^2 (station-gains form)
     n_px, n_ant = 16, 8
     xyz = small_array(n_ant, 5)
     u, v = oracle.uv(xyz, NU)

@@ -31,7 +31,7 @@ def brute_pairs(n_ant):
     return [(i, j) for i in range(n_ant) for j in range(i + 1, n_ant)]
 
 
-# ----------------------------------------------------------------- a1 / a2
+# ------------------------------------------------------ uv and cells
 def test_lambda_is_exact():
     assert C / NU_LAMBDA2 == 2.0
 
@@ -90,7 +90,7 @@ def test_cells_mirror_symmetry():
     assert np.array_equal(kur[~keep], ku[~keep])
 
 
-# ----------------------------------------------------------------- a3 / a4
+# -------------------------------------------------- grid and weights
 def tiny_case(n_ant=6, n_px=16, seed=5, lo=-6, hi=7):
     xyz = int_array(n_ant, lo, hi, seed)
     u, v = oracle.uv(xyz, NU_LAMBDA2)
@@ -147,7 +147,7 @@ def test_grid_is_hermitian():
         assert not g[0, :].any() and not g[:, 0].any()  # the -N/2 bins stay empty
 
 
-# ----------------------------------------------------------------- a5 - a7
+# ------------------------------------------------------------ image
 def direct_baseline_sum(u, v, vis, weights, delta_u, n_px):
     """sum_b w_b 2 Re(V_b exp(+2 pi i (u_b l + v_b m))) on the pixel grid."""
     p = (np.arange(n_px) - n_px // 2) / (n_px * delta_u)

@@ -75,7 +75,7 @@ def ws_sub(ws: synth.Workload, times, chans):
     return layers, vis.contiguous()
 
 
-# ----------------------------------------------------------------- a1 / a2
+# ------------------------------------------------------ uv and cells
 def gpu_cells(torch, ctx, xyz, layers, nb):
     d = torch.empty((len(layers), nb, 2), dtype=torch.int32, device="cuda")
     ctx.cells(to_dev(torch, xyz), layers, d)
@@ -83,9 +83,9 @@ def gpu_cells(torch, ctx, xyz, layers, nb):
     return d.cpu().numpy()
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
-def test_cells_bit_exact_on_every_config(torch, ctx, cfg):
-    ws = synth.CONFIGS[cfg](seed=cfg)
+@pytest.mark.parametrize("seed,name", list(enumerate(synth.WORKLOADS, start=1)))
+def test_cells_bit_exact_on_every_workload(torch, ctx, seed, name):
+    ws = synth.WORKLOADS[name](seed=seed)
     chans = sorted(set([0, ws.n_chan // 2, ws.n_chan - 1] + list(range(0, ws.n_chan, 97))))
     layers = [dict(n_px=int(ws.n_px[c]), weighting=ws.weighting, freq_hz=float(ws.freqs_hz[c]),
                    delta_u=float(ws.delta_u[c]), vis_offset=0) for c in chans]
@@ -93,7 +93,7 @@ def test_cells_bit_exact_on_every_config(torch, ctx, cfg):
     for k, L in enumerate(layers):
         u, v = oracle.uv(ws.ant_xyz, L["freq_hz"])
         ku, kv = oracle.cells(u, v, L["delta_u"], L["n_px"])
-        assert np.array_equal(got[k, :, 0], ku) and np.array_equal(got[k, :, 1], kv), (cfg, k)
+        assert np.array_equal(got[k, :, 0], ku) and np.array_equal(got[k, :, 1], kv), (name, k)
 
 
 def test_cells_ties_and_edges_bit_exact(torch, ctx):
@@ -118,7 +118,7 @@ def test_cells_ties_and_edges_bit_exact(torch, ctx):
     assert dropped > 0 and kept > 0  # both sides of the edge rule were exercised
 
 
-# ------------------------------------------------------------------- a3 / a4
+# -------------------------------------------------- grid and weights
 def gpu_grids(torch, ctx, xyz, layers, vis_cpu):
     out_layers, off = [], 0
     for L in layers:
@@ -142,9 +142,9 @@ def test_grid_matches_oracle(torch, ctx, weighting, n_px):
     # some order, so |error| <= (n - 1) u sum|V| (u = 2^-24) before the
     # weight, plus one rounding for the weight and one for the origin doubling.
     if n_px == 256:
-        ws, times, chans = synth.config1(seed=3), [0], [0]
+        ws, times, chans = synth.single_image(seed=3), [0], [0]
     else:
-        ws, times, chans = synth.config2(seed=3, n_times=2), [0, 1], [0, 31]
+        ws, times, chans = synth.station_batch(seed=3, n_times=2), [0, 1], [0, 31]
     ws.weighting = weighting
     ws.n_px = np.full(ws.n_chan, n_px)
     if n_px == 16:
@@ -172,7 +172,7 @@ def test_images_match_oracle_across_sizes(torch, ctx, n_px, weighting):
     # A 3 km array with the cell size filling the grid: every support row is
     # populated, so both the fused path (small N) and the row/column path
     # (large N) run with several tiles and ragged tails.
-    ws = synth.config1(seed=n_px)
+    ws = synth.single_image(seed=n_px)
     ws.weighting = weighting
     ws.n_px = np.array([n_px])
     ws.delta_u = np.array([synth.max_uv(ws.ant_xyz, ws.freqs_hz[0]) / (n_px / 2 - 1)])
@@ -183,52 +183,52 @@ def test_images_match_oracle_across_sizes(torch, ctx, n_px, weighting):
     assert np.allclose(wsum, wref, rtol=1e-7)
 
 
-def test_config2_slice_uniform_180(torch, ctx):
-    ws = synth.config2(seed=11, n_times=3)
+def test_station_batch_slice_uniform_180(torch, ctx):
+    ws = synth.station_batch(seed=11, n_times=3)
     layers, vis = ws_sub(ws, [0, 2], list(range(32)))
     got, wsum = gpu_images(torch, ctx, ws.ant_xyz, layers, vis)
     want, wref = oracle_images(ws.ant_xyz, layers, vis)
-    assert_images_close(got, want, what="cfg2")
+    assert_images_close(got, want, what="station")
     assert np.allclose(wsum, wref, rtol=1e-7)
 
 
-def test_config1_single_256(torch, ctx):
-    ws = synth.config1(seed=0)
+def test_single_image_single_256(torch, ctx):
+    ws = synth.single_image(seed=0)
     layers, vis = ws_sub(ws, [0], [0])
     got, _ = gpu_images(torch, ctx, ws.ant_xyz, layers, vis)
     want, _ = oracle_images(ws.ant_xyz, layers, vis)
-    assert_images_close(got, want, what="cfg1")
+    assert_images_close(got, want, what="single")
 
 
-def test_config3_mixed_sizes_in_one_call(torch, ctx):
-    ws = synth.config3(seed=5, n_times=30)
+def test_uneven_batch_mixed_sizes_in_one_call(torch, ctx):
+    ws = synth.uneven_batch(seed=5, n_times=30)
     chans = [0, 100, 200, 300, 767]          # sizes 128, 256, 512, 1024, 1024
     layers, vis = ws_sub(ws, [20, 25], chans)
     got, _ = gpu_images(torch, ctx, ws.ant_xyz, layers, vis)
     want, _ = oracle_images(ws.ant_xyz, layers, vis)
-    assert_images_close(got, want, what="cfg3")
+    assert_images_close(got, want, what="uneven")
 
 
-def test_config4_station_512(torch, ctx):
-    ws = synth.config4(seed=7, n_times=2)
+def test_station_512_station_512(torch, ctx):
+    ws = synth.station_512(seed=7, n_times=2)
     layers, vis = ws_sub(ws, [1], [0, 15])
     got, _ = gpu_images(torch, ctx, ws.ant_xyz, layers, vis)
     want, _ = oracle_images(ws.ant_xyz, layers, vis)
-    assert_images_close(got, want, what="cfg4")
+    assert_images_close(got, want, what="station512")
 
 
-def test_config5_station_1024_gains(torch, ctx):
-    ws = synth.config5(seed=9, n_times=1)
+def test_station_gains_station_1024_gains(torch, ctx):
+    ws = synth.station_gains(seed=9, n_times=1)
     layers, vis = ws_sub(ws, [0], [3])
     got, _ = gpu_images(torch, ctx, ws.ant_xyz, layers, vis)
     want, _ = oracle_images(ws.ant_xyz, layers, vis)
-    assert_images_close(got, want, what="cfg5")
+    assert_images_close(got, want, what="gains")
 
 
 # ----------------------------------------------------------- edge cases
 @pytest.mark.parametrize("weighting", [0, 1])
 def test_unit_source_at_centre_gives_summed_weight_on_gpu(torch, ctx, weighting):
-    ws = synth.config2(seed=2, n_times=1)
+    ws = synth.station_batch(seed=2, n_times=1)
     B = ws.n_baselines
     layers = [dict(n_px=180, weighting=weighting, freq_hz=float(f), delta_u=0.5,
                    vis_offset=k * B) for k, f in enumerate(ws.freqs_hz[:4])]
@@ -256,7 +256,7 @@ def test_ragged_baselines_and_unaligned_offsets(torch, ctx):
 
 
 def test_normalize_flag(torch, ctx):
-    ws = synth.config2(seed=8, n_times=1)
+    ws = synth.station_batch(seed=8, n_times=1)
     layers, vis = ws_sub(ws, [0], [0, 31])
     raw, wsum = gpu_images(torch, ctx, ws.ant_xyz, layers, vis)
     norm, _ = gpu_images(torch, ctx, ws.ant_xyz, layers, vis, flags=1)
@@ -265,7 +265,7 @@ def test_normalize_flag(torch, ctx):
 
 
 def test_all_baselines_dropped_gives_zero_image(torch, ctx):
-    ws = synth.config1(seed=1)
+    ws = synth.single_image(seed=1)
     # a cell far smaller than any baseline puts every baseline off the grid
     layers = [dict(n_px=16, weighting=1, freq_hz=160e6, delta_u=1e-9, vis_offset=0)]
     import torch as t
@@ -305,7 +305,7 @@ def test_invalid_arguments_are_rejected(torch, ctx):
 
 def test_plan_reuse_matches_batch(torch, ctx):
     from paper_2405_13478_gb300 import binding
-    ws = synth.config2(seed=12, n_times=2)
+    ws = synth.station_batch(seed=12, n_times=2)
     layers, vis = ws_sub(ws, [0, 1], list(range(0, 32, 5)))
     layers, total = binding.layer_out_offsets(layers)
     d_xyz = to_dev(torch, ws.ant_xyz)
@@ -330,7 +330,7 @@ def test_host_buffer_path_matches_device_path(torch, ctx):
     """blink_image_batch_host: host inputs and outputs, several pipeline
     chunks (the 512 MB staging limit is crossed), mixed sizes in a chunk."""
     from paper_2405_13478_gb300 import binding
-    ws = synth.config2(seed=15, n_times=70)          # 2240 layers, 585 MB of visibilities
+    ws = synth.station_batch(seed=15, n_times=70)          # 2240 layers, 585 MB of visibilities
     vis = ws.vis("cpu")
     layers = ws.layers()
     layers[5] = dict(layers[5], n_px=256, delta_u=0.3, weighting=0)
@@ -351,12 +351,12 @@ def test_host_buffer_path_matches_device_path(torch, ctx):
 
 
 # ------------------------------------------------- full bench configuration
-def test_config2_full_batch_sampled_layers(torch, ctx):
+def test_station_batch_full_batch_sampled_layers(torch, ctx):
     """The bench workload (32000 layers of 180^2, uniform) in one call;
     sampled layers against the oracle, every layer checked for finiteness and
     for the summed-weight identity of its channel."""
     from paper_2405_13478_gb300 import binding
-    ws = synth.config2(seed=0)
+    ws = synth.station_batch(seed=0)
     vis = ws.vis("cuda")                       # [1000][32][32640] complex64 on the GPU
     layers = ws.layers()
     layers, total = binding.layer_out_offsets(layers)
@@ -374,7 +374,7 @@ def test_config2_full_batch_sampled_layers(torch, ctx):
     o = out.cpu().numpy()
     got = [o[layers[k]["out_offset"]:layers[k]["out_offset"] + 180 * 180].reshape(180, 180)
            for k in pick]
-    assert_images_close(got, want, what="cfg2-full")
+    assert_images_close(got, want, what="station-full")
     w = wsum.cpu().numpy()
     assert np.allclose(w[pick], wref, rtol=1e-7)
     # summed weight depends only on the channel
@@ -387,7 +387,7 @@ def test_scheduled_gridding_is_bit_reproducible(torch, ctx):
     # gridding: every cell sums its visibilities in a fixed order, so two runs
     # give the same bits.
     from paper_2405_13478_gb300 import binding
-    ws = synth.config2(seed=14, n_times=2)
+    ws = synth.station_batch(seed=14, n_times=2)
     layers, vis = ws_sub(ws, [0, 1], list(range(0, 32, 3)))
     layers, total = binding.layer_out_offsets(layers)
     d_xyz = to_dev(torch, ws.ant_xyz)

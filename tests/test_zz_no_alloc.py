@@ -85,9 +85,9 @@ def workload(env, ws, times, chans):
 
 def test_noalloc_matches_image_batch_two_calls_in_a_row(env):
     # call 1: 96 uniform-weighted 180^2 layers over 32 channels (fused path)
-    a = workload(env, synth.config2(seed=21, n_times=3), [0, 1, 2], list(range(32)))
+    a = workload(env, synth.station_batch(seed=21, n_times=3), [0, 1, 2], list(range(32)))
     # call 2: 1024^2 natural layers of a 3 km array (row/column path with scratch rows)
-    w2 = synth.config1(seed=22)
+    w2 = synth.single_image(seed=22)
     w2.n_px = np.array([1024])
     w2.delta_u = np.array([synth.max_uv(w2.ant_xyz, w2.freqs_hz[0]) / 511])
     b = workload(env, w2, [0], [0])
@@ -101,7 +101,7 @@ def test_noalloc_matches_image_batch_two_calls_in_a_row(env):
 
 def test_noalloc_rejects_requests_beyond_its_limits(env):
     torch, binding, _, _ = env
-    ws = synth.config2(seed=23, n_times=1)
+    ws = synth.station_batch(seed=23, n_times=1)
     xyz = torch.as_tensor(ws.ant_xyz).cuda()
     vis = torch.zeros(ws.n_baselines, dtype=torch.complex64, device="cuda")
     # more distinct channels than the static limit
