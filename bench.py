@@ -59,6 +59,55 @@ def dist():
     return rank, world, local
 
 
+# ---------------------------------------------------------------- replicas
+# The path shards by layers: every rank images its own batch (its own time
+# steps), there is no data-path collective, and the only cross-rank traffic is
+# the barrier and the max-over-ranks of the timed interval (weak scaling).
+STATION_WORKLOAD = ("station: 256 antennas in a 38 m disk, 32640 baselines, 1000 time steps x "
+                    "32 channels (150-180 MHz), 180^2 all-sky images, uniform weighting, "
+                    "20 sources + sigma=1 noise")
+
+
+def init_replicas(backend: str):
+    """(rank, world, local_rank, process group module or None).  The group is
+    created only when WORLD_SIZE > 1 (torchrun sets RANK/WORLD_SIZE/MASTER_*)."""
+    rank, world, local = dist()
+    if world == 1:
+        return rank, world, local, None
+    import torch
+    import torch.distributed as tdist
+
+    if backend == "nccl":
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        tdist.init_process_group(backend)
+    return rank, world, local, tdist
+
+
+def max_over_ranks(value: float, pg, device) -> float:
+    """The slowest rank's value (the whole job ends when it does)."""
+    if pg is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, ms: float) -> float:
+    """Units per second over all ranks for `steps` steps of `ms` (max over ranks)."""
+    return world * units_per_rank * steps / (ms / 1e3)
+
+
+def rank_workload(rank: int, n_times: int):
+    """Rank `rank`'s own station batch: same shape on every rank, independent
+    data (seeded by the rank)."""
+    import synth
+
+    return synth.station_batch(seed=rank, n_times=n_times)
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in sorted(os.listdir(CSRC)):
@@ -283,7 +332,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "station 256 ant, 32640 baselines, 1000 x 32 ch, 180^2, uniform",
+        "config": {"workload": STATION_WORKLOAD, "layers_per_gpu": 32000, "n_px": 180,
+                   "baselines": ws.n_baselines,
+                   "parallelism": f"replicas x{world} (rank 0 times the oracle)",
                    "sample_layers_per_step": len(layers)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -300,11 +351,7 @@ def run_ours(args):
 
     rank, world, local = dist()
     torch.cuda.set_device(local)
-    pg = None
-    if world > 1:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        pg = tdist
+    rank, world, local, pg = init_replicas("nccl")
     if rank == 0:
         build.build()
     if pg:
@@ -312,7 +359,7 @@ def run_ours(args):
     lib = binding.lib()  # noqa: F841  (fails loudly when the library is missing)
 
     # Each rank images its own 1000 x 32 batch (weak scaling, no data-path collective).
-    ws = synth.station_batch(seed=rank, n_times=args.n_times or 1000)
+    ws = rank_workload(rank, args.n_times or 1000)
     layers = ws.layers()
     L = len(layers)
     B = ws.n_baselines
@@ -357,13 +404,9 @@ def run_ours(args):
     if pg:
         pg.barrier()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(t0.elapsed_time(t1), pg, "cuda")
     kern_ms = [a.elapsed_time(b) for a, b in kev]
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * L * args.steps / (ms / 1e3)
+    value = whole_job_rate(L, world, args.steps, ms)
     err = sampled_error(ctx, ws, d_xyz, vis, images, layers) if rank == 0 else None
     variants = None
     if rank == 0 and not args.no_variants:
@@ -383,12 +426,8 @@ def run_ours(args):
     t_e2e = time.perf_counter()
     for _ in range(args.e2e_steps):
         ctx.image_batch_host(ws.ant_xyz, larr, h_vis, h_img, h_ws)
-    e2e_ms = (time.perf_counter() - t_e2e) * 1e3
-    if pg:
-        t = torch.tensor([e2e_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * L * args.e2e_steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks((time.perf_counter() - t_e2e) * 1e3, pg, "cuda")
+    e2e_value = whole_job_rate(L, world, args.e2e_steps, e2e_ms)
     h2d_bytes = int(h_vis.numel() * 8)
     del h_vis
 
@@ -407,9 +446,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "station: 256 antennas in a 38 m disk, 32640 baselines, "
-                                   "1000 time steps x 32 channels (150-180 MHz), 180^2 all-sky "
-                                   "images, uniform weighting, 20 sources + sigma=1 noise",
+            "config": {"workload": STATION_WORKLOAD,
                        "layers_per_gpu": L, "n_px": N, "baselines": B,
                        "l2": "inputs larger than L2 (8.36 GB of visibilities per GPU)",
                        "parallelism": f"replicas x{world} (independent layers, no collective)"},
