@@ -947,7 +947,7 @@ int host_pipeline(blink_ctx *ctx, HostPipe &hp, const double *h_ant_xyz, int n_a
                   cudaStream_t s) {
     const int64_t nb = int64_t(n_ant) * (n_ant - 1) / 2;
     // chunks of consecutive layers bounded by the staging sizes
-    const size_t cap_vis = size_t(512) << 20, cap_out = size_t(512) << 20;
+    const size_t cap_vis = size_t(256) << 20, cap_out = size_t(256) << 20;
     std::vector<HostChunk> chunks;
     for (int l = 0; l < n_layers;) {
         HostChunk c{l, l, INT64_MAX, 0, INT64_MAX, 0};
@@ -978,6 +978,27 @@ int host_pipeline(blink_ctx *ctx, HostPipe &hp, const double *h_ant_xyz, int n_a
         ok = alloc(reinterpret_cast<void **>(&hp.d_vis[b]), need_vis) &&
              alloc(reinterpret_cast<void **>(&hp.d_out[b]), need_out);
     if (!ok) return fail(ctx, BLINK_ERR_WORKSPACE, "staging allocation failed");
+    for (int b = 0; b < 2; ++b) {
+        HTRY(cudaEventCreateWithFlags(&hp.ev_in[b], cudaEventDisableTiming));
+        HTRY(cudaEventCreateWithFlags(&hp.ev_comp[b], cudaEventDisableTiming));
+        HTRY(cudaEventCreateWithFlags(&hp.ev_out[b], cudaEventDisableTiming));
+    }
+    // The first chunks' visibilities need only the staging buffers: their
+    // copies start now and overlap the plan build (uv, cells, tables).
+    auto copy_in = [&](int ci) -> int {
+        const HostChunk &c = chunks[size_t(ci)];
+        const int b = ci % nbuf;
+        if (ci >= nbuf) HTRY(cudaStreamWaitEvent(ctx->copy_in, hp.ev_comp[b], 0));  // vis buffer free
+        HTRY(cudaMemcpyAsync(hp.d_vis[b], h_vis + 2 * c.vis_base, size_t(c.vis_end - c.vis_base) * 8,
+                             cudaMemcpyHostToDevice, ctx->copy_in));
+        HTRY(cudaEventRecord(hp.ev_in[b], ctx->copy_in));
+        return BLINK_OK;
+    };
+    HTRY(cudaEventRecord(hp.ev_out[0], s));  // staging allocated on s
+    HTRY(cudaStreamWaitEvent(ctx->copy_in, hp.ev_out[0], 0));
+    const int early = std::min<int>(nbuf, int(chunks.size()));
+    for (int ci = 0; ci < early; ++ci)
+        if (int e = copy_in(ci)) return e;
     HTRY(cudaMemcpyAsync(hp.d_xyz, h_ant_xyz, sizeof(double) * 3 * size_t(n_ant), cudaMemcpyHostToDevice, s));
     int st = build_plan(ctx, hp.d_xyz, n_ant, h_layers, n_layers, false, &hp.plan, s);
     if (st) return st;
@@ -1007,23 +1028,15 @@ int host_pipeline(blink_ctx *ctx, HostPipe &hp, const double *h_ant_xyz, int n_a
     if (!alloc(reinterpret_cast<void **>(&hp.d_cl), sizeof(DevLayer) * cl.size()))
         return fail(ctx, BLINK_ERR_WORKSPACE, "layer table allocation failed");
     HTRY(cudaMemcpyAsync(hp.d_cl, cl.data(), sizeof(DevLayer) * cl.size(), cudaMemcpyHostToDevice, s));
-    for (int b = 0; b < 2; ++b) {
-        HTRY(cudaEventCreateWithFlags(&hp.ev_in[b], cudaEventDisableTiming));
-        HTRY(cudaEventCreateWithFlags(&hp.ev_comp[b], cudaEventDisableTiming));
-        HTRY(cudaEventCreateWithFlags(&hp.ev_out[b], cudaEventDisableTiming));
-    }
-    // staging, plan and layer table are ready on s before the copy streams start
-    HTRY(cudaEventRecord(hp.ev_comp[1], s));
-    HTRY(cudaStreamWaitEvent(ctx->copy_in, hp.ev_comp[1], 0));
-    HTRY(cudaStreamWaitEvent(ctx->copy_out, hp.ev_comp[1], 0));
+    // plan and layer table are ready on s before any image copy-out
+    HTRY(cudaEventRecord(hp.ev_out[1], s));
+    HTRY(cudaStreamWaitEvent(ctx->copy_out, hp.ev_out[1], 0));
     size_t gi = 0;
     for (int ci = 0; ci < int(chunks.size()); ++ci) {
         const HostChunk &c = chunks[size_t(ci)];
         const int b = ci % nbuf;
-        if (ci >= nbuf) HTRY(cudaStreamWaitEvent(ctx->copy_in, hp.ev_comp[b], 0));  // vis buffer free
-        HTRY(cudaMemcpyAsync(hp.d_vis[b], h_vis + 2 * c.vis_base, size_t(c.vis_end - c.vis_base) * 8,
-                             cudaMemcpyHostToDevice, ctx->copy_in));
-        HTRY(cudaEventRecord(hp.ev_in[b], ctx->copy_in));
+        if (ci >= early)
+            if (int e = copy_in(ci)) return e;
         HTRY(cudaStreamWaitEvent(s, hp.ev_in[b], 0));
         if (ci >= nbuf) HTRY(cudaStreamWaitEvent(s, hp.ev_out[b], 0));  // image buffer drained
         for (; gi < groups.size() && groups[gi].chunk == ci; ++gi) {
