@@ -101,6 +101,9 @@ __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, i
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     auto ph = [](int q) { return PAD ? RowLayout<N>::phys(q) : q; };
     // step A: N1-point transforms along stride N2, then twiddle W_N^(n2 k1)
+    // lanes spread over the rows of the band: a warp then needs only a few
+    // distinct twiddles W_N^(n2 k1) (constant-cache reads serialise per
+    // distinct address, which costs more than the bank conflicts this leaves)
     for (int t = tid; t < nrows * N2; t += nt) {
         const int r = t % nrows, n2 = t / nrows;
         float2 *row = G + r * S;
@@ -133,11 +136,26 @@ __device__ __forceinline__ int pos_after_rows(int p) {
     return Plan<N>::N2 * (p % Plan<N>::N1) + p / Plan<N>::N1;
 }
 
+// Shared-memory layout of the pass-2 intermediate Z of P column pairs: the
+// element q of pair jj sits at jj * ZS + phys(q).  When N2 is a multiple of
+// 32, one padding element per 32 (phys(q) = q + q / 32) separates the k1
+// runs read by the lanes of pass-2 step B, and the pair stride ZS = 16 / P
+// (mod 16, in 8-byte bank pairs) spreads the P pairs of a half-warp over
+// distinct banks in both steps.
+template <int N, int P>
+struct ZLayout {
+    static constexpr bool pad = Plan<N>::N2 % 32 == 0;
+    static constexpr int len = pad ? N + N / 32 : N;
+    static constexpr int want = P >= 16 ? 1 : 16 / P;  // stride mod 16
+    static constexpr int S = len + ((want - len % 16) % 16 + 16) % 16;
+    __device__ __forceinline__ static int phys(int q) { return pad ? q + (q >> 5) : q; }
+};
+
 // Pass 2, step A for column pairs (j0 + jj, j0 + jj + N/2), jj < P.  `hrow(k,
 // p)` returns row k (< R) of the pass-1 output at frequency column p.  Writes
 // the four-step intermediate of pair jj to Z + jj * S.
-template <int N, int P, class HRow>
-__device__ __forceinline__ void cols_step_a(float2 *Z, int S, int R, int j0, HRow hrow, int tid,
+template <int N, int P, class ZL, class HRow>
+__device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow hrow, int tid,
                                             int nt) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
     for (int t = tid; t < P * N2; t += nt) {
@@ -165,24 +183,24 @@ __device__ __forceinline__ void cols_step_a(float2 *Z, int S, int R, int j0, HRo
             x[n1] = z;
         }
         dft<N1, +1>(x);
-        float2 *zp = Z + jj * S + n2;
+        float2 *zp = Z + jj * ZL::S;
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1)
-            zp[N2 * k1] = k1 == 0 ? x[0] : cmulc(x[k1], c_roots<N, +1>.v[n2 * k1]);
+            zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], c_roots<N, +1>.v[n2 * k1]);
     }
 }
 
 // Pass 2, step B: N2-point transforms, then the two real image columns with
 // the fftshift folded into the addresses.
-template <int N, int P>
-__device__ __forceinline__ void cols_step_b(const float2 *Z, int S, int j0, float *img, float scale,
+template <int N, int P, class ZL>
+__device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img, float scale,
                                             int tid, int nt, const float *ref) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
     for (int t = tid; t < P * N1; t += nt) {
         const int jj = t % P, k1 = t / P;
         const int ja = j0 + jj;
         if (ja >= H) continue;
-        const float2 *zp = Z + jj * S + N2 * k1;
+        const float2 *zp = Z + jj * ZL::S;
         float2 rf[N2];  // fused epilogue: reference values requested before the transform
         if (ref) {
 #pragma unroll
@@ -194,7 +212,7 @@ __device__ __forceinline__ void cols_step_b(const float2 *Z, int S, int j0, floa
         }
         float2 y[N2];
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[n2];
+        for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[ZL::phys(N2 * k1 + n2)];
         dft<N2, +1>(y);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
@@ -771,9 +789,10 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_rows(ImageArgs a, int l0) {
 
 // Pass 2 for P column pairs of one layer.  Grid: (ceil(N/2 / P), layers in wave).
 template <int N, bool EPI>
-__global__ void __launch_bounds__(LargeCfg<N>::NT) k_cols(ImageArgs a, int l0, float *__restrict__ out,
+__global__ void __launch_bounds__(LargeCfg<N>::NT, EPI ? 1 : 3) k_cols(ImageArgs a, int l0, float *__restrict__ out,
                                                           const float *__restrict__ ref) {
-    constexpr int NT = LargeCfg<N>::NT, S = LargeCfg<N>::S, P = LargeCfg<N>::P;
+    constexpr int NT = LargeCfg<N>::NT, P = LargeCfg<N>::P;
+    using ZL = ZLayout<N, P>;
     extern __shared__ float2 sm[];
     const int lw = blockIdx.y;
     const DevLayer L = a.layers[l0 + lw];
@@ -782,10 +801,10 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_cols(ImageArgs a, int l0, f
     const int j0 = blockIdx.x * P;
     const float2 *Hs = a.scratch + int64_t(lw) * a.r_alloc * N;
     auto hrow = [&](int k, int p) { return Hs[int64_t(k) * N + p]; };
-    cols_step_a<N, P>(sm, S, R, j0, hrow, threadIdx.x, NT);
+    cols_step_a<N, P, ZL>(sm, R, j0, hrow, threadIdx.x, NT);
     __syncthreads();
     const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
-    cols_step_b<N, P>(sm, S, j0, out + L.out_off, scale, threadIdx.x, NT,
+    cols_step_b<N, P, ZL>(sm, j0, out + L.out_off, scale, threadIdx.x, NT,
                       EPI && ref ? ref + L.out_off : nullptr);
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
 }
@@ -991,7 +1010,7 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
         return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
     const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer, a.wave_budget);
     const size_t smem_rows = size_t(C::RB) * C::S * sizeof(float2);
-    const size_t smem_cols = size_t(C::P) * C::S * sizeof(float2);
+    const size_t smem_cols = size_t(C::P) * ZLayout<N, C::P>::S * sizeof(float2);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         int(smem_rows)));
     auto cols = a.ref ? k_cols<N, true> : k_cols<N, false>;
