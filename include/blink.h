@@ -258,6 +258,15 @@ BLINK_API int blink_plan_capture(blink_plan *plan, const float *d_vis, float *d_
                                  uint32_t flags, const blink_epilogue *epi, void *stream);
 BLINK_API int blink_plan_replay(blink_plan *plan, void *stream);
 
+/* Limit, in nanoseconds, of the first barrier waits of the tensor-core
+ * kernels of every later launch on `ctx` (< 0: the default, one second).
+ * A wait that runs out records BLINK_ERR_TIMEOUT in the plan's status word
+ * (read by blink_plan_check), lets its own copies and MMAs finish, frees its
+ * tensor memory and returns without writing the image; the context stays
+ * usable.  0 makes those waits give up after one poll, which is how the
+ * timeout path is tested. */
+BLINK_API int blink_ctx_set_wait_limit(blink_ctx *ctx, int64_t limit_ns);
+
 /* Waits for `stream` and returns the plan's device status word: BLINK_OK, or
  * BLINK_ERR_TIMEOUT if a bounded device-side wait of an earlier launch gave
  * up (that launch's output is incomplete).  Clears the word. */

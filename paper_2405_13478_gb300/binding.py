@@ -29,7 +29,7 @@ EXPORTS = (
     "blink_image_batch_noalloc", "blink_image_batch_host", "blink_degrid", "blink_plan_degrid",
     "blink_apply_gains", "blink_gain_grad", "blink_plan_check", "blink_plan_autotune",
     "blink_plan_tuning", "blink_plan_set_tuning", "blink_plan_capture", "blink_plan_replay",
-    "blink_plan_image_ex",
+    "blink_plan_image_ex", "blink_ctx_set_wait_limit",
 )
 
 
@@ -108,6 +108,8 @@ def lib(path: str = LIB_PATH):
     L.blink_plan_create.argtypes = [P, P, I, LP, I, ctypes.POINTER(P), P]
     L.blink_plan_image.restype = I
     L.blink_plan_image.argtypes = [P, P, P, P, ctypes.c_uint32, P]
+    L.blink_ctx_set_wait_limit.restype = I
+    L.blink_ctx_set_wait_limit.argtypes = [P, ctypes.c_int64]
     L.blink_plan_image_ex.restype = I
     L.blink_plan_image_ex.argtypes = [P, P, P, P, ctypes.c_uint32, ctypes.POINTER(Epilogue), P]
     L.blink_plan_destroy.restype = None
@@ -237,6 +239,10 @@ class Context:
     def _raise(self, st):
         if st != OK:
             raise BlinkError(st, self._lib.blink_last_error(self.handle).decode())
+
+    def set_wait_limit(self, limit_ns):
+        """Bounded-wait limit of the tensor-core kernels (ns; < 0 = default 1 s)."""
+        self._raise(self._lib.blink_ctx_set_wait_limit(self.handle, int(limit_ns)))
 
     def cells(self, ant_xyz, layers, cells_out, stream=None):
         """Cell indices: int32 [n_layers][B][2]."""

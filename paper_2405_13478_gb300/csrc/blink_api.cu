@@ -26,6 +26,7 @@ struct blink_ctx {
     cudaMemPool_t pool = nullptr;
     cudaStream_t copy_in = nullptr;   // host-buffer pipeline: host -> device copies
     cudaStream_t copy_out = nullptr;  // host-buffer pipeline: device -> host copies
+    int64_t wait_ns = -1;             // bounded-wait limit of the tensor-core kernels (< 0: default)
     std::string err;
 };
 
@@ -392,6 +393,7 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.status = p->d_status;
     a.csr = p->d_csr;
     a.n_ant = p->n_ant;
+    a.wait_ns = p->ctx->wait_ns;
     a.force_path = g.force_path;
     a.wave_budget = g.wave_budget;
     return a;
@@ -676,6 +678,12 @@ int blink_plan_tuning(const blink_plan *p, int group, int *n_px, int *path, int6
     if (n_px) *n_px = grp.n_px;
     if (path) *path = grp.force_path;
     if (wave_bytes) *wave_bytes = int64_t(grp.wave_budget);
+    return BLINK_OK;
+}
+
+int blink_ctx_set_wait_limit(blink_ctx *ctx, int64_t limit_ns) {
+    if (!ctx) return BLINK_ERR_INVALID;
+    ctx->wait_ns = limit_ns < 0 ? -1 : limit_ns;
     return BLINK_OK;
 }
 

@@ -40,7 +40,9 @@ namespace blink {
 namespace {
 
 constexpr int kTileM = 128, kTileN = 256;
-constexpr long kWaitLimit = 1L << 26;
+// Bounded barrier waits: a wait gives up after this many nanoseconds of the
+// global timer (1 s; the transfers and MMAs it waits for take microseconds).
+constexpr unsigned long long kWaitNs = 1000000000ull;
 
 struct DftArgs {
     const uint16_t *a_hi, *a_lo;  // [N / 128] blocks of 128 x K (tiled)
@@ -53,6 +55,7 @@ struct DftArgs {
     int n_px, K;
     int *status;
     const float *ref;             // reference images (fused epilogue) or null
+    unsigned long long wait_ns;   // limit of the first barrier waits (failure tests lower it)
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -90,8 +93,27 @@ __device__ __forceinline__ float from_bits(uint16_t b) {
 template <bool FP16>
 constexpr int lo_shift() { return FP16 ? 11 : 0; }
 
-__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
-    for (long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Polls the barrier until its phase `parity` completes or `limit_ns` pass
+// (try_wait may suspend the thread for a while on each poll).  Limit 0: one
+// non-blocking test.  Returns whether the phase completed.
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kWaitNs) {
+    if (limit_ns == 0) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        return ok != 0;
+    }
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
@@ -99,8 +121,8 @@ __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (global_ns() - t0 >= limit_ns) return false;
     }
-    return false;
 }
 
 // ---------------------------------------------------------------- operand A
@@ -253,7 +275,9 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__
                 : "memory");
         }
     }
-    const bool loaded = wait_parity(saddr(&bar_load), 0);
+    // every decision below is CTA-uniform (the epilogue's tcgen05.ld is
+    // warp-collective, and the MMAs are issued only if all threads agree)
+    const bool loaded = __syncthreads_and(wait_parity(saddr(&bar_load), 0, d.wait_ns));
     bool ok = loaded;
     if (tid == 0 && loaded) {
         // D = A B^T over K in steps of 16: M = 128, N = 256, both K-major
@@ -277,7 +301,7 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__
                          saddr(&bar_mma))
                      : "memory");
     }
-    if (loaded) ok = wait_parity(saddr(&bar_mma), 0);
+    if (loaded) ok = __syncthreads_and(wait_parity(saddr(&bar_mma), 0, d.wait_ns));
     if (!ok) {
         if (tid == 0 && d.status) atomicExch(d.status, -4);  // BLINK_ERR_TIMEOUT
         // let copies or MMAs still in flight finish before the memory goes away
@@ -365,7 +389,7 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
         k_split<FP16><<<cnt, 256, 0, st>>>(T, a.r_alloc, N, Rp, a.layers, a.chans, l0, b_hi, b_lo, b_exp);
         BLINK_CUDA_TRY(cudaGetLastError());
         DftArgs d{a_hi, a_lo, b_hi, b_lo, b_exp, a.layers, a.chans, static_cast<float *>(a.out), a.flags, N, K, a.status,
-                  a.ref};
+                  a.ref, a.wait_ns < 0 ? kWaitNs : static_cast<unsigned long long>(a.wait_ns)};
         k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / kTileN), unsigned(cnt)), 128, smem, st>>>(
             d, l0, d.out, d.ref);
         BLINK_CUDA_TRY(cudaGetLastError());

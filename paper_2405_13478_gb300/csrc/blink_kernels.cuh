@@ -49,6 +49,7 @@ struct ImageArgs {
     const float2 *gprod;        // gain products g_i conj(g_j) [gain rows][nb], or null
                                 // (then the kernels form them from `gains`)
     const float *ref;           // reference images, addressed like the output
+    int64_t wait_ns = -1;       // first-wait limit of the tensor-core kernels (< 0: default 1 s)
 };
 
 // Per-size launchers (defined in blink_image_impl.cuh, instantiated once per
