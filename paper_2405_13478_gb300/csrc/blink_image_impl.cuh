@@ -206,7 +206,7 @@ __device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img,
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) {
                 const int q = k1 + N1 * k2;
-                const float *rp = ref + int64_t(q < H ? q + H : q - H) * N;
+                const float *rp = ref + (q < H ? q + H : q - H) * N;  // 32-bit: N * N < 2^31
                 rf[k2] = make_float2(__ldcs(rp + ja + H), __ldcs(rp + ja));
             }
         }
@@ -218,7 +218,7 @@ __device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img,
         for (int k2 = 0; k2 < N2; ++k2) {
             const int q = k1 + N1 * k2;               // FFT-order row
             const int row = q < H ? q + H : q - H;    // fftshift
-            const int64_t o = int64_t(row) * N;
+            const int o = row * N;  // offsets inside one image fit 32 bits
             float va = y[k2].x * scale, vb = y[k2].y * scale;
             if (ref) {
                 va -= rf[k2].x;
@@ -440,7 +440,7 @@ __device__ __forceinline__ void small_transform(float2 *G, float2 *Z, int R, con
 #pragma unroll
                         for (int k2 = 0; k2 < N2; ++k2) {
                             const int q = k1 + N1 * k2;
-                            const float *rp = ref + int64_t(q < H ? q + H : q - H) * N;
+                            const float *rp = ref + (q < H ? q + H : q - H) * N;  // 32-bit: N * N < 2^31
                             rf[k2] = make_float2(__ldcs(rp + ja + H), __ldcs(rp + ja));
                         }
                     }
@@ -452,7 +452,7 @@ __device__ __forceinline__ void small_transform(float2 *G, float2 *Z, int R, con
                     for (int k2 = 0; k2 < N2; ++k2) {
                         const int q = k1 + N1 * k2;
                         const int row = q < H ? q + H : q - H;
-                        const int64_t o = int64_t(row) * N;
+                        const int o = row * N;  // offsets inside one image fit 32 bits
                         float va = y[k2].x * scale, vb = y[k2].y * scale;
                         if (ref) {
                             va -= rf[k2].x;
