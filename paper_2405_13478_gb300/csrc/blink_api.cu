@@ -51,6 +51,7 @@ struct blink_plan {
         int max_seg;    // longest per-chunk schedule segment among them
         int force_path = 0;       // autotuned kernel choice (0 = default)
         size_t wave_budget = 0;   // autotuned wave size of the two-kernel path
+        int kmax = 0;             // max |k_u| over the group's channels
     };
     std::vector<Group> groups;
     // device memory (one pool allocation for the tables, one for scratch)
@@ -81,6 +82,9 @@ struct blink_plan {
 namespace {
 
 constexpr size_t kScratchCap = size_t(48) << 20;
+// Tensor-core transform scratch per plan: its waves trade L2 residency of the
+// pass-1 output for fewer, fuller launches (each wave is three kernels).
+constexpr size_t kTensorScratchCap = size_t(512) << 20;
 // Largest gain-product table (distinct gain rows x baselines x 8 bytes) the
 // fused epilogue builds; above it the kernels form g_i conj(g_j) per entry.
 constexpr size_t kGainTableCap = size_t(256) << 20;  // bytes of row-transform scratch per plan (L2-sized waves)
@@ -353,6 +357,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
             g.sched_ok = g.sched_ok && ci.sched_off >= 0 && ci.sched == 1;
             g.max_chunk = std::max(g.max_chunk, ci.chunk);
             g.max_seg = std::max(g.max_seg, ci.max_seg);
+            g.kmax = std::max(g.kmax, ci.kmax_u);
         }
         g.r_alloc = r;
         const size_t per = blink::image_scratch_per_layer(g.n_px, r);
@@ -394,6 +399,7 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.csr = p->d_csr;
     a.n_ant = p->n_ant;
     a.wait_ns = p->ctx->wait_ns;
+    a.kmax = g.kmax;
     a.force_path = g.force_path;
     a.wave_budget = g.wave_budget;
     return a;
@@ -552,9 +558,8 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
         for (const auto &grp : p->groups) {
             if (!gemm_ok(grp)) continue;
             const size_t per = blink::dftgemm_scratch_per_layer(grp.n_px, grp.r_alloc);
-            const int rp = (grp.r_alloc + 7) / 8 * 8;
-            const size_t fixed = 2 * size_t(grp.n_px) * 2 * rp * 2 + 512;
-            need = std::max(need, fixed + std::max(per, std::min(per * size_t(grp.count), kScratchCap)));
+            const size_t fixed = blink::dftgemm_scratch_fixed(grp.n_px, grp.r_alloc, grp.kmax);
+            need = std::max(need, fixed + std::max(per, std::min(per * size_t(grp.count), kTensorScratchCap)));
         }
         if (need) {
             void *ptr = nullptr;

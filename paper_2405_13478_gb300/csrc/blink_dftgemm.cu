@@ -356,6 +356,270 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
 }
 
+// ------------------------------------------------- pass 1 as a GEMM (BF16)
+// When the gridded support is narrow (|k_u| <= kmax), pass 1 is also a dense
+// real GEMM over the compact columns c = -kmax..kmax (Kc of them, padded to 8):
+//   T[r][p] = sum_c G[r][c] exp(+2 pi i c p / N)   (r < R, p FFT-order column),
+//   [Tr | Ti] (R x 2N) = [Gr | Gi] (R x 2Kc) B1^T  with, for n = (part, p),
+//   B1[(0, p)][k] = cos th (k < Kc), -sin th (k >= Kc);
+//   B1[(1, p)][k] = sin th (k < Kc),  cos th (k >= Kc),   th = 2 pi c_k p / N,
+// c_k = (k mod Kc) - kmax.  k_grid_a1 grids a layer straight into the compact
+// A1 = [Gr | Gi] (hi/lo, tiled, 128 rows), k_gemm1 multiplies on the tensor
+// cores and writes T in the layout of the pass-2 operand B (hi/lo), so the FP32
+// row FFT and the split pass are not needed.  BF16 only (no range control).
+constexpr int kTile1N = 128;  // output columns of one pass-1 CTA
+
+__global__ void k_row_table(int N, int kmax, int Kc, uint16_t *b_hi, uint16_t *b_lo) {
+    const int K1 = 2 * Kc;
+    const int64_t total = int64_t(2 * N) * K1;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int n = int(i / K1), k = int(i % K1);
+        const int part = n / N, p = n % N, kk = k % Kc;
+        float x = 0.f;
+        if (kk <= 2 * kmax) {
+            const int64_t m = ((int64_t(kk - kmax) * p) % N + N) % N;  // exact phase index
+            double sn, cs;
+            sincospi(2.0 * double(m) / double(N), &sn, &cs);
+            const bool re_in = k < Kc;
+            x = float(part == 0 ? (re_in ? cs : -sn) : (re_in ? sn : cs));
+        }
+        const uint16_t hb = to_bits<false>(x);
+        const int64_t o = int64_t(n / kTile1N) * kTile1N * K1 + tiled(n % kTile1N, k, K1);
+        b_hi[o] = hb;
+        b_lo[o] = to_bits<false>(x - from_bits<false>(hb));
+    }
+}
+
+struct Grid1Args {
+    const float2 *vis;
+    const DevLayer *layers;
+    const ChanInfo *chans;
+    const uint32_t *codes;
+    const float *wgt;
+    const unsigned char *csr;
+    int64_t nb;
+    int n_px, kmax, Kc;
+    uint16_t *a_hi, *a_lo;  // [wave] blocks of 128 x 2 Kc (tiled)
+};
+
+// Grid: (bands of 8 rows, layers of the wave).  Compact gridding of rows
+// [8 band, 8 band + 8) of one layer (columns |k_u| <= kmax), weights,
+// Hermitian completion of row 0, then those rows of A1 (hi/lo).  With two
+// layers per A1 block (support <= 64 rows) layer lw fills rows 64 (lw & 1) +.
+__global__ void __launch_bounds__(256) k_grid_a1(Grid1Args g, int l0, int pack) {
+    extern __shared__ float2 gc[];  // [8][Kc]
+    const int band = blockIdx.x, lw = blockIdx.y;
+    const DevLayer L = g.layers[l0 + lw];
+    const ChanInfo ci = g.chans[L.chan];
+    const int R = ci.rows, Kc = g.Kc, kmax = g.kmax, N = g.n_px, H = N / 2, K1 = 2 * Kc;
+    const int r0 = band * 8;
+    // bands past the layer's support still write their (zero) rows: the A1
+    // block may hold a larger-support layer of an earlier wave
+    const int nrows = max(0, min(8, R - r0));
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < 8 * Kc; i += nt) gc[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const float2 *vis = g.vis + L.vis_off;
+    auto put = [&](uint32_t cd, float2 v) {
+        const int r = int(code_row(cd)) - r0, col = int(code_col(cd));
+        const int ku = col <= H ? col : col - N;
+        if (r < 0 || r >= nrows || ku < -kmax || ku > kmax) return;
+        if (code_conj(cd)) v.y = -v.y;
+        float2 *cell = gc + r * Kc + (ku + kmax);
+        atomicAdd(&cell->x, v.x);
+        atomicAdd(&cell->y, v.y);
+    };
+    if (nrows == 0) {
+        // nothing to grid: the rows below are written as zeros
+    } else if (g.csr && ci.csr_off >= 0) {  // only this band's baselines, from the row buckets
+        const CsrLayout cl(N, g.nb);
+        const int32_t *ptr = reinterpret_cast<const int32_t *>(g.csr + ci.csr_off + cl.row_ptr);
+        const uint2 *ents = reinterpret_cast<const uint2 *>(g.csr + ci.csr_off + cl.ents);
+        const int e1 = ptr[r0 + nrows];
+        for (int e = ptr[r0] + tid; e < e1; e += nt) {
+            const uint2 en = __ldg(ents + e);
+            put(en.y, __ldg(vis + en.x));
+        }
+    } else {
+        const uint32_t *code = g.codes + ci.code_off;
+        for (int64_t b = tid; b < g.nb; b += nt) {
+            const uint32_t cd = __ldg(code + b);
+            if (cd != kCodeDropped) put(cd, __ldcs(vis + b));
+        }
+    }
+    __syncthreads();
+    const float *w = ci.weighting == 1 ? g.wgt + ci.wgt_off : nullptr;
+    if (w)
+        for (int i = tid; i < nrows * Kc; i += nt) {
+            const int r = i / Kc, kk = i % Kc, ku = kk - kmax;
+            if (r0 + r == 0 || kk > 2 * kmax) continue;
+            const float wv = w[(r0 + r) * N + (ku < 0 ? ku + N : ku)];
+            gc[i].x *= wv;
+            gc[i].y *= wv;
+        }
+    __syncthreads();
+    // row 0: k_u >= 0 was gridded; weight it and mirror the conjugate to -k_u;
+    // the origin carries V and conj V of its baselines: 2 Re * w
+    if (r0 == 0)
+        for (int ku = tid; ku <= kmax; ku += nt) {
+            const float wv = w ? w[ku] : 1.f;
+            const float2 v = gc[kmax + ku];
+            if (ku == 0) {
+                gc[kmax] = make_float2(2.f * v.x * wv, 0.f);
+            } else {
+                gc[kmax + ku] = make_float2(v.x * wv, v.y * wv);
+                gc[kmax - ku] = make_float2(v.x * wv, -v.y * wv);
+            }
+        }
+    __syncthreads();
+    // A1 rows: k < Kc real parts, k >= Kc imaginary parts (rows >= R of the band zero)
+    const int blk = pack ? lw >> 1 : lw, roff = pack ? 64 * (lw & 1) : 0;
+    uint16_t *hi = g.a_hi + int64_t(blk) * 128 * K1;
+    uint16_t *lo = g.a_lo + int64_t(blk) * 128 * K1;
+    for (int i = tid; i < 8 * (K1 / 8); i += nt) {
+        const int r = i % 8, k8 = i / 8;
+        uint16_t h[8], l[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = 8 * k8 + j, kk = k % Kc;
+            float x = 0.f;
+            if (r < nrows) x = k < Kc ? gc[r * Kc + kk].x : gc[r * Kc + kk].y;
+            h[j] = to_bits<false>(x);
+            l[j] = to_bits<false>(x - from_bits<false>(h[j]));
+        }
+        const int o = tiled(roff + r0 + r, 8 * k8, K1);
+        uint4 hv, lv;
+        hv.x = h[0] | (uint32_t(h[1]) << 16); hv.y = h[2] | (uint32_t(h[3]) << 16);
+        hv.z = h[4] | (uint32_t(h[5]) << 16); hv.w = h[6] | (uint32_t(h[7]) << 16);
+        lv.x = l[0] | (uint32_t(l[1]) << 16); lv.y = l[2] | (uint32_t(l[3]) << 16);
+        lv.z = l[4] | (uint32_t(l[5]) << 16); lv.w = l[6] | (uint32_t(l[7]) << 16);
+        *reinterpret_cast<uint4 *>(hi + o) = hv;
+        *reinterpret_cast<uint4 *>(lo + o) = lv;
+    }
+}
+
+struct Gemm1Args {
+    const uint16_t *a_hi, *a_lo;  // [wave] 128 x K1 (tiled)
+    const uint16_t *b_hi, *b_lo;  // B1 table, [2N / 128] blocks of 128 x K1
+    uint16_t *t_hi, *t_lo;        // pass-2 operand B: [wave][N / 256] blocks of 256 x K2
+    const DevLayer *layers;
+    const ChanInfo *chans;
+    int n_px, K1, Rp;
+    int *status;
+    unsigned long long wait_ns;
+};
+
+// Grid: (2N / 128, A1 blocks of the wave).  128 threads; D (128 x 128, FP32
+// in TMEM) = A1 B1^T over K1, then each row r < Rp of a layer (TMEM lane r, or
+// 64 + r for the second layer of a packed block) goes to column k2 = r (real
+// part) or Rp + r (imaginary part) of that layer's pass-2 operand.
+template <int SPLIT>
+__global__ void __launch_bounds__(128, 1) k_gemm1(Gemm1Args d, int l0, int pack, int cnt) {
+    constexpr uint32_t NCOL = kTile1N;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t bar_load, bar_mma;
+    __shared__ uint32_t tmem_base;
+    const int K1 = d.K1, N = d.n_px, Rp = d.Rp, K2 = 2 * Rp;
+    const int nt = blockIdx.x, blk = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t a_bytes = 128u * K1 * 2, b_bytes = uint32_t(kTile1N) * K1 * 2;
+    unsigned char *sA_hi = sm, *sA_lo = sm + a_bytes;
+    unsigned char *sB_hi = sm + (SPLIT == 3 ? 2 : 1) * a_bytes;
+    unsigned char *sB_lo = sB_hi + b_bytes;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_load)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_mma)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                     "r"(NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        const uint32_t total = (SPLIT == 3 ? 2 : 1) * (a_bytes + b_bytes);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&bar_load)), "r"(total)
+                     : "memory");
+        const uint16_t *ga[2] = {d.a_hi + int64_t(blk) * 128 * K1, d.a_lo + int64_t(blk) * 128 * K1};
+        const uint16_t *gb[2] = {d.b_hi + int64_t(nt) * kTile1N * K1, d.b_lo + int64_t(nt) * kTile1N * K1};
+        unsigned char *sa[2] = {sA_hi, sA_lo}, *sb[2] = {sB_hi, sB_lo};
+        for (int h = 0; h < (SPLIT == 3 ? 2 : 1); ++h) {
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    saddr(sa[h])),
+                "l"(ga[h]), "r"(a_bytes), "r"(saddr(&bar_load))
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    saddr(sb[h])),
+                "l"(gb[h]), "r"(b_bytes), "r"(saddr(&bar_load))
+                : "memory");
+        }
+    }
+    const bool loaded = __syncthreads_and(wait_parity(saddr(&bar_load), 0, d.wait_ns));
+    bool ok = loaded;
+    if (tid == 0 && loaded) {
+        // D = A1 B1^T over K1 in steps of 16: M = 128, N = 128, both K-major, BF16
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTile1N >> 3) << 17) |
+                               (uint32_t(128 >> 4) << 24);
+        const uint32_t sbo = uint32_t(K1 / 8) * 128;
+        for (int s = 0; s < K1 / 16; ++s) {
+            const uint64_t ah = smem_desc(saddr(sA_hi) + s * 256, 128, sbo);
+            const uint64_t bh = smem_desc(saddr(sB_hi) + s * 256, 128, sbo);
+            mma_f16(tmem, ah, bh, idesc, s > 0);
+            if constexpr (SPLIT == 3) {
+                const uint64_t al = smem_desc(saddr(sA_lo) + s * 256, 128, sbo);
+                const uint64_t bl = smem_desc(saddr(sB_lo) + s * 256, 128, sbo);
+                mma_f16(tmem, ah, bl, idesc, 1u);
+                mma_f16(tmem, al, bh, idesc, 1u);
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         saddr(&bar_mma))
+                     : "memory");
+    }
+    if (loaded) ok = __syncthreads_and(wait_parity(saddr(&bar_mma), 0, d.wait_ns));
+    if (!ok) {
+        if (tid == 0 && d.status) atomicExch(d.status, -4);  // BLINK_ERR_TIMEOUT
+        wait_parity(saddr(&bar_load), 0);
+        if (loaded) wait_parity(saddr(&bar_mma), 0);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = warp * 32 + lane;  // TMEM lane = row of D
+        const int lw = pack ? 2 * blk + (row >> 6) : blk, r = pack ? row & 63 : row;
+        const bool live = lw < cnt;
+        const int R = live ? d.chans[d.layers[l0 + lw].chan].rows : 0;
+        uint16_t *th = d.t_hi + int64_t(lw) * N * K2;
+        uint16_t *tl = d.t_lo + int64_t(lw) * N * K2;
+        for (int c0 = 0; c0 < kTile1N; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32<32>(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (live && r < Rp) {
+                const int n0 = nt * kTile1N + c0;  // 32 columns of one part (N % 128 == 0)
+                const int part = n0 / N, k2 = part ? Rp + r : r;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int p = (n0 + j) % N;
+                    const float x = r < R ? __uint_as_float(v[j]) : 0.f;
+                    const uint16_t hb = to_bits<false>(x);
+                    const int64_t o = int64_t(p / kTileN) * kTileN * K2 + tiled(p % kTileN, k2, K2);
+                    th[o] = hb;
+                    tl[o] = to_bits<false>(x - from_bits<false>(hb));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
+}
+
 template <bool FP16, int SPLIT>
 Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
     const int K = 2 * Rp;
@@ -375,9 +639,54 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
     uint16_t *b_hi = reinterpret_cast<uint16_t *>(wave_base + size_t(wave) * t_bytes);
     uint16_t *b_lo = b_hi + size_t(wave) * b_elems;
     int *b_exp = reinterpret_cast<int *>(b_lo + size_t(wave) * b_elems);
+    const size_t smem = size_t(SPLIT == 3 ? 2 : 1) * (size_t(kTileM) + kTileN) * K * 2;
+    // both passes on the tensor cores when the compact support fits (BF16)
+    const int Kc = (2 * a.kmax + 1 + 7) / 8 * 8, K1 = 2 * Kc;
+    const size_t smem1 = size_t(SPLIT == 3 ? 2 : 1) * (128 + kTile1N) * size_t(K1) * 2;
+    if (!FP16 && !a.gains && a.kmax > 0 && a.r_alloc <= 128 && smem1 <= 227 * 1024) {
+        const size_t b1_elems = size_t(2 * N) * K1, a1_elems = size_t(128) * K1;
+        const size_t fixed1 = 2 * a_elems * 2 + 2 * b1_elems * 2 + 512;
+        const size_t per1 = 2 * a1_elems * 2 + 2 * b_elems * 2;
+        if (a.scratch_bytes < fixed1 + per1) return Error{-5, "tensor-core transform scratch too small"};
+        const int wave1 = int(std::min<size_t>(size_t(a.n_layers), std::min<size_t>(65535, (a.scratch_bytes - fixed1) / per1)));
+        uint16_t *b1_hi = a_lo + a_elems, *b1_lo = b1_hi + b1_elems;
+        unsigned char *wb = base + ((fixed1 + 255) / 256) * 256;
+        uint16_t *a1_hi = reinterpret_cast<uint16_t *>(wb), *a1_lo = a1_hi + size_t(wave1) * a1_elems;
+        uint16_t *t_hi = a1_lo + size_t(wave1) * a1_elems, *t_lo = t_hi + size_t(wave1) * b_elems;
+        k_dft_table<false><<<256, 256, 0, st>>>(N, Rp, a_hi, a_lo);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_row_table<<<256, 256, 0, st>>>(N, a.kmax, Kc, b1_hi, b1_lo);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        const size_t smem_g = size_t(8) * Kc * sizeof(float2);
+        const int pack = a.r_alloc <= 64 ? 1 : 0;  // two layers per 128-row A1 block
+        // rows of A1 no band writes (>= R of a layer, the unused half of a pair) stay zero
+        BLINK_CUDA_TRY(cudaMemsetAsync(a1_hi, 0, 2 * size_t(wave1) * a1_elems * sizeof(uint16_t), st));
+        BLINK_CUDA_TRY(cudaFuncSetAttribute(k_gemm1<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem1)));
+        BLINK_CUDA_TRY(cudaFuncSetAttribute(k_dftgemm<FP16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        const unsigned long long wns = a.wait_ns < 0 ? kWaitNs : static_cast<unsigned long long>(a.wait_ns);
+        for (int l0 = 0; l0 < a.n_layers; l0 += wave1) {
+            const int cnt = std::min(wave1, a.n_layers - l0);
+            if (pack && (cnt & 1)) {  // odd wave: the last block's second half must read zero
+                BLINK_CUDA_TRY(cudaMemsetAsync(a1_hi + size_t(cnt / 2) * a1_elems, 0, a1_elems * sizeof(uint16_t), st));
+                BLINK_CUDA_TRY(cudaMemsetAsync(a1_lo + size_t(cnt / 2) * a1_elems, 0, a1_elems * sizeof(uint16_t), st));
+            }
+            Grid1Args g1{a.vis, a.layers, a.chans, a.codes, a.wgt, a.csr, a.nb, N, a.kmax, Kc, a1_hi, a1_lo};
+            k_grid_a1<<<dim3(unsigned((a.r_alloc + 7) / 8), unsigned(cnt)), 256, smem_g, st>>>(g1, l0, pack);
+            BLINK_CUDA_TRY(cudaGetLastError());
+            Gemm1Args d1{a1_hi, a1_lo, b1_hi, b1_lo, t_hi, t_lo, a.layers, a.chans, N, K1, Rp, a.status, wns};
+            const int blocks = pack ? (cnt + 1) / 2 : cnt;
+            k_gemm1<SPLIT><<<dim3(unsigned(2 * N / kTile1N), unsigned(blocks)), 128, smem1, st>>>(d1, l0, pack, cnt);
+            BLINK_CUDA_TRY(cudaGetLastError());
+            DftArgs d{a_hi, a_lo, t_hi, t_lo, nullptr, a.layers, a.chans, static_cast<float *>(a.out), a.flags, N, K,
+                      a.status, a.ref, wns};
+            k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / kTileN), unsigned(cnt)), 128, smem, st>>>(
+                d, l0, d.out, d.ref);
+            BLINK_CUDA_TRY(cudaGetLastError());
+        }
+        return Error{0, ""};
+    }
     k_dft_table<FP16><<<256, 256, 0, st>>>(N, Rp, a_hi, a_lo);
     BLINK_CUDA_TRY(cudaGetLastError());
-    const size_t smem = size_t(SPLIT == 3 ? 2 : 1) * (size_t(kTileM) + kTileN) * K * 2;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_dftgemm<FP16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     for (int l0 = 0; l0 < a.n_layers; l0 += wave) {
         const int cnt = std::min(wave, a.n_layers - l0);
@@ -404,6 +713,12 @@ bool dftgemm_supported(int n_px, int r_alloc, int mode) {
     const size_t smem = size_t(mode == 2 || mode == 4 ? 2 : 1) * (size_t(kTileM) + kTileN) * 2 * Rp * 2;
     return n_px >= kTileN && n_px % kTileN == 0 && image_size_supported(n_px) && 2 * Rp <= 256 &&
            smem <= 227 * 1024;
+}
+
+size_t dftgemm_scratch_fixed(int n_px, int r_alloc, int kmax) {
+    const int Rp = (r_alloc + 7) / 8 * 8;
+    const int K1 = 2 * ((2 * kmax + 1 + 7) / 8 * 8);
+    return 2 * size_t(n_px) * 2 * Rp * 2 + 2 * size_t(2 * n_px) * K1 * 2 + 1024;
 }
 
 size_t dftgemm_scratch_per_layer(int n_px, int r_alloc) {

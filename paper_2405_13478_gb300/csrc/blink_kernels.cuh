@@ -50,6 +50,7 @@ struct ImageArgs {
                                 // (then the kernels form them from `gains`)
     const float *ref;           // reference images, addressed like the output
     int64_t wait_ns = -1;       // first-wait limit of the tensor-core kernels (< 0: default 1 s)
+    int kmax = 0;               // max |k_u| of the group's channels (compact support of pass 1)
 };
 
 // Per-size launchers (defined in blink_image_impl.cuh, instantiated once per
@@ -84,6 +85,8 @@ Error launch_rows_wave(int n_px, const ImageArgs &a, int l0, int cnt, cudaStream
 // mode: 1 BF16, 2 BF16 x3 (split-precision), 3 FP16, 4 FP16 x3.
 bool dftgemm_supported(int n_px, int r_alloc, int mode);
 size_t dftgemm_scratch_per_layer(int n_px, int r_alloc);
+// Layer-independent part of that scratch (DFT tables of both passes).
+size_t dftgemm_scratch_fixed(int n_px, int r_alloc, int kmax);
 Error launch_dftgemm_group(int n_px, int mode, const ImageArgs &a, cudaStream_t st);
 
 // Adjoint of the image path: resid (float [N][N] at out_off) -> dvis
