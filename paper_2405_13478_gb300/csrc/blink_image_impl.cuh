@@ -787,6 +787,60 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_rows(ImageArgs a, int l0) {
     }
 }
 
+// The column pass can stage its scratch columns through shared memory when
+// step A has exactly one task per thread (P N2 == NT) and the pairs tile N/2.
+template <int N>
+struct ColsStaged {
+    static constexpr int P = LargeCfg<N>::P, N2 = Plan<N>::N2;
+    static constexpr bool value = P * N2 == LargeCfg<N>::NT && (N / 2) % P == 0 && P % 2 == 0;
+};
+
+// Pass 2, step A from shared memory: all of the CTA's scratch columns (pairs
+// j0..j0+P and their partners + N/2, rows k < R) are copied with cp.async at
+// once into the buffer Z later holds; each thread reads its N1 inputs into
+// registers, the CTA synchronises, then the intermediate overwrites the buffer.
+template <int N, int P, class ZL>
+__device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, const float2 *Hs, int tid) {
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2, NT = LargeCfg<N>::NT;
+    float2 *stg = Z;  // [R][2P]: columns j0.. then j0 + N/2..
+    for (int i = tid; i < R * P; i += NT) {  // P 16-byte pieces per row
+        const int k = i / P, piece = i % P, half = piece / (P / 2), q = piece % (P / 2);
+        const float2 *src = Hs + int64_t(k) * N + (half ? j0 + H : j0) + 2 * q;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(uint32_t(__cvta_generic_to_shared(
+                         stg + k * 2 * P + half * P + 2 * q))),
+                     "l"(src)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const int jj = tid % P, n2 = tid / P;  // one task per thread
+    float2 x[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+        const int k = N2 * n1 + n2;
+        float2 z = make_float2(0.f, 0.f);
+        if (k < H) {
+            if (k < R) {
+                const float2 a = stg[k * 2 * P + jj], b = stg[k * 2 * P + P + jj];
+                z = make_float2(a.x - b.y, a.y + b.x);  // H_a + i H_b
+            }
+        } else if (k > H) {
+            const int m = N - k;
+            if (m < R) {
+                const float2 a = stg[m * 2 * P + jj], b = stg[m * 2 * P + P + jj];
+                z = make_float2(a.x + b.y, b.x - a.y);  // conj(H_a) + i conj(H_b)
+            }
+        }
+        x[n1] = z;
+    }
+    __syncthreads();  // every staged value is in registers: the buffer becomes Z
+    dft<N1, +1>(x);
+    float2 *zp = Z + jj * ZL::S;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+        zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], c_roots<N, +1>.v[n2 * k1]);
+}
+
 // Pass 2 for P column pairs of one layer.  Grid: (ceil(N/2 / P), layers in wave).
 template <int N, bool EPI>
 __global__ void __launch_bounds__(LargeCfg<N>::NT, EPI ? 1 : 3) k_cols(ImageArgs a, int l0, float *__restrict__ out,
@@ -800,8 +854,12 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT, EPI ? 1 : 3) k_cols(ImageArgs
     const int R = ci.rows;
     const int j0 = blockIdx.x * P;
     const float2 *Hs = a.scratch + int64_t(lw) * a.r_alloc * N;
-    auto hrow = [&](int k, int p) { return Hs[int64_t(k) * N + p]; };
-    cols_step_a<N, P, ZL>(sm, R, j0, hrow, threadIdx.x, NT);
+    if constexpr (ColsStaged<N>::value) {
+        cols_step_a_staged<N, P, ZL>(sm, R, j0, Hs, threadIdx.x);
+    } else {
+        auto hrow = [&](int k, int p) { return Hs[int64_t(k) * N + p]; };
+        cols_step_a<N, P, ZL>(sm, R, j0, hrow, threadIdx.x, NT);
+    }
     __syncthreads();
     const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
     cols_step_b<N, P, ZL>(sm, j0, out + L.out_off, scale, threadIdx.x, NT,
@@ -1010,7 +1068,9 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
         return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
     const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer, a.wave_budget);
     const size_t smem_rows = size_t(C::RB) * C::S * sizeof(float2);
-    const size_t smem_cols = size_t(C::P) * ZLayout<N, C::P>::S * sizeof(float2);
+    size_t smem_cols = size_t(C::P) * ZLayout<N, C::P>::S * sizeof(float2);
+    if constexpr (ColsStaged<N>::value)  // the staged columns share the buffer
+        smem_cols = std::max(smem_cols, size_t(a.r_alloc) * 2 * C::P * sizeof(float2));
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         int(smem_rows)));
     auto cols = a.ref ? k_cols<N, true> : k_cols<N, false>;
