@@ -286,4 +286,23 @@ BLINK_PLAN(768, 24, 32)
 BLINK_PLAN(1024, 32, 32)
 #undef BLINK_PLAN
 
+// Four-step twiddles W_N^(n2 k1) (inverse direction) in transposed order,
+// index k1 N2 + n2: copied to shared memory they are read by lanes running
+// along n2 without bank conflicts (the constant cache would serialise the 32
+// distinct addresses of such a warp).
+template <int N>
+struct FourStepTable {
+    c32 v[N];
+    constexpr FourStepTable() : v{} {
+        for (int k1 = 0; k1 < Plan<N>::N1; ++k1)
+            for (int n2 = 0; n2 < Plan<N>::N2; ++n2) {
+                const c64d w = unit_root((n2 * k1) % N, N);
+                v[k1 * Plan<N>::N2 + n2] = c32{float(w.x), float(w.y)};
+            }
+    }
+};
+
+template <int N>
+__device__ FourStepTable<N> g_four_step = FourStepTable<N>();
+
 }  // namespace blink

@@ -96,30 +96,41 @@ __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begi
 
 // Pass 1 on rows [0, nrows) of G (row stride S): N-point inverse DFT of each
 // row in place.  Output frequency p ends at position N2 * (p % N1) + p / N1.
-template <int N, int SIGN = +1, bool PAD = false>
-__device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt) {
+// With TW (`tw`: the transposed four-step twiddles in shared memory) lanes run
+// along a row (n2 in step A, k1 in step B): with the padded layout and the
+// table's order every shared access of a warp is conflict-free.  Without it
+// lanes spread over the rows of the band, so a warp needs only a few distinct
+// twiddles from the constant cache (which serialises distinct addresses).
+template <int N, int SIGN = +1, bool PAD = false, bool TW = false>
+__device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt,
+                                         const float2 *tw = nullptr) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     auto ph = [](int q) { return PAD ? RowLayout<N>::phys(q) : q; };
     // step A: N1-point transforms along stride N2, then twiddle W_N^(n2 k1)
-    // lanes spread over the rows of the band: a warp then needs only a few
-    // distinct twiddles W_N^(n2 k1) (constant-cache reads serialise per
-    // distinct address, which costs more than the bank conflicts this leaves)
     for (int t = tid; t < nrows * N2; t += nt) {
-        const int r = t % nrows, n2 = t / nrows;
+        const int r = TW ? t / N2 : t % nrows, n2 = TW ? t % N2 : t / nrows;
         float2 *row = G + r * S;
         float2 x[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) x[n1] = row[ph(N2 * n1 + n2)];
         dft<N1, SIGN>(x);
+        if constexpr (TW) {
 #pragma unroll
-        for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmulc(x[k1], root_rt<N, SIGN>(n2 * k1));
+            for (int k1 = 1; k1 < N1; ++k1) {
+                const float2 w = tw[k1 * N2 + n2];
+                x[k1] = cmulc(x[k1], c32{w.x, SIGN > 0 ? w.y : -w.y});
+            }
+        } else {
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmulc(x[k1], root_rt<N, SIGN>(n2 * k1));
+        }
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) row[ph(N2 * k1 + n2)] = x[k1];
     }
     __syncthreads();
     // step B: N2-point transforms on contiguous runs, result kept in place
     for (int t = tid; t < nrows * N1; t += nt) {
-        const int r = t % nrows, k1 = t / nrows;
+        const int r = TW ? t / N1 : t % nrows, k1 = TW ? t % N1 : t / nrows;
         float2 *run = G + r * S;
         float2 y[N2];
 #pragma unroll
@@ -739,10 +750,28 @@ struct LargeCfg {
     static constexpr int P = std::max(1, std::min(32, NT / Plan<N>::N1));
 };
 
+// Shared-memory offset (in float2) of the four-step twiddle table behind the
+// RB rows of the large-image row kernels (16-byte aligned), and its copy.
+template <int N>
+constexpr int tw_offset() { return (LargeCfg<N>::RB * LargeCfg<N>::S + 1) & ~1; }
+
+template <int N>
+constexpr size_t rows_smem() { return (size_t(tw_offset<N>()) + N) * sizeof(float2); }
+
+template <int N>
+__device__ __forceinline__ void stage_four_step(float2 *dst, int tid, int nt) {
+    const c32 *src = g_four_step<N>.v;
+    for (int i = tid; i < N / 2; i += nt)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(uint32_t(__cvta_generic_to_shared(dst + 2 * i))),
+                     "l"(src + 2 * i)
+                     : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 // Pass 1 for a band of RB canonical rows of one layer, written in natural
 // order to scratch[layer_in_wave][r][p].  Grid: (bands, layers in wave).
 template <int N>
-__global__ void __launch_bounds__(LargeCfg<N>::NT) k_rows(ImageArgs a, int l0) {
+__global__ void __launch_bounds__(LargeCfg<N>::NT, Plan<N>::N1 == 24 ? 2 : 3) k_rows(ImageArgs a, int l0) {
     constexpr int NT = LargeCfg<N>::NT, S = LargeCfg<N>::S, RB = LargeCfg<N>::RB;
     extern __shared__ float2 sm[];
     const int lw = blockIdx.y;
@@ -753,6 +782,8 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_rows(ImageArgs a, int l0) {
     if (r0 >= R) return;
     const int nrows = min(RB, R - r0);
     const int tid = threadIdx.x;
+    float2 *tw = sm + tw_offset<N>();
+    stage_four_step<N>(tw, tid, NT);
     for (int i = tid; i < nrows * S; i += NT) sm[i] = make_float2(0.f, 0.f);
     __syncthreads();
     if (a.csr && ci.csr_off >= 0) {
@@ -778,8 +809,9 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_rows(ImageArgs a, int l0) {
     }
     __syncthreads();
     weight_and_complete<N, true>(sm, S, r0, r0 + nrows, ci, a.wgt, tid, NT);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table in place
     __syncthreads();
-    rows_fft<N, +1, true>(sm, S, nrows, tid, NT);
+    rows_fft<N, +1, true, true>(sm, S, nrows, tid, NT, tw);
     float2 *out = a.scratch + (int64_t(lw) * a.r_alloc + r0) * N;
     for (int i = tid; i < nrows * N; i += NT) {
         const int r = i / N, p = i % N;
@@ -969,9 +1001,12 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_degrid_rows(ImageArgs a, fl
     if (r0 >= R) return;
     const int nrows = min(RB, R - r0);
     const float2 *in = a.scratch + (int64_t(lw) * a.r_alloc + r0) * N;
+    float2 *tw = sm + tw_offset<N>();
+    stage_four_step<N>(tw, tid, NT);
     for (int i = tid; i < nrows * N; i += NT) sm[(i / N) * S + RowLayout<N>::phys(i % N)] = in[i];
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    rows_fft<N, -1, true>(sm, S, nrows, tid, NT);
+    rows_fft<N, -1, true, true>(sm, S, nrows, tid, NT, tw);
     const float *w = ci.weighting == 1 ? a.wgt + ci.wgt_off : nullptr;
     const float scale = 2.f * (((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f);
     if (a.csr && ci.csr_off >= 0) {
@@ -1014,7 +1049,7 @@ Error launch_degrid_n(const ImageArgs &a, const float *resid, float2 *dvis, cuda
         return Error{-5, "degrid scratch too small for image size " + std::to_string(N)};
     const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer);
     const size_t smem_c = degrid_cols_smem<N>();
-    const size_t smem_r = size_t(LargeCfg<N>::RB) * LargeCfg<N>::S * sizeof(float2);
+    const size_t smem_r = rows_smem<N>();
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_c)));
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_r)));
     const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
@@ -1067,7 +1102,7 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     if (!a.scratch || a.scratch_bytes < per_layer)
         return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
     const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer, a.wave_budget);
-    const size_t smem_rows = size_t(C::RB) * C::S * sizeof(float2);
+    const size_t smem_rows = rows_smem<N>();
     size_t smem_cols = size_t(C::P) * ZLayout<N, C::P>::S * sizeof(float2);
     if constexpr (ColsStaged<N>::value)  // the staged columns share the buffer
         smem_cols = std::max(smem_cols, size_t(a.r_alloc) * 2 * C::P * sizeof(float2));
@@ -1102,7 +1137,7 @@ Error SizeOps<N>::image(const ImageArgs &a, cudaStream_t st) { return launch_ima
 template <int N>
 Error SizeOps<N>::rows_wave(const ImageArgs &a, int l0, int cnt, cudaStream_t st) {
     using C = LargeCfg<N>;
-    const size_t smem_rows = size_t(C::RB) * C::S * sizeof(float2);
+    const size_t smem_rows = rows_smem<N>();
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_rows)));
     const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
     k_rows<N><<<dim3(bands, unsigned(cnt)), C::NT, smem_rows, st>>>(a, l0);
