@@ -74,3 +74,55 @@ def test_normalize_and_wsum_with_tensor_cores(env):
         x, y = a[o:o + n].cpu().numpy(), b[o:o + n].cpu().numpy()
         assert np.abs(y * w[k] - x).max() <= 1e-5 * np.abs(x).max()
     plan.close()
+
+
+def _run_modes(torch, binding, ctx, xyz, layers, vis, modes):
+    layers, total = binding.layer_out_offsets(layers)
+    want, _ = oracle.image_batch(xyz, layers, vis.numpy(), "fft")
+    plan = ctx.plan(torch.as_tensor(xyz).cuda(), layers)
+    d_vis = vis.cuda()
+    worst = {}
+    for mode in modes:
+        out = torch.full((total,), float("nan"), device="cuda")
+        plan.image(d_vis, out, None, mode)
+        plan.check()
+        o = out.cpu().numpy()
+        errs = []
+        for L, w in zip(layers, want):
+            n = L["n_px"]
+            g = o[L["out_offset"]:L["out_offset"] + n * n].reshape(n, n)
+            assert np.isfinite(g).all()
+            errs.append(float(np.abs(g - w).max() / np.abs(w).max()))
+        worst[mode] = max(errs)
+    plan.close()
+    return worst
+
+
+@pytest.mark.parametrize("n_px", [512, 1024])
+def test_two_gemm_path_without_layer_packing(env, n_px):
+    """An array elongated north-south: more than 64 support rows (one layer per
+    128-row tile of the row-pass GEMM) but a narrow k_u range (compact K)."""
+    torch, binding, ctx = env[0], env[1], env[2]
+    rng = np.random.default_rng(5)
+    xyz = np.zeros((64, 3))
+    xyz[:, 0] = rng.uniform(-8, 8, 64)
+    xyz[:, 1] = rng.uniform(-40, 40, 64)
+    nb = 64 * 63 // 2
+    freqs = np.linspace(160e6, 180e6, 5)
+    layers = [dict(n_px=n_px, weighting=k % 2, freq_hz=float(f), delta_u=0.5, vis_offset=k * nb)
+              for k, f in enumerate(freqs)]
+    vis = synth.noise((5 * nb,), 1.0, 6, "cpu")
+    worst = _run_modes(torch, binding, ctx, xyz, layers, vis, (0x10, 0x20))
+    assert worst[0x10] <= BOUNDS[0x10] and worst[0x20] <= BOUNDS[0x20], worst
+
+
+def test_wide_support_falls_back_to_the_fft_row_pass(env):
+    """A finer cell (delta_u = 0.2) gives |k_u| up to ~114: the compact row GEMM
+    does not fit, the BF16 modes take the FP32 row pass + GEMM, same bounds."""
+    torch, binding, ctx, ws = env[0], env[1], env[2], env[3]
+    B = ws.n_baselines
+    layers = [dict(n_px=512, weighting=0, freq_hz=float(ws.freqs_hz[c]), delta_u=0.2,
+                   vis_offset=k * B) for k, c in enumerate((0, 15))]
+    vis = ws.vis("cpu", times=[0])[0, [0, 15], :].contiguous().reshape(-1)
+    worst = _run_modes(torch, binding, ctx, ws.ant_xyz, layers, vis, (0x10, 0x20))
+    assert worst[0x10] <= BOUNDS[0x10] and worst[0x20] <= BOUNDS[0x20], worst
