@@ -835,11 +835,14 @@ template <int N, int P, class ZL>
 __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, const float2 *Hs, int tid) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2, NT = LargeCfg<N>::NT;
     float2 *stg = Z;  // [R][2P]: columns j0.. then j0 + N/2..
+    // with P = 8 a staged row is one 16-bank row; column c of row k sits at
+    // c ^ 8 (k & 1) so the two rows a half-warp reads fall in distinct banks
+    auto sw = [](int k, int c) { return P == 8 ? c ^ ((k & 1) << 3) : c; };
     for (int i = tid; i < R * P; i += NT) {  // P 16-byte pieces per row
         const int k = i / P, piece = i % P, half = piece / (P / 2), q = piece % (P / 2);
         const float2 *src = Hs + int64_t(k) * N + (half ? j0 + H : j0) + 2 * q;
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(uint32_t(__cvta_generic_to_shared(
-                         stg + k * 2 * P + half * P + 2 * q))),
+                         stg + k * 2 * P + sw(k, half * P + 2 * q)))),
                      "l"(src)
                      : "memory");
     }
@@ -853,13 +856,13 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
         float2 z = make_float2(0.f, 0.f);
         if (k < H) {
             if (k < R) {
-                const float2 a = stg[k * 2 * P + jj], b = stg[k * 2 * P + P + jj];
+                const float2 a = stg[k * 2 * P + sw(k, jj)], b = stg[k * 2 * P + sw(k, P + jj)];
                 z = make_float2(a.x - b.y, a.y + b.x);  // H_a + i H_b
             }
         } else if (k > H) {
             const int m = N - k;
             if (m < R) {
-                const float2 a = stg[m * 2 * P + jj], b = stg[m * 2 * P + P + jj];
+                const float2 a = stg[m * 2 * P + sw(m, jj)], b = stg[m * 2 * P + sw(m, P + jj)];
                 z = make_float2(a.x + b.y, b.x - a.y);  // conj(H_a) + i conj(H_b)
             }
         }
