@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the plan-reuse and fused-epilogue timings of the default workload")
@@ -432,13 +432,15 @@ def run_ours(args):
         pg.barrier()
     ctx.image_batch_host(ws.ant_xyz, larr, h_vis, h_img, h_ws)   # warm-up (staging pool)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter()
+    calls_ms = []
     for _ in range(args.e2e_steps):
         t_call = time.perf_counter()
         ctx.image_batch_host(ws.ant_xyz, larr, h_vis, h_img, h_ws)
-        print(f"e2e call: {1e3 * (time.perf_counter() - t_call):.1f} ms", file=sys.stderr, flush=True)
-    e2e_ms = max_over_ranks((time.perf_counter() - t_e2e) * 1e3, pg, "cuda")
-    e2e_value = whole_job_rate(L, world, args.e2e_steps, e2e_ms)
+        calls_ms.append(1e3 * (time.perf_counter() - t_call))
+        print(f"e2e call: {calls_ms[-1]:.1f} ms", file=sys.stderr, flush=True)
+    # the median call: the host of a shared GPU machine occasionally stalls one call
+    e2e_ms = max_over_ranks(statistics.median(calls_ms), pg, "cuda")
+    e2e_value = whole_job_rate(L, world, 1, e2e_ms)
     h2d_bytes = int(h_vis.numel() * 8)
     del h_vis
 
@@ -472,6 +474,9 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT,
+                    "method": f"median of {args.e2e_steps} timed calls of blink_image_batch_host "
+                              "(pinned host buffers) after one warm-up call",
+                    "calls_ms": [round(c, 2) for c in calls_ms],
                     "h2d_bytes_per_step": h2d_bytes,
                     "d2h_bytes_per_step": int(images.numel() * 4 + wsum.numel() * 4)},
             "gpu_launches": 7 * args.steps,  # 6 table kernels + 1 fused image kernel per step
