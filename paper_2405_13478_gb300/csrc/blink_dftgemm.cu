@@ -29,6 +29,7 @@
 // word and the CTA still releases its tensor memory.
 #include "blink_common.cuh"
 #include "blink_kernels.cuh"
+#include "blink_sync.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -40,9 +41,6 @@ namespace blink {
 namespace {
 
 constexpr int kTileM = 128, kTileN = 256;
-// Bounded barrier waits: a wait gives up after this many nanoseconds of the
-// global timer (1 s; the transfers and MMAs it waits for take microseconds).
-constexpr unsigned long long kWaitNs = 1000000000ull;
 
 struct DftArgs {
     const uint16_t *a_hi, *a_lo;  // [N / 128] blocks of 128 x K (tiled)
@@ -92,38 +90,6 @@ __device__ __forceinline__ float from_bits(uint16_t b) {
 
 template <bool FP16>
 constexpr int lo_shift() { return FP16 ? 11 : 0; }
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Polls the barrier until its phase `parity` completes or `limit_ns` pass
-// (try_wait may suspend the thread for a while on each poll).  Limit 0: one
-// non-blocking test.  Returns whether the phase completed.
-__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kWaitNs) {
-    if (limit_ns == 0) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        return ok != 0;
-    }
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (global_ns() - t0 >= limit_ns) return false;
-    }
-}
 
 // ---------------------------------------------------------------- operand A
 // A[y][k] for one image size, hi and lo parts, tiled per 128-row block.

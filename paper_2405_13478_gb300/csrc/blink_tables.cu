@@ -141,10 +141,18 @@ __global__ void k_finalize(ChanInfo *__restrict__ info, float *__restrict__ wgt)
 }
 
 // Register-accumulation schedule, step 1 (one CTA per scheduled channel):
-// hand the occupied cells out to (slot j, thread t) in order of decreasing
-// entry count, then size every (chunk, slot, warp) block of the entry stream
-// to its longest lane.  Falls back (sched = 0) when the cells need more than
-// kSchedSlots slots per thread or the padded stream outgrows its buffer.
+// rank the occupied cells by their largest per-chunk entry count and cut the
+// ranking into groups of 32 (the lanes of one warp in one slot); hand the
+// groups out to (slot j, warp w), heaviest group first to the warp with the
+// least work so far (longest-processing-time rule); then size every (chunk,
+// slot, warp) block of the entry stream to its longest lane.  A block is
+// padded to the longest lane of its chunk, so cells that peak alike share a
+// warp: on the 256-antenna station at 180^2 the stream holds ~1.6x the
+// baselines (~2x when cells are ranked by their total count), and the
+// busiest warp of a chunk -- which every chunk waits for -- carries ~5 %
+// more than the mean (~30 % when groups fill the warps in rank order).
+// Falls back (sched = 0) when the cells need more than kSchedSlots slots per
+// thread or the padded stream outgrows its buffer.
 constexpr int kHistBins = 1024;
 constexpr int kMaxItems = 4096;
 
@@ -165,17 +173,24 @@ __global__ void __launch_bounds__(1024) k_sched_slots(ChanInfo *__restrict__ inf
     __shared__ int hist[kHistBins];
     __shared__ int cursor[kHistBins];
     __shared__ int items_l[kMaxItems];
+    __shared__ int g_work[kSchedSlots * kSchedWarps], g_order[kSchedSlots * kSchedWarps],
+        g_place[kSchedSlots * kSchedWarps];
     __shared__ int s_occ, s_ok;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < kHistBins; i += nt) hist[i] = 0;
     if (tid == 0) s_occ = 0;
     __syncthreads();
     const int cells = R * n;
+    const int64_t cells_all = int64_t(n / 2) * n;
+    auto peak = [&](int idx) {  // largest count of the cell over the chunks
+        int m = 0;
+        for (int q = 0; q < Q; ++q) m = max(m, cnt_q[int64_t(q) * cells_all + idx]);
+        return min(m, kHistBins - 1);
+    };
     int occ = 0;
     for (int idx = tid; idx < cells; idx += nt) {
-        const int m = cnt[idx];
-        if (m > 0) {
-            atomicAdd(&hist[min(m, kHistBins - 1)], 1);
+        if (cnt[idx] > 0) {
+            atomicAdd(&hist[peak(idx)], 1);
             ++occ;
         }
     }
@@ -201,12 +216,55 @@ __global__ void __launch_bounds__(1024) k_sched_slots(ChanInfo *__restrict__ inf
         slot_pos[i] = kSlotEmpty;
         slot_w[i] = 0.f;
     }
+    const int G = M * kSchedWarps;  // groups of 32 ranked cells
+    for (int i = tid; i < items; i += nt) items_l[i] = 0;
+    __syncthreads();
+    // rank of every cell (kept in cell_slot for now) and, per chunk, the
+    // longest lane of every group: items_l[q G + g]
+    for (int idx = tid; idx < cells; idx += nt) {
+        if (cnt[idx] <= 0) continue;
+        const int i = atomicAdd(&cursor[peak(idx)], 1);
+        cell_slot[idx] = i;
+        for (int q = 0; q < Q; ++q) atomicMax(&items_l[q * G + i / 32], cnt_q[int64_t(q) * cells_all + idx]);
+    }
+    __syncthreads();
+    // groups by decreasing padded work (rank sort, ties by index) ...
+    for (int g = tid; g < G; g += nt) {
+        int w = 0;
+        for (int q = 0; q < Q; ++q) w += items_l[q * G + g];
+        g_work[g] = w;
+    }
+    __syncthreads();
+    for (int g = tid; g < G; g += nt) {
+        const int wg = g_work[g];
+        int rank = 0;
+        for (int h = 0; h < G; ++h) rank += g_work[h] > wg || (g_work[h] == wg && h < g);
+        g_order[rank] = g;
+    }
+    __syncthreads();
+    // ... each to the least-loaded warp that still has a free slot (lane w of
+    // warp 0 tracks warp w; key = load * 32 + w, a redux.sync min per group)
+    if (tid < 32) {
+        const int w = tid;
+        int load = 0, used = 0;
+        for (int k = 0; k < G; ++k) {
+            const int g = g_order[k];
+            const unsigned key = (w < kSchedWarps && used < M) ? unsigned(load) * 32u + unsigned(w) : 0xFFFFFFFFu;
+            const unsigned best = __reduce_min_sync(0xFFFFFFFFu, key);
+            if (w == int(best & 31u)) {
+                g_place[g] = used * kSchedWarps + w;  // slot j, warp w
+                ++used;
+                load += g_work[g];
+            }
+        }
+    }
     __syncthreads();
     for (int idx = tid; idx < cells; idx += nt) {
         const int m = cnt[idx];
         if (m <= 0) continue;
-        const int i = atomicAdd(&cursor[min(m, kHistBins - 1)], 1);
-        const int t = i % kSchedThreads, j = i / kSchedThreads;
+        const int i = cell_slot[idx];
+        const int jw = g_place[i / 32];
+        const int j = jw / kSchedWarps, t = (jw % kSchedWarps) * 32 + i % 32;
         const int r = idx / n, c = idx % n;
         uint32_t pos = uint32_t(r * S + c);
         const bool origin = idx == 0;
@@ -219,7 +277,6 @@ __global__ void __launch_bounds__(1024) k_sched_slots(ChanInfo *__restrict__ inf
         cell_slot[idx] = (j << 16) | t;
     }
     __syncthreads();
-    const int64_t cells_all = int64_t(n / 2) * n;
     for (int it = tid; it < items; it += nt) {
         const int q = it / (M * kSchedWarps), j = (it / kSchedWarps) % M, w = it % kSchedWarps;
         int L = 0;
