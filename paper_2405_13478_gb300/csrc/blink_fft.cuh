@@ -95,25 +95,25 @@ __device__ __forceinline__ c32 root_rt(int e) {
 }
 
 // ----------------------------------------------------------- complex helpers
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 cmulc(float2 a, c32 w) {
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, c32 w) {
     return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
 }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 // multiply by S*i
 template <int S>
-__device__ __forceinline__ float2 mul_si(float2 a) {
+__host__ __device__ __forceinline__ float2 mul_si(float2 a) {
     return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
 // --------------------------------------------------------- in-register DFTs
 // Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E).
 template <int B, int E, class F>
-__device__ __forceinline__ void static_for(F &&f) {
+__host__ __device__ __forceinline__ void static_for(F &&f) {
     if constexpr (B < E) {
         f(std::integral_constant<int, B>{});
         static_for<B + 1, E>(f);
@@ -122,7 +122,7 @@ __device__ __forceinline__ void static_for(F &&f) {
 
 // z * W_N^(S e) with e a compile-time exponent: the root is an immediate.
 template <int N, int S, int E>
-__device__ __forceinline__ float2 twiddle(float2 z) {
+__host__ __device__ __forceinline__ float2 twiddle(float2 z) {
     constexpr int e = ((E % N) + N) % N;
     if constexpr (e == 0) {
         return z;
@@ -145,18 +145,37 @@ constexpr int first_radix() {
     return (N % 4 == 0) ? 4 : (N % 2 == 0) ? 2 : (N % 3 == 0) ? 3 : (N % 5 == 0) ? 5 : N;
 }
 
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+// Largest factor A of N with gcd(A, N / A) == 1 and 1 < A < N (0 if none):
+// such N take the prime-factor (Good-Thomas) split, which needs no twiddles.
+template <int N>
+constexpr int coprime_factor() {
+    int best = 0;
+    for (int a = 2; a < N; ++a)
+        if (N % a == 0 && gcd_c(a, N / a) == 1) best = a;
+    return best;
+}
+
+// (a^-1) mod m for gcd(a, m) == 1, m >= 1.
+constexpr int inv_mod(int a, int m) {
+    for (int x = 0; x < m; ++x)
+        if ((a % m) * x % m == 1 % m) return x;
+    return 0;
+}
+
 template <int N, int S>
-__device__ __forceinline__ void dft(float2 (&x)[N]);
+__host__ __device__ __forceinline__ void dft(float2 (&x)[N]);
 
 template <int S>
-__device__ __forceinline__ void bfly2(float2 &a, float2 &b) {
+__host__ __device__ __forceinline__ void bfly2(float2 &a, float2 &b) {
     const float2 t = a;
     a = cadd(t, b);
     b = csub(t, b);
 }
 
 template <int S>
-__device__ __forceinline__ void bfly3(float2 (&x)[3]) {
+__host__ __device__ __forceinline__ void bfly3(float2 (&x)[3]) {
     constexpr float h = 0.866025403784438646763723170752936f;  // sin(2 pi / 3) = sqrt(3)/2
     const float2 t1 = cadd(x[1], x[2]);
     const float2 t2 = make_float2(fmaf(-0.5f, t1.x, x[0].x), fmaf(-0.5f, t1.y, x[0].y));
@@ -168,7 +187,7 @@ __device__ __forceinline__ void bfly3(float2 (&x)[3]) {
 }
 
 template <int S>
-__device__ __forceinline__ void bfly4(float2 (&x)[4]) {
+__host__ __device__ __forceinline__ void bfly4(float2 (&x)[4]) {
     const float2 s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
     const float2 s13 = cadd(x[1], x[3]), d13 = mul_si<S>(csub(x[1], x[3]));
     x[0] = cadd(s02, s13);
@@ -178,7 +197,7 @@ __device__ __forceinline__ void bfly4(float2 (&x)[4]) {
 }
 
 template <int S>
-__device__ __forceinline__ void bfly5(float2 (&x)[5]) {
+__host__ __device__ __forceinline__ void bfly5(float2 (&x)[5]) {
     // cos/sin of 2 pi/5 and 4 pi/5 from their closed forms in sqrt(5)
     constexpr float c1 = 0.309016994374947424102293417182819f;   // (sqrt5 - 1) / 4
     constexpr float c2 = -0.809016994374947424102293417182819f;  // -(sqrt5 + 1) / 4
@@ -200,7 +219,7 @@ __device__ __forceinline__ void bfly5(float2 (&x)[5]) {
 
 // Plain DFT for a prime radix without a dedicated butterfly.
 template <int P, int S>
-__device__ __forceinline__ void dft_prime(float2 (&x)[P]) {
+__host__ __device__ __forceinline__ void dft_prime(float2 (&x)[P]) {
     float2 y[P];
     static_for<0, P>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
@@ -216,7 +235,7 @@ __device__ __forceinline__ void dft_prime(float2 (&x)[P]) {
 }
 
 template <int N, int S>
-__device__ __forceinline__ void dft(float2 (&x)[N]) {
+__host__ __device__ __forceinline__ void dft(float2 (&x)[N]) {
     if constexpr (N == 1) {
         return;
     } else if constexpr (N == 2) {
@@ -229,6 +248,28 @@ __device__ __forceinline__ void dft(float2 (&x)[N]) {
         bfly5<S>(x);
     } else if constexpr (first_radix<N>() == N) {
         dft_prime<N, S>(x);
+    } else if constexpr (coprime_factor<N>() != 0) {
+        // Prime-factor split N = A B, gcd(A, B) = 1: input n = (B a + A b) mod
+        // N, length-A transforms over a, length-B transforms over b, output
+        // k = CRT(k_a, k_b) with W_N^(n k) = W_A^(a k_a) W_B^(b k_b).
+        constexpr int A = coprime_factor<N>(), B = N / A;
+        constexpr int eA = B * inv_mod(B, A), eB = A * inv_mod(A, B);  // k = (k_a eA + k_b eB) mod N
+        float2 t[B][A];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+#pragma unroll
+            for (int a = 0; a < A; ++a) t[b][a] = x[(B * a + A * b) % N];
+            dft<A, S>(t[b]);
+        }
+#pragma unroll
+        for (int ka = 0; ka < A; ++ka) {
+            float2 u[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) u[b] = t[b][ka];
+            dft<B, S>(u);
+#pragma unroll
+            for (int kb = 0; kb < B; ++kb) x[(ka * eA + kb * eB) % N] = u[kb];
+        }
     } else {
         // Decimation in time: residue classes j mod P, length-M transforms,
         // twiddles W_N^(r k), then length-P transforms across the classes.
