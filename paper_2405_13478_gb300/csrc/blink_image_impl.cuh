@@ -162,6 +162,16 @@ struct ZLayout {
     __device__ __forceinline__ static int phys(int q) { return pad ? q + (q >> 5) : q; }
 };
 
+// Four-step twiddle W_N^(n2 k1) of the inverse transform (SIGN > 0) or its
+// conjugate, read from the transposed global table: the lanes of a warp
+// differ in n2, and the constant cache would serialise their distinct
+// addresses where this read coalesces.
+template <int N, int SIGN>
+__device__ __forceinline__ c32 four_step_tw(int k1, int n2) {
+    const float2 w = __ldg(reinterpret_cast<const float2 *>(&g_four_step<N>.v[k1 * Plan<N>::N2 + n2]));
+    return c32{w.x, SIGN > 0 ? w.y : -w.y};
+}
+
 // Pass 2, step A for column pairs (j0 + jj, j0 + jj + N/2), jj < P.  `hrow(k,
 // p)` returns row k (< R) of the pass-1 output at frequency column p.  Writes
 // the four-step intermediate of pair jj to Z + jj * S.
@@ -197,7 +207,7 @@ __device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow hrow,
         float2 *zp = Z + jj * ZL::S;
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1)
-            zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], c_roots<N, +1>.v[n2 * k1]);
+            zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], four_step_tw<N, +1>(k1, n2));
     }
 }
 
@@ -365,10 +375,15 @@ __device__ __forceinline__ void small_transform(float2 *G, float2 *Z, int R, con
     constexpr int NT = SmallCfg<N>::NT, GR = SmallCfg<N>::GROUPS, P = SmallCfg<N>::P;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, S = N + 1, H = N / 2;
     const int ln = tid & 15, grp = tid >> 4;
-    // four-step twiddles W_N^(n2 k1) for n2 = ln (kept in registers)
+    // four-step twiddles W_N^(n2 k1) for n2 = ln (kept in registers), from
+    // the transposed table: coalesced loads instead of constant-cache reads,
+    // which would serialise over the 16 distinct lanes
     c32 tw[N1];
+    {
+        const int n2c = ln < N2 ? ln : N2 - 1;  // lanes >= N2 idle in the A steps
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) tw[k1] = c_roots<N, +1>.v[(ln * k1) % N];
+        for (int k1 = 0; k1 < N1; ++k1) tw[k1] = four_step_tw<N, +1>(k1, n2c);
+    }
 
     // pass 1, step A
     for (int r = grp; r < R; r += GR) {
@@ -639,16 +654,19 @@ __global__ void __launch_bounds__(SmallCfg<N>::NT, 2) k_image_sched(ImageArgs a,
     for (int j = 0; j < kSchedSlots; ++j) acc[j] = make_float2(0.f, 0.f);
     if (tid == 0) stage[K] = make_float2(0.f, 0.f);  // sentinel target
     const int per_chunk = M * kSchedWarps;
+    // stream segment bounds of chunk q: [s_beg, s_end); the end of the next
+    // chunk is requested one chunk ahead so its latency hides behind a gather
+    auto seg_start = [&](int c) { return c < Q ? int(__ldg(&meta_g[c * per_chunk].x)) : ci.stream_len; };
+    int s_beg = seg_start(0), s_end = seg_start(1);
     for (int q = 0; q < Q; ++q) {
         const int64_t rem = a.nb - int64_t(q) * K;
         const int n_q = int(rem < K ? rem : int64_t(K));
-        const int s_beg = int(meta_g[q * per_chunk].x);
-        const int s_end = q + 1 < Q ? int(meta_g[(q + 1) * per_chunk].x) : ci.stream_len;
         const int s0 = s_beg & ~7;
         stage_async<NT>(stage, vis + int64_t(q) * K, n_q, tid, pol_vis);
         cp16_async<NT>(smc + sl.ent, stream_g + s0, (s_end - s0 + 7) >> 3, tid);
         cp16_async<NT>(smc + sl.meta, meta_g + q * per_chunk, per_chunk >> 1, tid);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
+        const int s_next = seg_start(q + 2);
         stage_wait();
         __syncthreads();
         if (EPI && gl) {
@@ -697,11 +715,25 @@ __global__ void __launch_bounds__(SmallCfg<N>::NT, 2) k_image_sched(ImageArgs a,
                 acc[j].y += s.y;
             }
         }
+        s_beg = s_end;
+        s_end = s_next;
         __syncthreads();
     }
-    // the staging area becomes the grid: zero the support rows, write the slots
+    // the staging area becomes the grid: zero the support rows, write the
+    // slots.  The first kSlotBatch slot positions and weights are requested
+    // before the zeroing so their latency overlaps it.
     float2 *G = sm;
     float2 *Z = sm + size_t(a.r_alloc) * S;
+    const uint32_t *slot_pos = reinterpret_cast<const uint32_t *>(blk + lay.slot_pos);
+    const float *slot_w = reinterpret_cast<const float *>(blk + lay.slot_w);
+    constexpr int kSlotBatch = 8;
+    uint32_t sp_b[kSlotBatch];
+    float w_b[kSlotBatch];
+#pragma unroll
+    for (int j = 0; j < kSlotBatch; ++j) {
+        sp_b[j] = j < M ? __ldg(slot_pos + j * NT + tid) : kSlotEmpty;
+        w_b[j] = j < M ? __ldg(slot_w + j * NT + tid) : 0.f;
+    }
     {
         float4 *g4 = reinterpret_cast<float4 *>(G);
         const int n4 = (R * S) >> 1;
@@ -709,23 +741,19 @@ __global__ void __launch_bounds__(SmallCfg<N>::NT, 2) k_image_sched(ImageArgs a,
         if (((R * S) & 1) && tid == 0) G[R * S - 1] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    {
-        const uint32_t *slot_pos = reinterpret_cast<const uint32_t *>(blk + lay.slot_pos);
-        const float *slot_w = reinterpret_cast<const float *>(blk + lay.slot_w);
 #pragma unroll
-        for (int j = 0; j < kSchedSlots; ++j) {
-            if (j < M) {
-                const uint32_t sp = __ldg(slot_pos + j * NT + tid);
-                if (sp != kSlotEmpty) {
-                    const float wv = __ldg(slot_w + j * NT + tid);
-                    const int p = int(sp & 0x3FFFFFFFu);
-                    if (sp & kSlotOrigin) {
-                        G[p] = make_float2(2.f * acc[j].x * wv, 0.f);
-                    } else {
-                        const float2 g = make_float2(acc[j].x * wv, acc[j].y * wv);
-                        G[p] = g;
-                        if (sp & kSlotMirror) G[N - p] = make_float2(g.x, -g.y);
-                    }
+    for (int j = 0; j < kSchedSlots; ++j) {
+        if (j < M) {
+            const uint32_t sp = j < kSlotBatch ? sp_b[j] : __ldg(slot_pos + j * NT + tid);
+            if (sp != kSlotEmpty) {
+                const float wv = j < kSlotBatch ? w_b[j] : __ldg(slot_w + j * NT + tid);
+                const int p = int(sp & 0x3FFFFFFFu);
+                if (sp & kSlotOrigin) {
+                    G[p] = make_float2(2.f * acc[j].x * wv, 0.f);
+                } else {
+                    const float2 g = make_float2(acc[j].x * wv, acc[j].y * wv);
+                    G[p] = g;
+                    if (sp & kSlotMirror) G[N - p] = make_float2(g.x, -g.y);
                 }
             }
         }
@@ -873,7 +901,7 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
     float2 *zp = Z + jj * ZL::S;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-        zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], c_roots<N, +1>.v[n2 * k1]);
+        zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], four_step_tw<N, +1>(k1, n2));
 }
 
 // Pass 2 for P column pairs of one layer.  Grid: (ceil(N/2 / P), layers in wave).
@@ -961,7 +989,7 @@ __global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, c
         dft<N1, -1>(x);
         float2 *zp = Z + jj * S + n2;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) zp[N2 * k1] = k1 == 0 ? x[0] : cmulc(x[k1], root_rt<N, -1>(n2 * k1));
+        for (int k1 = 0; k1 < N1; ++k1) zp[N2 * k1] = k1 == 0 ? x[0] : cmulc(x[k1], four_step_tw<N, -1>(k1, n2));
     }
     __syncthreads();
     // step B: outputs in natural order to zn (the strip is no longer read)
