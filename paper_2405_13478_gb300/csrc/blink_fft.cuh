@@ -10,7 +10,11 @@
 //
 // Roots of unity are computed at compile time from their Taylor series after
 // an exact integer reduction of the angle to the first octant, so the short
-// transforms get their twiddles as immediate operands.
+// transforms get their twiddles as immediate operands.  The four-step
+// twiddles, whose exponent depends on the lane, come from a transposed table
+// in global memory (FourStepTable), read with coalesced loads or staged in
+// shared memory: lanes reading distinct constant-memory addresses would be
+// serialised.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -69,29 +73,6 @@ constexpr c64d unit_root(long long k, long long n) {
         case 2: return c64d{-c, -s};
         default: return c64d{s, -c};
     }
-}
-
-// W_N^e for the given transform direction (S = +1 inverse, -1 forward).
-template <int N, int S>
-struct RootTable {
-    c32 v[N];
-    constexpr RootTable() : v{} {
-        for (int e = 0; e < N; ++e) {
-            const c64d w = unit_root(e, N);
-            v[e] = c32{float(w.x), float(S * w.y)};
-        }
-    }
-};
-
-// Table for runtime exponents (the four-step twiddles W_N^(n2 k1)); the
-// forward direction uses the conjugates (root_rt).
-template <int N, int S>
-__constant__ RootTable<N, S> c_roots = RootTable<N, S>();
-
-template <int N, int S>
-__device__ __forceinline__ c32 root_rt(int e) {
-    const c32 w = c_roots<N, +1>.v[e];
-    return S > 0 ? w : c32{w.x, -w.y};
 }
 
 // ----------------------------------------------------------- complex helpers

@@ -94,35 +94,28 @@ __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begi
     }
 }
 
-// Pass 1 on rows [0, nrows) of G (row stride S): N-point inverse DFT of each
-// row in place.  Output frequency p ends at position N2 * (p % N1) + p / N1.
-// With TW (`tw`: the transposed four-step twiddles in shared memory) lanes run
-// along a row (n2 in step A, k1 in step B): with the padded layout and the
-// table's order every shared access of a warp is conflict-free.  Without it
-// lanes spread over the rows of the band, so a warp needs only a few distinct
-// twiddles from the constant cache (which serialises distinct addresses).
-template <int N, int SIGN = +1, bool PAD = false, bool TW = false>
-__device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt,
-                                         const float2 *tw = nullptr) {
+// Pass 1 on rows [0, nrows) of G (row stride S): N-point DFT (direction
+// SIGN) of each row in place.  Output frequency p ends at position
+// N2 * (p % N1) + p / N1.  `tw` holds the transposed four-step twiddles in
+// shared memory; lanes run along a row (n2 in step A, k1 in step B), so with
+// the padded layout (PAD) and the table's order every shared access of a
+// warp is conflict-free.
+template <int N, int SIGN = +1, bool PAD = false>
+__device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt, const float2 *tw) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     auto ph = [](int q) { return PAD ? RowLayout<N>::phys(q) : q; };
     // step A: N1-point transforms along stride N2, then twiddle W_N^(n2 k1)
     for (int t = tid; t < nrows * N2; t += nt) {
-        const int r = TW ? t / N2 : t % nrows, n2 = TW ? t % N2 : t / nrows;
+        const int r = t / N2, n2 = t % N2;
         float2 *row = G + r * S;
         float2 x[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) x[n1] = row[ph(N2 * n1 + n2)];
         dft<N1, SIGN>(x);
-        if constexpr (TW) {
 #pragma unroll
-            for (int k1 = 1; k1 < N1; ++k1) {
-                const float2 w = tw[k1 * N2 + n2];
-                x[k1] = cmulc(x[k1], c32{w.x, SIGN > 0 ? w.y : -w.y});
-            }
-        } else {
-#pragma unroll
-            for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmulc(x[k1], root_rt<N, SIGN>(n2 * k1));
+        for (int k1 = 1; k1 < N1; ++k1) {
+            const float2 w = tw[k1 * N2 + n2];
+            x[k1] = cmulc(x[k1], c32{w.x, SIGN > 0 ? w.y : -w.y});
         }
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) row[ph(N2 * k1 + n2)] = x[k1];
@@ -130,7 +123,7 @@ __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, i
     __syncthreads();
     // step B: N2-point transforms on contiguous runs, result kept in place
     for (int t = tid; t < nrows * N1; t += nt) {
-        const int r = TW ? t / N1 : t % nrows, k1 = TW ? t % N1 : t / nrows;
+        const int r = t / N1, k1 = t % N1;
         float2 *run = G + r * S;
         float2 y[N2];
 #pragma unroll
@@ -839,7 +832,7 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT, Plan<N>::N1 == 24 ? 2 : 3) k_
     weight_and_complete<N, true>(sm, S, r0, r0 + nrows, ci, a.wgt, tid, NT);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table in place
     __syncthreads();
-    rows_fft<N, +1, true, true>(sm, S, nrows, tid, NT, tw);
+    rows_fft<N, +1, true>(sm, S, nrows, tid, NT, tw);
     float2 *out = a.scratch + (int64_t(lw) * a.r_alloc + r0) * N;
     for (int i = tid; i < nrows * N; i += NT) {
         const int r = i / N, p = i % N;
@@ -1037,7 +1030,7 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_degrid_rows(ImageArgs a, fl
     for (int i = tid; i < nrows * N; i += NT) sm[(i / N) * S + RowLayout<N>::phys(i % N)] = in[i];
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    rows_fft<N, -1, true, true>(sm, S, nrows, tid, NT, tw);
+    rows_fft<N, -1, true>(sm, S, nrows, tid, NT, tw);
     const float *w = ci.weighting == 1 ? a.wgt + ci.wgt_off : nullptr;
     const float scale = 2.f * (((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f);
     if (a.csr && ci.csr_off >= 0) {
