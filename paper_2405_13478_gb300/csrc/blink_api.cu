@@ -27,8 +27,33 @@ struct blink_ctx {
     cudaStream_t copy_in = nullptr;   // host-buffer pipeline: host -> device copies
     cudaStream_t copy_out = nullptr;  // host-buffer pipeline: device -> host copies
     int64_t wait_ns = -1;             // bounded-wait limit of the tensor-core kernels (< 0: default)
+    void *h_stage = nullptr;          // pinned staging of plan tables (host -> device copies)
+    size_t h_stage_bytes = 0;
     std::string err;
 };
+
+namespace {
+
+// Pinned host buffer of at least `bytes` owned by the context, for the plan
+// tables' copies: from pinned memory they are asynchronous DMA, where a
+// pageable source makes the host wait for the stream to reach the copy.  The
+// contents are not kept across calls; a context is used by one host thread
+// and every plan build waits for its copies before it returns.
+void *ctx_stage(blink_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->h_stage_bytes) return ctx->h_stage;
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    const size_t want = std::max<size_t>(bytes, size_t(1) << 20);
+    if (cudaHostAlloc(&ctx->h_stage, want, cudaHostAllocDefault) != cudaSuccess) {
+        ctx->h_stage = nullptr;
+        return nullptr;
+    }
+    ctx->h_stage_bytes = want;
+    return ctx->h_stage;
+}
+
+}  // namespace
 
 struct blink_plan {
     blink_ctx *ctx = nullptr;
@@ -270,7 +295,14 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     if (!grouped)
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return h_layers[a].n_px < h_layers[b].n_px; });
-    std::vector<DevLayer> dl(static_cast<size_t>(n_layers));
+    // geometry, channel and layer tables staged in the context's pinned buffer
+    const size_t sz_geom = align_up(sizeof(ChanGeom) * size_t(p->n_chan), 256);
+    const size_t sz_info = align_up(sizeof(ChanInfo) * size_t(p->n_chan), 256);
+    char *hs = static_cast<char *>(ctx_stage(ctx, sz_geom + sz_info + sizeof(DevLayer) * size_t(std::max(n_layers, 1))));
+    if (!hs) return fail(ctx, BLINK_ERR_WORKSPACE, "pinned staging allocation failed");
+    ChanGeom *h_geom = reinterpret_cast<ChanGeom *>(hs);
+    ChanInfo *h_info = reinterpret_cast<ChanInfo *>(hs + sz_geom);
+    DevLayer *dl = reinterpret_cast<DevLayer *>(hs + sz_geom + sz_info);
     for (int k = 0; k < n_layers; ++k) {
         const int l = order[size_t(k)];
         dl[size_t(k)] = DevLayer{h_layers[l].vis_offset, h_layers[l].out_offset,
@@ -310,14 +342,13 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
             return fail(ctx, BLINK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
     if (p->n_chan) {
-        TRY(cudaMemcpyAsync(p->d_geom, p->geoms.data(), sizeof(ChanGeom) * p->geoms.size(),
-                            cudaMemcpyHostToDevice, st));
-        TRY(cudaMemcpyAsync(p->d_info, p->infos.data(), sizeof(ChanInfo) * p->infos.size(),
-                            cudaMemcpyHostToDevice, st));
+        std::copy(p->geoms.begin(), p->geoms.end(), h_geom);
+        std::copy(p->infos.begin(), p->infos.end(), h_info);
+        TRY(cudaMemcpyAsync(p->d_geom, h_geom, sizeof(ChanGeom) * p->geoms.size(), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(p->d_info, h_info, sizeof(ChanInfo) * p->infos.size(), cudaMemcpyHostToDevice, st));
     }
     if (n_layers)
-        TRY(cudaMemcpyAsync(p->d_layers, dl.data(), sizeof(DevLayer) * dl.size(),
-                            cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(p->d_layers, dl, sizeof(DevLayer) * size_t(n_layers), cudaMemcpyHostToDevice, st));
     if (p->any_uniform) TRY(cudaMemsetAsync(p->d_wgt, 0, sizeof(float) * size_t(wgt_total), st));
     TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
     if (sched_total) {
@@ -341,9 +372,9 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
                                     p->d_csr);
     if (er.status) return fail(ctx, er);
     if (p->n_chan)
-        TRY(cudaMemcpyAsync(p->infos.data(), p->d_info, sizeof(ChanInfo) * p->infos.size(),
-                            cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(h_info, p->d_info, sizeof(ChanInfo) * p->infos.size(), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
+    std::copy(h_info, h_info + p->infos.size(), p->infos.begin());
     // support rows per size group, scratch for the large-image path
     size_t scratch = 0;
     for (auto &g : p->groups) {
@@ -444,6 +475,7 @@ void blink_ctx_destroy(blink_ctx *ctx) {
         if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
         if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     }
     delete ctx;
 }

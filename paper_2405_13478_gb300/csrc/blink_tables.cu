@@ -4,6 +4,7 @@
 // do not change with time (Sec. 4.3, Eqs. 4-5), so every time step of a
 // channel shares its cells and weights.
 #include "blink_common.cuh"
+#include "blink_div.cuh"
 #include "blink_kernels.cuh"
 #include "blink_pairs.cuh"
 
@@ -12,9 +13,10 @@
 namespace blink {
 
 // One axis of the cell assignment: k = round half away from zero of (w / delta_u); false if the
-// baseline leaves the grid (|k| > N/2 - 1) or is not finite.
-__device__ __forceinline__ bool axis_cell(double w, double delta_u, int n_px, int &k) {
-    const double t = __ddiv_rn(w, delta_u);
+// baseline leaves the grid (|k| > N/2 - 1) or is not finite.  inv_du = RN(1 / delta_u): the
+// quotient is the correctly rounded one (div_by).
+__device__ __forceinline__ bool axis_cell(double w, double delta_u, double inv_du, int n_px, int &k) {
+    const double t = div_by(w, delta_u, inv_du);
     if (!(fabs(t) <= 2.0 * double(n_px))) return false;
     const long long r = llround(t);
     const long long kmax = n_px / 2 - 1;
@@ -42,10 +44,14 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
         cnt_q = reinterpret_cast<int32_t *>(sched + ci0.sched_off + lay.cnt_q);
         rank = reinterpret_cast<int32_t *>(sched + ci0.sched_off + lay.rank);
     }
-    __shared__ double s_lambda;
-    if (threadIdx.x == 0) s_lambda = __ddiv_rn(kSpeedOfLight, g.freq_hz);  // lambda = c / nu
+    __shared__ double s_lambda, s_inv_lambda, s_inv_du;
+    if (threadIdx.x == 0) {
+        s_lambda = __ddiv_rn(kSpeedOfLight, g.freq_hz);  // lambda = c / nu
+        s_inv_lambda = __drcp_rn(s_lambda);
+        s_inv_du = __drcp_rn(g.delta_u);
+    }
     __syncthreads();
-    const double lambda = s_lambda;
+    const double lambda = s_lambda, inv_lambda = s_inv_lambda, inv_du = s_inv_du;
     const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int n = g.n_px;
     int row = -1, kabs = 0, kept = 0;
@@ -54,11 +60,11 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
         baseline_pair(b, n_ant, i, j);
         const double dx = __dsub_rn(ant_xyz[3 * j + 0], ant_xyz[3 * i + 0]);
         const double dy = __dsub_rn(ant_xyz[3 * j + 1], ant_xyz[3 * i + 1]);
-        const double u = __ddiv_rn(dx, lambda);
-        const double v = __ddiv_rn(dy, lambda);
+        const double u = div_by(dx, lambda, inv_lambda);  // correctly rounded dx / lambda
+        const double v = div_by(dy, lambda, inv_lambda);
         int ku = 0, kv = 0;
         uint32_t code = kCodeDropped;
-        if (axis_cell(u, g.delta_u, n, ku) && axis_cell(v, g.delta_u, n, kv)) {
+        if (axis_cell(u, g.delta_u, inv_du, n, ku) && axis_cell(v, g.delta_u, inv_du, n, kv)) {
             // canonical half: k_v > 0, or k_v == 0 and k_u >= 0; else mirror and conjugate
             const bool mirror = kv < 0 || (kv == 0 && ku < 0);
             const int r = mirror ? -kv : kv;
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(1024) k_sched_slots(ChanInfo *__restrict__ inf
     uint2 *meta = reinterpret_cast<uint2 *>(blk + lay.meta);
     __shared__ int hist[kHistBins];
     __shared__ int cursor[kHistBins];
-    __shared__ int items_l[kMaxItems];
+    __shared__ int items_l[kMaxItems], items_p[kMaxItems];
     __shared__ int g_work[kSchedSlots * kSchedWarps], g_order[kSchedSlots * kSchedWarps],
         g_place[kSchedSlots * kSchedWarps];
     __shared__ int s_occ, s_ok;
@@ -277,27 +283,17 @@ __global__ void __launch_bounds__(1024) k_sched_slots(ChanInfo *__restrict__ inf
         cell_slot[idx] = (j << 16) | t;
     }
     __syncthreads();
-    for (int it = tid; it < items; it += nt) {
-        const int q = it / (M * kSchedWarps), j = (it / kSchedWarps) % M, w = it % kSchedWarps;
-        int L = 0;
-        for (int lane = 0; lane < 32; ++lane) {
-            const uint32_t sp = slot_pos[j * kSchedThreads + w * 32 + lane];
-            if (sp == kSlotEmpty) continue;
-            const int p = int(sp & 0x3FFFFFFFu);
-            const int cell = (p / S) * n + (p % S);
-            L = max(L, cnt_q[int64_t(q) * cells_all + cell]);
-        }
-        items_l[it] = L;
-    }
+    // block lengths in stream order: group g of chunk q is block (q, slot j, warp w)
+    for (int it = tid; it < items; it += nt) items_p[(it / G) * G + g_place[it % G]] = items_l[it];
     __syncthreads();
     if (tid == 0) {
         int64_t acc = 0, seg = 0, max_seg = 0;
         const int per_chunk = M * kSchedWarps;
         for (int it = 0; it < items; ++it) {
             if (it % per_chunk == 0) seg = 0;
-            meta[it] = make_uint2(uint32_t(acc), uint32_t(items_l[it]));
-            acc += 32 * int64_t(items_l[it]);
-            seg += 32 * int64_t(items_l[it]);
+            meta[it] = make_uint2(uint32_t(acc), uint32_t(items_p[it]));
+            acc += 32 * int64_t(items_p[it]);
+            seg += 32 * int64_t(items_p[it]);
             max_seg = max(max_seg, seg);
         }
         s_ok = acc <= lay.stream_cap;
