@@ -212,6 +212,8 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
 // Images up to this size are gridded by the fused kernels, which can use the
 // register-accumulation schedule.
 constexpr int kSchedMaxPx = 256;
+// Plan tables above this many bytes are copied from the context's pinned buffer.
+constexpr size_t kPinnedStageMin = 64 * 1024;
 
 // Builds the channel tables of a plan on `st` and waits for them.
 int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_layer *h_layers,
@@ -295,11 +297,21 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     if (!grouped)
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return h_layers[a].n_px < h_layers[b].n_px; });
-    // geometry, channel and layer tables staged in the context's pinned buffer
+    // geometry, channel and layer tables: large ones staged in the context's
+    // pinned buffer (asynchronous DMA), small ones copied from pageable memory,
+    // which the driver passes inline with less latency than a DMA
     const size_t sz_geom = align_up(sizeof(ChanGeom) * size_t(p->n_chan), 256);
     const size_t sz_info = align_up(sizeof(ChanInfo) * size_t(p->n_chan), 256);
-    char *hs = static_cast<char *>(ctx_stage(ctx, sz_geom + sz_info + sizeof(DevLayer) * size_t(std::max(n_layers, 1))));
-    if (!hs) return fail(ctx, BLINK_ERR_WORKSPACE, "pinned staging allocation failed");
+    const size_t sz_all = sz_geom + sz_info + sizeof(DevLayer) * size_t(std::max(n_layers, 1));
+    std::vector<char> h_small;
+    char *hs = nullptr;
+    if (sz_all > kPinnedStageMin) {
+        hs = static_cast<char *>(ctx_stage(ctx, sz_all));
+        if (!hs) return fail(ctx, BLINK_ERR_WORKSPACE, "pinned staging allocation failed");
+    } else {
+        h_small.resize(sz_all);
+        hs = h_small.data();
+    }
     ChanGeom *h_geom = reinterpret_cast<ChanGeom *>(hs);
     ChanInfo *h_info = reinterpret_cast<ChanInfo *>(hs + sz_geom);
     DevLayer *dl = reinterpret_cast<DevLayer *>(hs + sz_geom + sz_info);

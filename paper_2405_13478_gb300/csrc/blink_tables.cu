@@ -12,19 +12,6 @@
 
 namespace blink {
 
-// One axis of the cell assignment: k = round half away from zero of (w / delta_u); false if the
-// baseline leaves the grid (|k| > N/2 - 1) or is not finite.  inv_du = RN(1 / delta_u): the
-// quotient is the correctly rounded one (div_by).
-__device__ __forceinline__ bool axis_cell(double w, double delta_u, double inv_du, int n_px, int &k) {
-    const double t = div_by(w, delta_u, inv_du);
-    if (!(fabs(t) <= 2.0 * double(n_px))) return false;
-    const long long r = llround(t);
-    const long long kmax = n_px / 2 - 1;
-    if (r > kmax || r < -kmax) return false;
-    k = int(r);
-    return true;
-}
-
 // uv and cell for every (channel, baseline).  Grid: (ceil(B / blockDim), n_chan).
 // Writes the packed canonical cell, optionally the signed cell pair, counts
 // the entries of uniform-weighted channels and reduces the support bounds.
@@ -45,13 +32,16 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
         rank = reinterpret_cast<int32_t *>(sched + ci0.sched_off + lay.rank);
     }
     __shared__ double s_lambda, s_inv_lambda, s_inv_du;
+    __shared__ float s_s32;
     if (threadIdx.x == 0) {
         s_lambda = __ddiv_rn(kSpeedOfLight, g.freq_hz);  // lambda = c / nu
         s_inv_lambda = __drcp_rn(s_lambda);
         s_inv_du = __drcp_rn(g.delta_u);
+        s_s32 = float(s_inv_lambda * s_inv_du);
     }
     __syncthreads();
     const double lambda = s_lambda, inv_lambda = s_inv_lambda, inv_du = s_inv_du;
+    const float s32 = s_s32;
     const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int n = g.n_px;
     int row = -1, kabs = 0, kept = 0;
@@ -60,11 +50,10 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
         baseline_pair(b, n_ant, i, j);
         const double dx = __dsub_rn(ant_xyz[3 * j + 0], ant_xyz[3 * i + 0]);
         const double dy = __dsub_rn(ant_xyz[3 * j + 1], ant_xyz[3 * i + 1]);
-        const double u = div_by(dx, lambda, inv_lambda);  // correctly rounded dx / lambda
-        const double v = div_by(dy, lambda, inv_lambda);
         int ku = 0, kv = 0;
         uint32_t code = kCodeDropped;
-        if (axis_cell(u, g.delta_u, inv_du, n, ku) && axis_cell(v, g.delta_u, inv_du, n, kv)) {
+        if (axis_cell(dx, lambda, inv_lambda, g.delta_u, inv_du, s32, n, ku) &&
+            axis_cell(dy, lambda, inv_lambda, g.delta_u, inv_du, s32, n, kv)) {
             // canonical half: k_v > 0, or k_v == 0 and k_u >= 0; else mirror and conjugate
             const bool mirror = kv < 0 || (kv == 0 && ku < 0);
             const int r = mirror ? -kv : kv;
@@ -92,16 +81,32 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
             atomicAdd(cnt_r + 1 + (code == kCodeDropped ? n / 2 : int(code_row(code))), 1);
         }
     }
-    // warp reductions, then one atomic per warp
+    // warp reductions, a block reduction, then one atomic per block and field
+    // (per-warp atomics on the channel's three fields serialised in L2)
     const unsigned full = 0xFFFFFFFFu;
     const int wrow = __reduce_max_sync(full, row);
     const int wk = __reduce_max_sync(full, kabs);
     const unsigned wkept = __reduce_add_sync(full, unsigned(kept));
+    __shared__ int s_row[32], s_k[32];
+    __shared__ unsigned s_kept[32];
+    const int warp = int(threadIdx.x >> 5), n_warps = int((blockDim.x + 31) >> 5);
     if ((threadIdx.x & 31) == 0) {
-        if (wrow >= 0) atomicMax(&info[ch].rows, wrow + 1);
-        atomicMax(&info[ch].kmax_u, wk);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&info[ch].n_kept),
-                  (unsigned long long)wkept);
+        s_row[warp] = wrow;
+        s_k[warp] = wk;
+        s_kept[warp] = wkept;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int brow = -1, bk = 0;
+        unsigned long long bkept = 0;
+        for (int w = 0; w < n_warps; ++w) {
+            brow = max(brow, s_row[w]);
+            bk = max(bk, s_k[w]);
+            bkept += s_kept[w];
+        }
+        if (brow >= 0) atomicMax(&info[ch].rows, brow + 1);
+        atomicMax(&info[ch].kmax_u, bk);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&info[ch].n_kept), bkept);
     }
 }
 

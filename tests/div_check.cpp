@@ -1,6 +1,9 @@
 // Host check of blink::div_by (blink_div.cuh) against IEEE division: random
 // quotients over wide exponent ranges, the wavelength and cell-size ranges
-// of the cell assignment, exact and near-halfway quotients.  Prints "ok N".
+// of the cell assignment, exact and near-halfway quotients; then
+// blink::axis_cell (FP32 estimate, exact FP64 fallback near cell edges)
+// against its definition on 20 M offsets, most of them within 10^-12 to
+// 10^-1 cells of a cell edge or of the grid border.  Prints "ok ...".
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -55,6 +58,51 @@ int main() {
     for (double a : edge)
         for (double b : {3.0, 0.1, 1.7, 1e-5, 2.0})
             if (!check(a, b)) return 1;
-    std::printf("ok %lld\n", n);
+
+    // axis_cell (FP32 fast path + exact fallback) against its definition:
+    // k = llround(RN(RN(d / lambda) / delta_u)), dropped beyond 2N or N/2 - 1
+    long long nc = 0, slow = 0;
+    const int sizes[] = {16, 20, 24, 32, 36, 48, 64, 96, 120, 128, 160, 180, 192, 256, 360, 384, 512, 768, 1024};
+    std::uniform_real_distribution<double> fr(50e6, 350e6), dul(-3.0, 1.0), off(-1e-2, 1e-2);
+    std::uniform_int_distribution<int> si(0, 18), lg(-12, -1);
+    auto cell_check = [&](double d, double lambda, double du, int n) {
+        const double il = 1.0 / lambda, idu = 1.0 / du;
+        const float s32 = float(il * idu);
+        int k = 12345;
+        const bool got = blink::axis_cell(d, lambda, il, du, idu, s32, n, k);
+        const double t = (d / lambda) / du;
+        bool want = std::fabs(t) <= 2.0 * n;
+        long long r = 0;
+        if (want) {
+            r = std::llround(t);
+            want = r <= n / 2 - 1 && r >= -(n / 2 - 1);
+        }
+        ++nc;
+        const float tf = float(d) * s32;
+        if (!(std::fabs(tf) < 2.0f * float(n) - 1.0f) ||
+            !(std::fabs(std::fabs(tf) - std::trunc(std::fabs(tf)) - 0.5f) > std::fma(std::fabs(tf), 4e-7f, 1e-6f)))
+            ++slow;
+        if (got != want || (got && k != r)) {
+            std::printf("FAIL cell d=%.17g lambda=%.17g du=%.17g n=%d got=%d/%d want=%d/%lld\n", d, lambda, du, n,
+                        int(got), k, int(want), r);
+            return false;
+        }
+        return true;
+    };
+    for (int i = 0; i < 4000000; ++i) {
+        const double lambda = 299792458.0 / fr(rng), du = std::pow(10.0, dul(rng));
+        const int n = sizes[si(rng)];
+        // a quotient near a half-integer (or the grid edge), offset by 10^-12 .. 10^-1 cells
+        const double half = std::floor(sgn(rng) * (n / 2 + 2)) + 0.5;
+        const double eps = (sgn(rng) < 0 ? -1 : 1) * std::pow(10.0, double(lg(rng)));
+        const double d1 = (half + eps) * lambda * du;
+        const double d2 = base(rng) * 1e-2;  // anywhere
+        if (!cell_check(d1, lambda, du, n) || !cell_check(d2, lambda, du, n)) return 1;
+        if (!cell_check(std::nextafter(half * lambda * du, 1e300), lambda, du, n) ||
+            !cell_check(std::nextafter(half * lambda * du, -1e300), lambda, du, n) ||
+            !cell_check(half * lambda * du, lambda, du, n))
+            return 1;
+    }
+    std::printf("ok %lld quotients, %lld cells (%lld on the exact path)\n", n, nc, slow);
     return 0;
 }
