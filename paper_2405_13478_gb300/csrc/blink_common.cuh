@@ -85,6 +85,15 @@ constexpr uint32_t kSlotEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kSlotOrigin = 1u << 30;  // slot is the origin cell: 2 Re(sum) * w
 constexpr uint32_t kSlotMirror = 1u << 31;  // row-0 slot: also write conj at N - c
 
+// The fused single-CTA image kernels (k_image_sched, k_image_small) take a
+// group when its support rows plus the pass-2 column-pair buffer (24 pairs,
+// 384 threads in 16-lane groups) fit this shared-memory budget.
+constexpr int kSmallColPairs = 24;
+constexpr size_t kSmallSmemLimit = 200 * 1024;
+__host__ __device__ inline bool small_path_fits(int n_px, int rows) {
+    return n_px <= 256 && size_t(rows + kSmallColPairs) * size_t(n_px + 1) * 8 <= kSmallSmemLimit;
+}
+
 struct SchedLayout {
     int64_t cnt_q, rank, cell_slot, slot_pos, slot_w, meta, stream, bytes;
     int64_t stream_cap;

@@ -1088,15 +1088,10 @@ Error launch_degrid_n(const ImageArgs &a, const float *resid, float2 *dvis, cuda
     return Error{0, ""};
 }
 
-constexpr size_t kSmallSmemLimit = 200 * 1024;
-
 template <int N>
 bool use_small(int r_alloc) {
-    if constexpr (N <= 256) {
-        return small_smem<N>(r_alloc) <= kSmallSmemLimit;
-    } else {
-        return false;
-    }
+    static_assert(SmallCfg<N>::P == kSmallColPairs, "column-pair buffer of the fused kernels");
+    return small_path_fits(N, r_alloc);
 }
 
 template <int N>

@@ -173,6 +173,10 @@ __global__ void __launch_bounds__(1024) k_sched_slots(ChanInfo *__restrict__ inf
     ChanInfo ci = info[ch];
     if (ci.sched_off < 0) return;
     const int n = ci.n_px, S = n + 1, R = max(ci.rows, 1), Q = ci.n_chunks;
+    if (!small_path_fits(n, R)) {  // the channel's images take the two-kernel path
+        if (threadIdx.x == 0) info[ch].sched = 0;
+        return;
+    }
     const SchedLayout lay(n, nb, Q);
     unsigned char *blk = sched + ci.sched_off;
     const int32_t *cnt = reinterpret_cast<const int32_t *>(wgt + ci.wgt_off);
