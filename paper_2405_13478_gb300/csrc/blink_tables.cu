@@ -163,7 +163,8 @@ __global__ void k_finalize(ChanInfo *__restrict__ info, float *__restrict__ wgt)
 // busiest warp of a chunk -- which every chunk waits for -- carries ~5 %
 // more than the mean (~30 % when groups fill the warps in rank order).
 // Falls back (sched = 0) when the cells need more than kSchedSlots slots per
-// thread or the padded stream outgrows its buffer.
+// thread or the padded stream outgrows its buffer, and skips channels whose
+// support rows do not fit the fused kernels.
 constexpr int kPeakBins = 64;  // peaks above 63 share the last bucket
 constexpr int kMaxItems = 4096;
 
