@@ -30,6 +30,14 @@ UNIFORM = 1
 
 
 # --------------------------------------------------------------------- arrays
+def antennas_grid(side: int, spacing_m: float) -> np.ndarray:
+    """side x side antennas on a square grid (a maximally redundant array:
+    the shortest spacing repeats side * (side - 1) times per axis)."""
+    g = (np.arange(side) - (side - 1) / 2.0) * spacing_m
+    x, y = np.meshgrid(g, g, indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), np.zeros(side * side)], axis=1)
+
+
 def antennas_disk(n_ant: int, diameter_m: float, seed: int) -> np.ndarray:
     """Antenna positions uniform in area inside a disk, z = 0 (coplanar)."""
     rng = np.random.Generator(np.random.PCG64(seed))

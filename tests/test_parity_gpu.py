@@ -246,13 +246,32 @@ def test_ragged_baselines_and_unaligned_offsets(torch, ctx):
     xyz = np.zeros((7, 3))
     xyz[:, :2] = rng.uniform(-20, 20, (7, 2))
     B = 21
-    import torch as t
-    vis = (t.randn(5 * B + 3, dtype=t.complex64))
+    vis = synth.noise((5 * B + 3,), 1.0, 41, "cpu")
     layers = [dict(n_px=n, weighting=w, freq_hz=1.5e8, delta_u=0.6, vis_offset=off)
               for n, w, off in ((16, 0, 1), (32, 1, B + 2), (180, 0, 3 * B + 3), (256, 1, 2 * B))]
     got, _ = gpu_images(torch, ctx, xyz, layers, vis)
     want, _ = oracle_images(xyz, layers, vis)
     assert_images_close(got, want, what="ragged")
+
+
+@pytest.mark.parametrize("weighting", [0, 1])
+def test_redundant_grid_array_long_schedule_blocks(torch, ctx, weighting):
+    # A 12 x 12 grid of antennas at 2 m: 10296 baselines in two staging
+    # chunks, the shortest spacings repeat up to 132 times, so a schedule
+    # block can exceed the bank-ordered length and a cell's peak exceeds the
+    # ranking's last bucket.  Images against the oracle, bits across plans.
+    xyz = synth.antennas_grid(12, 2.0)
+    nb = 144 * 143 // 2
+    chans = (150e6, 165e6, 180e6)
+    layers = [dict(n_px=n, weighting=weighting, freq_hz=f, delta_u=0.5, vis_offset=k * nb)
+              for k, (n, f) in enumerate(zip((128, 180, 256), chans))]
+    vis = synth.noise((len(layers) * nb,), 1.0, 43, "cpu")
+    got, _ = gpu_images(torch, ctx, xyz, layers, vis)
+    want, _ = oracle_images(xyz, layers, vis)
+    assert_images_close(got, want, what="grid array")
+    again, _ = gpu_images(torch, ctx, xyz, layers, vis)
+    for a, b in zip(got, again):
+        assert np.array_equal(a, b)
 
 
 def test_normalize_flag(torch, ctx):
@@ -268,8 +287,7 @@ def test_all_baselines_dropped_gives_zero_image(torch, ctx):
     ws = synth.single_image(seed=1)
     # a cell far smaller than any baseline puts every baseline off the grid
     layers = [dict(n_px=16, weighting=1, freq_hz=160e6, delta_u=1e-9, vis_offset=0)]
-    import torch as t
-    vis = t.randn(ws.n_baselines, dtype=t.complex64)
+    vis = synth.noise((ws.n_baselines,), 1.0, 42, "cpu")
     got, wsum = gpu_images(torch, ctx, ws.ant_xyz, layers, vis)
     assert not got[0].any() and wsum[0] == 0
 
