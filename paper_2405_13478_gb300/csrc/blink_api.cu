@@ -1004,7 +1004,7 @@ int host_pipeline(blink_ctx *ctx, HostPipe &hp, const double *h_ant_xyz, int n_a
                   cudaStream_t s) {
     const int64_t nb = int64_t(n_ant) * (n_ant - 1) / 2;
     // chunks of consecutive layers bounded by the staging sizes
-    const size_t cap_vis = size_t(256) << 20, cap_out = size_t(256) << 20;
+    const size_t cap_vis = size_t(128) << 20, cap_out = size_t(128) << 20;  // 128 MB: shorter fill and drain of the copy pipeline
     std::vector<HostChunk> chunks;
     for (int l = 0; l < n_layers;) {
         HostChunk c{l, l, INT64_MAX, 0, INT64_MAX, 0};

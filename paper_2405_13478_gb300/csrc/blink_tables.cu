@@ -423,7 +423,7 @@ __device__ void bank_order_warp(uint16_t *col, uint32_t m, uint16_t sent, uint32
         mask |= ((cnt_lo >> (8 * b)) & 0xFFu ? 1u : 0u) << b;
         mask |= ((cnt_hi >> (8 * b)) & 0xFFu ? 1u : 0u) << (b + 8);
     }
-    for (uint32_t k = 0; k < m; ++k) {
+    for (uint32_t k = 0; k + 1 < m; ++k) {  // the last step is each lane's last entry
         words[lane] = mask;
         __syncwarp();
         const uint32_t left = m - k;
