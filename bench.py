@@ -38,7 +38,7 @@ CSRC = os.path.join(ROOT, "paper_2405_13478_gb300", "csrc")
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=60)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--e2e-steps", type=int, default=5)
@@ -158,16 +158,31 @@ class ClockSampler:
         self.proc = None
         self.path = None
 
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return f.read().splitlines()
+        except OSError:
+            return []
+
     def start(self):
+        """Starts sampling every 50 ms and returns once the sampler writes, so
+        the samples taken after this call fall in the timed region."""
         fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
         os.close(fd)
+        self.skip = 0
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while not self._lines() and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.skip = len(self._lines())
 
     def stop(self):
         if not self.proc:
@@ -177,21 +192,30 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        lines = self._lines()
+        os.unlink(self.path)
+        # samples written during the region; the last one before it if none
+        inside = lines[self.skip:]
+        fallback = not inside
+        if fallback:
+            inside = lines[max(0, self.skip - 1):self.skip]
         rows = []
-        for ln in open(self.path):
+        for ln in inside:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) >= 9:
                 rows.append(parts)
-        os.unlink(self.path)
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None,
+               "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+               "samples": len(rows)}
+        if fallback:
+            out["sampled_just_before_region"] = True
+        return out
 
 
 def cpu_baseline(ws, seconds: float = 10.0):
