@@ -590,7 +590,10 @@ def run_single(args):
     _line(args, 1e3 / ms, ms, {"workload": "single 256^2 image, 128 antennas in a 3 km disk, 8128 "
                                            "baselines, 160 MHz, natural weighting"}, clk,
           {"latency_us": ms * 1e3, "latency_plan_cached_us": ms_k * 1e3, "err_vs_oracle": err,
-           "gpu_launches": 5 * args.steps})
+           # per call: k_cells, the four schedule kernels (the schedule builder
+           # returns at once: a 256^2 image of this array takes the two-kernel
+           # path), k_csr_scan, k_csr_fill, k_finalize, then k_rows and k_cols
+           "gpu_launches": 10 * args.steps})
     plan.close()
     ctx.close()
 
