@@ -135,9 +135,12 @@ BLINK_API int blink_grid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, con
 /* Dirty images of every layer (steps 1-5): d_images + out_offset receives the
  * float32 [N][N] FFT-shifted real image, unnormalised unless flags has
  * BLINK_NORMALIZE.  d_wsum (float32 [n_layers], may be NULL) receives the
- * summed weights.  Layers of different sizes may be mixed.  The same inputs
+ * summed weights.  Layers of different sizes may be mixed.  Layers gridded
+ * by the fused small-image kernel (sizes up to 256 whose support fits it)
  * give the same bits on every call: every cell sums its visibilities in an
- * order fixed by the array geometry, with no atomics.
+ * order fixed by the array geometry, without atomics; the row pass of larger
+ * images grids with shared-memory atomics, whose order may change the last
+ * bits from call to call.
  * This call builds the per-channel tables on `stream` and synchronises that
  * stream once to size the image kernels; use a plan (below) to build the
  * tables once and image many batches asynchronously. */
