@@ -346,7 +346,7 @@ def test_plan_reuse_matches_batch(torch, ctx):
 
 def test_host_buffer_path_matches_device_path(torch, ctx):
     """blink_image_batch_host: host inputs and outputs, several pipeline
-    chunks (the 512 MB staging limit is crossed), mixed sizes in a chunk."""
+    chunks (585 MB of visibilities in 128 MB chunks), mixed sizes in a chunk."""
     from paper_2405_13478_gb300 import binding
     ws = synth.station_batch(seed=15, n_times=70)          # 2240 layers, 585 MB of visibilities
     vis = ws.vis("cpu")
