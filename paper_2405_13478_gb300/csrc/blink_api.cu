@@ -29,6 +29,8 @@ struct blink_ctx {
     int64_t wait_ns = -1;             // bounded-wait limit of the tensor-core kernels (< 0: default)
     void *h_stage = nullptr;          // pinned staging of plan tables (host -> device copies)
     size_t h_stage_bytes = 0;
+    cudaStream_t aux = nullptr;       // second stream of the large-image path
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 };
 
@@ -445,6 +447,9 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.kmax = g.kmax;
     a.force_path = g.force_path;
     a.wave_budget = g.wave_budget;
+    a.aux = p->ctx->aux;
+    a.ev_fork = p->ctx->ev_fork;
+    a.ev_join = p->ctx->ev_join;
     return a;
 }
 
@@ -475,6 +480,12 @@ int blink_ctx_create(blink_ctx **out, int device) {
     }
     uint64_t keep = std::numeric_limits<uint64_t>::max();
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        blink_ctx_destroy(ctx);
+        return BLINK_ERR_CUDA;
+    }
     *out = ctx;
     return BLINK_OK;
 }
@@ -486,6 +497,9 @@ void blink_ctx_destroy(blink_ctx *ctx) {
         cudaDeviceSynchronize();
         if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
         if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
+        if (ctx->aux) cudaStreamDestroy(ctx->aux);
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     }

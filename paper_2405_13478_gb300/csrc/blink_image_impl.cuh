@@ -1131,12 +1131,41 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     BLINK_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_cols)));
     const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
     const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
+    // With an auxiliary stream each wave is split in two halves, one per
+    // stream, each with its own half of the scratch: the row and column passes
+    // of one half fill the launch gaps and partial last waves of CTAs of the
+    // other.  The auxiliary stream is forked from `st` and joined back to it.
+    const bool two = a.aux && a.ev_fork && a.ev_join && wave >= 2;
+    if (two) {
+        BLINK_CUDA_TRY(cudaEventRecord(a.ev_fork, st));
+        BLINK_CUDA_TRY(cudaStreamWaitEvent(a.aux, a.ev_fork, 0));
+    }
+    auto pass = [&](const ImageArgs &b, int l0, int cnt, cudaStream_t s) -> Error {
+        k_rows<N><<<dim3(bands, unsigned(cnt)), C::NT, smem_rows, s>>>(b, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        cols<<<dim3(pchunks, unsigned(cnt)), C::NT, smem_cols, s>>>(b, l0, static_cast<float *>(b.out), b.ref);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        return Error{0, ""};
+    };
+    const int half = wave / 2;  // scratch slots [0, half) on st, [half, wave) on aux
+    ImageArgs hb = a;
+    hb.scratch = a.scratch + size_t(half) * a.r_alloc * N;
     for (int l0 = 0; l0 < a.n_layers; l0 += wave) {
         const int cnt = std::min(wave, a.n_layers - l0);
-        k_rows<N><<<dim3(bands, unsigned(cnt)), C::NT, smem_rows, st>>>(a, l0);
-        BLINK_CUDA_TRY(cudaGetLastError());
-        cols<<<dim3(pchunks, unsigned(cnt)), C::NT, smem_cols, st>>>(a, l0, static_cast<float *>(a.out), a.ref);
-        BLINK_CUDA_TRY(cudaGetLastError());
+        if (two && cnt >= 2) {
+            const int h = std::min(half, cnt - 1);
+            Error e = pass(a, l0, h, st);
+            if (e.status) return e;
+            e = pass(hb, l0 + h, cnt - h, a.aux);
+            if (e.status) return e;
+        } else {
+            Error e = pass(a, l0, cnt, st);
+            if (e.status) return e;
+        }
+    }
+    if (two) {
+        BLINK_CUDA_TRY(cudaEventRecord(a.ev_join, a.aux));
+        BLINK_CUDA_TRY(cudaStreamWaitEvent(st, a.ev_join, 0));
     }
     return Error{0, ""};
 }

@@ -51,6 +51,10 @@ struct ImageArgs {
     const float *ref;           // reference images, addressed like the output
     int64_t wait_ns = -1;       // first-wait limit of the tensor-core kernels (< 0: default 1 s)
     int kmax = 0;               // max |k_u| of the group's channels (compact support of pass 1)
+    // optional second stream for the large-image path (forked from and joined
+    // back to the launch stream with these two events); null: one stream
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // Per-size launchers (defined in blink_image_impl.cuh, instantiated once per
