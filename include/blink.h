@@ -105,7 +105,10 @@ BLINK_API int blink_supported_sizes(int32_t *sizes, int cap);
 
 /* Creates a context on CUDA device `device` (makes it current for the call).
  * The context owns a device workspace that grows on demand and is freed by
- * blink_ctx_destroy.  *out is NULL on failure. */
+ * blink_ctx_destroy, and an auxiliary stream: large images run half of each
+ * wave of layers on it, forked from and joined back to the caller's stream
+ * with events, so every call stays ordered on the caller's stream (and can
+ * be captured in a CUDA graph).  *out is NULL on failure. */
 BLINK_API int blink_ctx_create(blink_ctx **out, int device);
 BLINK_API void blink_ctx_destroy(blink_ctx *ctx);
 
