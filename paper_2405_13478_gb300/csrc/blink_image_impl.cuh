@@ -1078,12 +1078,38 @@ Error launch_degrid_n(const ImageArgs &a, const float *resid, float2 *dvis, cuda
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_r)));
     const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
     const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
+    // waves split over the auxiliary stream as in the forward path
+    const bool two = a.aux && a.ev_fork && a.ev_join && wave >= 2;
+    if (two) {
+        BLINK_CUDA_TRY(cudaEventRecord(a.ev_fork, st));
+        BLINK_CUDA_TRY(cudaStreamWaitEvent(a.aux, a.ev_fork, 0));
+    }
+    auto pass = [&](const ImageArgs &b, int l0, int cnt, cudaStream_t s) -> Error {
+        k_degrid_cols<N><<<dim3(pchunks, unsigned(cnt)), C::NT, smem_c, s>>>(b, resid, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_degrid_rows<N><<<dim3(bands, unsigned(cnt)), LargeCfg<N>::NT, smem_r, s>>>(b, dvis, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        return Error{0, ""};
+    };
+    const int half = wave / 2;
+    ImageArgs hb = a;
+    hb.scratch = a.scratch + size_t(half) * a.r_alloc * N;
     for (int l0 = 0; l0 < a.n_layers; l0 += wave) {
         const int cnt = std::min(wave, a.n_layers - l0);
-        k_degrid_cols<N><<<dim3(pchunks, unsigned(cnt)), C::NT, smem_c, st>>>(a, resid, l0);
-        BLINK_CUDA_TRY(cudaGetLastError());
-        k_degrid_rows<N><<<dim3(bands, unsigned(cnt)), LargeCfg<N>::NT, smem_r, st>>>(a, dvis, l0);
-        BLINK_CUDA_TRY(cudaGetLastError());
+        if (two && cnt >= 2) {
+            const int h = std::min(half, cnt - 1);
+            Error e = pass(a, l0, h, st);
+            if (e.status) return e;
+            e = pass(hb, l0 + h, cnt - h, a.aux);
+            if (e.status) return e;
+        } else {
+            Error e = pass(a, l0, cnt, st);
+            if (e.status) return e;
+        }
+    }
+    if (two) {
+        BLINK_CUDA_TRY(cudaEventRecord(a.ev_join, a.aux));
+        BLINK_CUDA_TRY(cudaStreamWaitEvent(st, a.ev_join, 0));
     }
     return Error{0, ""};
 }
