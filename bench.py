@@ -108,11 +108,13 @@ def rank_workload(rank: int, n_times: int):
     return synth.station_batch(seed=rank, n_times=n_times)
 
 
-# Sources the dominant kernel (the fused 180^2 image kernel) is compiled from,
-# plus the plan tables it reads: the committed DRAM-traffic figure is valid only
-# while these are unchanged.
+# Sources the dominant kernel (the fused 180^2 image kernel, its launcher and
+# argument struct) is compiled from, plus the schedule builder whose tables it
+# reads: the committed DRAM-traffic figure is valid only while these are
+# unchanged.  The large-image, tensor-core and adjoint kernels live in other
+# files and do not void it.
 KERNEL_SOURCES = ("blink_common.cuh", "blink_fft.cuh", "blink_kernels.cuh", "blink_pairs.cuh",
-                  "blink_image_impl.cuh", "blink_image_180_192.cu", "blink_tables.cu")
+                  "blink_image_small.cuh", "blink_tables.cu")
 
 
 def kernel_source_hash() -> str:
@@ -132,9 +134,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None if there is none for the current kernel sources."""
+def ncu_record():
+    """The committed ncu summary of the dominant kernel (DRAM bytes and FP32
+    instruction counts per layer), or None if it was taken from other kernel
+    sources than the current ones."""
     path = os.path.join(ROOT, "profiles", "k_image_sched_180_traffic.json")
     try:
         with open(path) as f:
@@ -143,7 +146,49 @@ def ncu_traffic():
         return None
     if d.get("csrc_sha") != kernel_source_hash():
         return None
-    return float(d["dram_bytes_per_layer"])
+    return d
+
+
+def ncu_traffic():
+    """DRAM bytes per layer of the dominant kernel from the committed ncu
+    summary, or None if there is none for the current kernel sources."""
+    d = ncu_record()
+    return None if d is None else float(d["dram_bytes_per_layer"])
+
+
+def fft_flops(n: int) -> float:
+    """Flops of one complex n-point FFT by the usual 5 n log2 n convention."""
+    import math
+    return 5.0 * n * math.log2(n)
+
+
+def image_flops(n_px: int, rows: int, entries: int) -> float:
+    """Algorithmic FP32 flops of one dirty image on the half-plane path:
+    `entries` complex additions of gridding (2 flops each), pass 1 on the
+    `rows` support rows, pass 2 as n_px/2 paired transforms (each gives two
+    real image columns)."""
+    return 2.0 * entries + (rows + n_px // 2) * fft_flops(n_px)
+
+
+def support_rows(ant_xyz, freqs_hz, delta_u, n_px):
+    """Support rows R of each channel (largest |k_v| + 1 over the baselines,
+    capped at n_px/2) -- bookkeeping for the flop count only."""
+    import numpy as np
+    i, j = np.triu_indices(len(ant_xyz), k=1)
+    dy = ant_xyz[j, 1] - ant_xyz[i, 1]
+    out = []
+    for f in np.atleast_1d(freqs_hz):
+        k = np.rint(np.abs(dy) * f / 299792458.0 / delta_u).max()
+        out.append(int(min(k, n_px // 2 - 1)) + 1)
+    return out
+
+
+def alu_peak():
+    """Measured FP32 and FP64 FMA rates of this GPU (TFLOP/s)."""
+    from paper_2405_13478_gb300 import binding
+    import torch
+    dev = torch.cuda.current_device()
+    return binding.fma_peak_tflops(dev, 32), binding.fma_peak_tflops(dev, 64)
 
 
 class ClockSampler:
@@ -337,6 +382,48 @@ def epilogue_variants(torch, binding, ctx, ws, d_xyz, larr, vis, images, wsum, l
                                            "at the store"}}
 
 
+def link_ceiling(torch, h_vis, h_img, chunk=128 << 20):
+    """What the host link alone allows for the e2e step: plain pinned-memory
+    cudaMemcpyAsync copies of the same bytes (the visibilities host -> device
+    and the images device -> host, in 128 MB pieces like the library's
+    pipeline), each direction alone and both at once on two streams."""
+    src = torch.view_as_real(h_vis).reshape(-1).view(torch.uint8)
+    dst = h_img.reshape(-1).view(torch.uint8)
+    d_in = torch.empty(chunk, dtype=torch.uint8, device="cuda")
+    d_out = torch.zeros(chunk, dtype=torch.uint8, device="cuda")
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def h2d():
+        with torch.cuda.stream(s_in):
+            for o in range(0, src.numel(), chunk):
+                m = min(chunk, src.numel() - o)
+                d_in[:m].copy_(src[o:o + m], non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s_out):
+            for o in range(0, dst.numel(), chunk):
+                m = min(chunk, dst.numel() - o)
+                dst[o:o + m].copy_(d_out[:m], non_blocking=True)
+
+    def timed(*fns):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for f in fns:
+            f()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0)
+
+    timed(h2d, d2h)  # warm
+    ms_in = min(timed(h2d) for _ in range(2))
+    ms_out = min(timed(d2h) for _ in range(2))
+    ms_both = min(timed(h2d, d2h) for _ in range(2))
+    del d_in, d_out
+    return {"link_gbs_h2d": src.numel() / ms_in / 1e6, "link_gbs_d2h": dst.numel() / ms_out / 1e6,
+            "link_ms_both": ms_both,
+            "link_method": "plain pinned cudaMemcpyAsync of the same bytes in 128 MB pieces, H2D and "
+                           "D2H on two streams at once (best of 2); frac_of_link = that time / e2e time"}
+
+
 def run_reference(args):
     import synth
 
@@ -466,6 +553,8 @@ def run_ours(args):
     e2e_ms = max_over_ranks(statistics.median(calls_ms), pg, "cuda")
     e2e_value = whole_job_rate(L, world, 1, e2e_ms)
     h2d_bytes = int(h_vis.numel() * 8)
+    d2h_bytes = int(images.numel() * 4 + wsum.numel() * 4)
+    link = link_ceiling(torch, h_vis, h_img) if rank == 0 else None
     del h_vis
 
     cpu = None
@@ -477,7 +566,31 @@ def run_ours(args):
         bytes_per_layer = B * 8 + N * N * 4          # vis in + image out (algorithmic)
         kms = statistics.mean(kern_ms)
         achieved = L * bytes_per_layer / (kms / 1e3) / 1e9
-        tr = ncu_traffic()
+        rec = ncu_record()
+        tr = None if rec is None else float(rec["dram_bytes_per_layer"])
+        # FP32 arithmetic of the same kernel against the measured FMA peak
+        rows = support_rows(ws.ant_xyz, ws.freqs_hz, float(ws.delta_u[0]), N)
+        flops_layer = statistics.mean(image_flops(N, r, 2 * B) for r in rows)
+        try:
+            p32, p64 = alu_peak()
+        except Exception:
+            p32 = p64 = None
+        alu = {"unit": "TFLOP/s", "flops_per_image": flops_layer,
+               "convention": "5 n log2 n per complex n-point FFT on the support rows and the n/2 paired "
+                             "columns, plus 2 flops per gridded entry",
+               "achieved": L * flops_layer / (kms / 1e3) / 1e12, "peak": p32,
+               "peak_kind": "measured (blink_probe_fma_peak, FP32 FMA)", "fp64_peak": p64}
+        alu["frac"] = alu["achieved"] / p32 if p32 else None
+        if rec is not None and rec.get("fp32_flops_per_layer"):
+            alu["executed_fp32_flops_per_image"] = rec["fp32_flops_per_layer"]
+            alu["executed_achieved"] = L * rec["fp32_flops_per_layer"] / (kms / 1e3) / 1e12
+            alu["executed_frac"] = alu["executed_achieved"] / p32 if p32 else None
+        variants = variants or {}
+        if not args.no_variants:
+            del images, wsum
+            torch.cuda.empty_cache()
+            variants["workloads"] = secondary_workloads(torch, binding, ctx, min(args.steps, 20),
+                                                        args.warmup)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -494,7 +607,8 @@ def run_ours(args):
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": (tr * L) if tr is not None else None,
                          "kernel": KERNEL, "kernel_ms": kms,
-                         "algorithmic_bytes_per_launch": L * bytes_per_layer},
+                         "algorithmic_bytes_per_launch": L * bytes_per_layer,
+                         "alu": alu},
             "cpu_baseline": cpu,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT,
@@ -502,9 +616,12 @@ def run_ours(args):
                               "(pinned host buffers) after one warm-up call",
                     "calls_ms": [round(c, 2) for c in calls_ms],
                     "h2d_bytes_per_step": h2d_bytes,
-                    "d2h_bytes_per_step": int(images.numel() * 4 + wsum.numel() * 4)},
+                    "d2h_bytes_per_step": d2h_bytes},
             "gpu_launches": 7 * args.steps,  # 6 table kernels + 1 fused image kernel per step
         }
+        if link:
+            out["e2e"].update(link)
+            out["e2e"]["frac_of_link"] = link["link_ms_both"] / e2e_ms
         print(json.dumps(out), flush=True)
     ctx.close()
     if pg:
@@ -512,10 +629,11 @@ def run_ours(args):
 
 
 # --------------------------------------------------------------------------
-# Secondary workloads (one JSON line each, same schema): the single-image
-# latency, the uneven mixed-size batch, the tensor-core transform modes and
-# the differentiable path.  Single GPU (rank 0 only); not part of the
-# default run.
+# Secondary workloads: the single-image latency, the uneven mixed-size batch,
+# the tensor-core transform modes and the differentiable path.  Each measure_*
+# returns a dict; the default run reports them (at reduced time steps) under
+# "variants" of its line, and `--workload NAME` prints a full-size line of its
+# own with the same schema.  Single GPU (rank 0 only).
 def _setup_single():
     import torch
 
@@ -570,12 +688,24 @@ def _sample_error(torch, ws, layers, vis_flat, out, picks):
     return worst
 
 
-def run_single(args):
+def _hbm_roofline(nbytes, ms, kernel, per_unit=None):
+    peak, kind = measured_peaks()
+    gbs = nbytes / (ms / 1e3) / 1e9
+    out = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+           "peak_kind": kind, "traffic": None, "kernel": kernel, "algorithmic_bytes_per_launch": nbytes}
+    if per_unit:
+        out["algorithmic_bytes_per_image"] = per_unit
+    return out
+
+
+def _layer_array(binding, layers):
+    return binding.layer_array([d["n_px"] for d in layers], [d["weighting"] for d in layers],
+                               [d["freq_hz"] for d in layers], [d["delta_u"] for d in layers],
+                               [d["vis_offset"] for d in layers], [d["out_offset"] for d in layers])
+
+
+def measure_single(torch, binding, ctx, steps, warmup):
     """One 256^2 image of a 128-antenna 3 km array: latency of a whole call."""
-    env = _setup_single()
-    if env is None:
-        return
-    torch, binding, ctx = env
     import synth
 
     ws = synth.single_image(seed=0)
@@ -583,43 +713,32 @@ def run_single(args):
     vis = ws.vis("cuda").reshape(-1)
     out = torch.empty(total, device="cuda")
     d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
-    ms, clk = _time_steps(torch, lambda: ctx.image_batch(d_xyz, layers, vis, out), args.steps, args.warmup)
+    ms, clk = _time_steps(torch, lambda: ctx.image_batch(d_xyz, layers, vis, out), steps, warmup)
     plan = ctx.plan(d_xyz, layers)
-    ms_k, _ = _time_steps(torch, lambda: plan.image(vis, out), args.steps, args.warmup)
+    ms_k, _ = _time_steps(torch, lambda: plan.image(vis, out), steps, warmup)
     err = _sample_error(torch, ws, layers, vis, out, [0])
-    _line(args, 1e3 / ms, ms, {"workload": "single 256^2 image, 128 antennas in a 3 km disk, 8128 "
-                                           "baselines, 160 MHz, natural weighting"}, clk,
-          {"latency_us": ms * 1e3, "latency_plan_cached_us": ms_k * 1e3, "err_vs_oracle": err,
-           # per call: k_cells, the four schedule kernels (the schedule builder
-           # returns at once: a 256^2 image of this array takes the two-kernel
-           # path), k_csr_scan, k_csr_fill, k_finalize, then k_rows and k_cols
-           "gpu_launches": 10 * args.steps})
     plan.close()
-    ctx.close()
+    return {"workload": "single 256^2 image, 128 antennas in a 3 km disk, 8128 baselines, 160 MHz, "
+                        "natural weighting (latency of one blink_image_batch call; no roofline claim)",
+            "images_per_s": 1e3 / ms, "ms_per_step": ms, "latency_us": ms * 1e3,
+            "latency_plan_cached_us": ms_k * 1e3, "err_vs_oracle": err, "clocks": clk,
+            "l2": "inputs fit in L2 (latency of a single call)"}
 
 
-def run_uneven(args):
-    """Uneven batch: 768 channels x T steps, 128^2..1024^2 by channel group."""
-    env = _setup_single()
-    if env is None:
-        return
-    torch, binding, ctx = env
+def measure_uneven(torch, binding, ctx, n_t, steps, warmup):
+    """Uneven batch: 768 channels x n_t steps, 128^2..1024^2 by channel group."""
     import synth
 
-    n_t = args.n_times or 100
     ws = synth.uneven_batch(seed=0, n_times=n_t)
-    layers = ws.layers()
-    layers, total = binding.layer_out_offsets(layers)
-    larr = binding.layer_array([d["n_px"] for d in layers], [d["weighting"] for d in layers],
-                               [d["freq_hz"] for d in layers], [d["delta_u"] for d in layers],
-                               [d["vis_offset"] for d in layers], [d["out_offset"] for d in layers])
+    layers, total = binding.layer_out_offsets(ws.layers())
+    larr = _layer_array(binding, layers)
     free, _ = torch.cuda.mem_get_info()
     if total * 4 + ws.n_layers * ws.n_baselines * 8 > 0.85 * free:
         raise SystemExit(f"uneven with {n_t} time steps does not fit in device memory; pass --n-times")
     vis = ws.vis("cuda").reshape(-1)
     out = torch.empty(total, device="cuda")
     d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
-    ms, clk = _time_steps(torch, lambda: ctx.image_batch(d_xyz, larr, vis, out), args.steps, args.warmup)
+    ms, clk = _time_steps(torch, lambda: ctx.image_batch(d_xyz, larr, vis, out), steps, warmup)
     t_s = min(20, n_t - 1)  # the pulse reaches the top channel at step 20
     picks = [t_s * 768 + c for c in (0, 100, 200, 300, 767)]
     err = _sample_error(torch, ws, layers, vis, out, picks)
@@ -627,55 +746,47 @@ def run_uneven(args):
     # the same batch through a reused plan: default kernels, autotuned kernels,
     # and the autotuned launches replayed as one CUDA graph
     plan = ctx.plan(d_xyz, larr)
-    ms_plan, _ = _time_steps(torch, lambda: plan.image(vis, out), args.steps, args.warmup)
+    ms_plan, _ = _time_steps(torch, lambda: plan.image(vis, out), steps, warmup)
     plan.autotune(vis, out)
-    ms_tuned, _ = _time_steps(torch, lambda: plan.image(vis, out), args.steps, args.warmup)
+    ms_tuned, _ = _time_steps(torch, lambda: plan.image(vis, out), steps, warmup)
     plan.capture(vis, out)
-    ms_graph, _ = _time_steps(torch, lambda: plan.replay(), args.steps, args.warmup)
+    ms_graph, _ = _time_steps(torch, lambda: plan.replay(), steps, warmup)
     err_graph = _sample_error(torch, ws, layers, vis, out, picks)
     tuning = plan.tuning()
     plan.close()
     nbytes = L * ws.n_baselines * 8 + total * 4
-    peak, kind = measured_peaks()
-    gbs = nbytes / (ms / 1e3) / 1e9
-    _line(args, L / (ms / 1e3), ms,
-          {"workload": f"uneven batch: 128 antennas in a 3 km disk, 768 channels x {n_t} steps, "
-                       "images 128/256/512/1024 by channel group, dispersed pulse + noise",
-           "layers": L, "image_floats": total}, clk,
-          {"err_vs_oracle": err,
-           "variants": {"planned": {"images_per_s": L / (ms_plan / 1e3), "ms_per_step": ms_plan},
-                        "autotuned": {"images_per_s": L / (ms_tuned / 1e3), "ms_per_step": ms_tuned},
-                        "autotuned_graph": {"images_per_s": L / (ms_graph / 1e3), "ms_per_step": ms_graph,
-                                            "err_vs_oracle": err_graph,
-                                            "hbm_frac": nbytes / (ms_graph / 1e3) / 1e9 / peak},
-                        "tuning": [{"n_px": n, "path": ["default", "scheduled fused", "atomic fused",
-                                                        "two-kernel"][p_], "wave_bytes": w}
-                                   for n, p_, w in tuning]},
-           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                        "peak_kind": kind, "traffic": None, "kernel": "whole step (all sizes)",
-                        "algorithmic_bytes_per_launch": nbytes}})
-    ctx.close()
+    peak, _ = measured_peaks()
+    del vis, out
+    return {"workload": f"uneven batch: 128 antennas in a 3 km disk, 768 channels x {n_t} steps, "
+                        "images 128/256/512/1024 by channel group, dispersed pulse + noise",
+            "layers": L, "image_floats": total, "images_per_s": L / (ms / 1e3), "ms_per_step": ms,
+            "err_vs_oracle": err, "clocks": clk,
+            "l2": f"inputs larger than L2 ({total * 4 / 1e9:.1f} GB of images per step)",
+            "roofline": _hbm_roofline(nbytes, ms, "whole step, plan build included (all sizes)"),
+            "planned": {"images_per_s": L / (ms_plan / 1e3), "ms_per_step": ms_plan,
+                        "hbm_frac": nbytes / (ms_plan / 1e3) / 1e9 / peak},
+            "autotuned": {"images_per_s": L / (ms_tuned / 1e3), "ms_per_step": ms_tuned,
+                          "hbm_frac": nbytes / (ms_tuned / 1e3) / 1e9 / peak},
+            "autotuned_graph": {"images_per_s": L / (ms_graph / 1e3), "ms_per_step": ms_graph,
+                                "err_vs_oracle": err_graph,
+                                "hbm_frac": nbytes / (ms_graph / 1e3) / 1e9 / peak},
+            "tuning": [{"n_px": n, "path": ["default", "scheduled fused", "atomic fused",
+                                            "two-kernel"][p_], "wave_bytes": w} for n, p_, w in tuning]}
 
 
-def run_station512(args):
+def measure_station512(torch, binding, ctx, n_t, steps, warmup):
     """Station 512^2 batch: FP32 FFT against the tensor-core modes."""
-    env = _setup_single()
-    if env is None:
-        return
-    torch, binding, ctx = env
     import synth
 
-    n_t = args.n_times or 2000
     ws = synth.station_512(seed=0, n_times=n_t)
-    layers = ws.layers()
-    layers, total = binding.layer_out_offsets(layers)
-    larr = binding.layer_array([d["n_px"] for d in layers], [d["weighting"] for d in layers],
-                               [d["freq_hz"] for d in layers], [d["delta_u"] for d in layers],
-                               [d["vis_offset"] for d in layers], [d["out_offset"] for d in layers])
+    layers, total = binding.layer_out_offsets(ws.layers())
+    larr = _layer_array(binding, layers)
     vis = ws.vis("cuda").reshape(-1)
     out = torch.empty(total, device="cuda")
     d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
     L = len(layers)
+    per_image = ws.n_baselines * 8 + 512 * 512 * 4
+    peak, _ = measured_peaks()
     modes = {"fft_fp32": 0x00, "bf16": 0x10, "bf16x3": 0x20, "fp16": 0x30, "fp16x3": 0x40}
     res, clk0 = {}, None
     for name, flag in modes.items():
@@ -683,41 +794,43 @@ def run_station512(args):
             plan = binding.Plan(ctx, d_xyz, larr)
             plan.image(vis, out, None, flag)
             plan.close()
-        ms, clk = _time_steps(torch, step, args.steps, args.warmup)
+        ms, clk = _time_steps(torch, step, steps, warmup)
         clk0 = clk0 or clk
         err = _sample_error(torch, ws, layers, vis, out, [0, L // 2, L - 1])
-        res[name] = {"images_per_s": L / (ms / 1e3), "ms_per_step": ms, "err_vs_oracle": err}
-    # tensor work of the split mode: 3 products of 512 x 512 x K, K = 2 * 48
-    flops = 3 * 2 * 512 * 512 * 96 * L
+        res[name] = {"images_per_s": L / (ms / 1e3), "ms_per_step": ms, "err_vs_oracle": err,
+                     "hbm_frac": L * per_image / (ms / 1e3) / 1e9 / peak}
+    # tensor work of the split mode: 3 products of pass 2 (512 x 512 x 2 Rp,
+    # Rp = 48) and of pass 1 (2 x 512 columns x 2 Kc, Kc = 96, per 64-row half
+    # of a 128-row tile)
+    flops = 3 * (2 * 512 * 512 * 96 + 2 * 64 * 1024 * 192) * L
     tf = flops / (res["bf16x3"]["ms_per_step"] / 1e3) / 1e12
     try:
         peak_tf = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
         kind = "measured"
     except Exception:
         peak_tf, kind = 1900.0, "fallback"
-    _line(args, res["fft_fp32"]["images_per_s"], res["fft_fp32"]["ms_per_step"],
-          {"workload": f"station: 256 antennas, 32640 baselines, {n_t} steps x 16 channels, 512^2 "
-                       "images, natural weighting, 50 sources 1e-3..10 Jy + noise", "layers": L}, clk0,
-          {"modes": res,
-           "roofline": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
-                        "frac": tf / peak_tf, "peak_kind": kind, "traffic": None,
-                        "kernel": "whole bf16x3 step (tcgen05 GEMM + pass 1 + split)",
-                        "algorithmic_flops_per_launch": flops}})
-    ctx.close()
+    del vis, out
+    return {"workload": f"station: 256 antennas, 32640 baselines, {n_t} steps x 16 channels, 512^2 "
+                        "images, natural weighting, 50 sources 1e-3..10 Jy + noise",
+            "layers": L, "images_per_s": res["fft_fp32"]["images_per_s"],
+            "ms_per_step": res["fft_fp32"]["ms_per_step"], "err_vs_oracle": res["fft_fp32"]["err_vs_oracle"],
+            "clocks": clk0, "l2": f"inputs larger than L2 ({total * 4 / 1e9:.1f} GB of images per step)",
+            "modes": res,
+            "roofline": _hbm_roofline(L * per_image, res["fft_fp32"]["ms_per_step"],
+                                      "whole FP32 FFT step, plan build included", per_image),
+            "tensor_bf16x3": {"achieved": tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf,
+                              "peak_kind": kind, "algorithmic_flops_per_step": flops,
+                              "note": "the split-precision GEMMs at 512^2 are below the ridge point "
+                                      "(about 115 flop/byte): HBM is their bound"}}
 
 
-def run_gains(args):
+def measure_gains(torch, binding, ctx, n_t, steps, warmup):
     """Differentiable 1024^2 imaging with antenna gains: forward + backward."""
-    env = _setup_single()
-    if env is None:
-        return
-    torch, binding, ctx = env
     import numpy as np
 
     import synth
     from paper_2405_13478_gb300 import autograd
 
-    n_t = args.n_times or 100
     ws = synth.station_gains(seed=0, n_times=n_t)
     B, n_ant = ws.n_baselines, ws.n_ant
     model_c = torch.as_tensor(synth.model_vis(ws.ant_xyz, ws.freqs_hz, ws.sky).astype(np.complex64)).cuda()
@@ -727,6 +840,7 @@ def run_gains(args):
     plan = ctx.plan(d_xyz, layers)
     target = autograd.dirty_images(model, plan, total).detach()
     g0 = torch.as_tensor(ws.gains.astype(np.complex64)).cuda()
+    box = {}
 
     def step():
         g = g0.clone().requires_grad_(True)
@@ -734,16 +848,72 @@ def run_gains(args):
         img = autograd.dirty_images(vis, plan, total)
         loss = ((img - target) ** 2).sum()
         loss.backward()
+        box["vis"], box["img"] = vis, img
         return g.grad
 
-    ms, clk = _time_steps(torch, step, args.steps, args.warmup)
+    ms, clk = _time_steps(torch, step, steps, warmup)
     L = len(layers)
-    _line(args, L / (ms / 1e3), ms,
-          {"workload": f"station: 256 antennas, {n_t} steps x 8 channels, 1024^2 images, gains on a "
-                       "20-source model, loss = sum (image - model image)^2, forward + backward",
-           "layers": L}, clk, {"gpu_launches_note": "gains, image, degrid and gain-gradient kernels"})
+    err = _sample_error(torch, ws, layers, box["vis"].detach(), box["img"].detach(), [0, L - 1])
+    n2 = 1024 * 1024
+    per_image = 8 * B + 4 * n2 + 4 * n2 + 8 * B   # vis in, image out, dL/dI in, dL/dV out
     plan.close()
+    return {"workload": f"station: 256 antennas, {n_t} steps x 8 channels, 1024^2 images, gains on a "
+                        "20-source model, loss = sum (image - model image)^2, forward + backward",
+            "layers": L, "images_per_s": L / (ms / 1e3), "ms_per_step": ms, "clocks": clk,
+            "err_vs_oracle": err, "err_what": "forward images vs the oracle (gradients: GPU tests)",
+            "l2": f"inputs larger than L2 ({2 * total * 4 / 1e9:.2f} GB of images and image gradients)",
+            "roofline": _hbm_roofline(L * per_image, ms, "whole forward + backward step", per_image)}
+
+
+def _standalone(args, fn, n_default, **kw):
+    env = _setup_single()
+    if env is None:
+        return
+    torch, binding, ctx = env
+    if n_default is None:
+        d = fn(torch, binding, ctx, args.steps, args.warmup)
+    else:
+        d = fn(torch, binding, ctx, args.n_times or n_default, args.steps, args.warmup)
     ctx.close()
+    value, ms, clk = d.pop("images_per_s"), d.pop("ms_per_step"), d.pop("clocks")
+    cfg = {"workload": d.pop("workload")}
+    for k in ("layers", "image_floats", "l2"):
+        if k in d:
+            cfg[k] = d.pop(k)
+    _line(args, value, ms, cfg, clk, d)
+
+
+def run_single(args):
+    _standalone(args, measure_single, None)
+
+
+def run_uneven(args):
+    _standalone(args, measure_uneven, 100)
+
+
+def run_station512(args):
+    _standalone(args, measure_station512, 2000)
+
+
+def run_gains(args):
+    _standalone(args, measure_gains, 100)
+
+
+def secondary_workloads(torch, binding, ctx, steps, warmup):
+    """The four secondary workloads at reduced time steps (device memory and
+    run time of the default bench); full sizes: --workload NAME."""
+    out = {}
+    for name, fn, n_t in (("single", measure_single, None), ("uneven", measure_uneven, 10),
+                          ("station512", measure_station512, 200), ("gains", measure_gains, 20)):
+        try:
+            d = fn(torch, binding, ctx, steps, warmup) if n_t is None else fn(torch, binding, ctx, n_t, steps, warmup)
+            if n_t is not None:
+                d["reduced"] = f"{n_t} time steps (full size: bench.py --workload {name})"
+            out[name] = d
+        except Exception as e:  # report, never hide, a failed variant
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():

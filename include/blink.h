@@ -284,6 +284,16 @@ BLINK_API int blink_plan_check(blink_plan *plan, void *stream);
  * copies; no device work). */
 BLINK_API int blink_plan_layer_info(const blink_plan *plan, int layer, float *wsum, int64_t *n_kept);
 
+/* ------------------------------------------------------------- measurement */
+/* Not a step of the paper's method: measures the FMA rate of the CUDA cores
+ * of `device` (bits = 32: FP32, 64: FP64) so roofline fractions of the
+ * arithmetic-bound kernels (the transforms in FP32, the cell assignment in
+ * FP64) are stated against a measured peak.  One full-occupancy launch of
+ * eight independent FMA chains per thread; *tflops = 2 flops per FMA over its
+ * CUDA-event time.  Synchronous (own stream); BLINK_ERR_INVALID for other
+ * `bits`, BLINK_ERR_CUDA when the launch fails. */
+BLINK_API int blink_probe_fma_peak(int device, int bits, double *tflops);
+
 /* ------------------------------------------------- allocation-free variant */
 /* The paper has no counterpart of this entry point; it serves callers that
  * must not allocate device memory while they run -- for example a real-time

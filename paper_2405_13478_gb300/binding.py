@@ -29,7 +29,7 @@ EXPORTS = (
     "blink_image_batch_noalloc", "blink_image_batch_host", "blink_degrid", "blink_plan_degrid",
     "blink_apply_gains", "blink_gain_grad", "blink_plan_check", "blink_plan_autotune",
     "blink_plan_tuning", "blink_plan_set_tuning", "blink_plan_capture", "blink_plan_replay",
-    "blink_plan_image_ex", "blink_ctx_set_wait_limit",
+    "blink_plan_image_ex", "blink_ctx_set_wait_limit", "blink_probe_fma_peak",
 )
 
 
@@ -140,8 +140,20 @@ def lib(path: str = LIB_PATH):
     L.blink_plan_layer_info.restype = I
     L.blink_plan_layer_info.argtypes = [P, I, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int64)]
+    L.blink_probe_fma_peak.restype = I
+    L.blink_probe_fma_peak.argtypes = [I, I, ctypes.POINTER(ctypes.c_double)]
     _lib = L
     return L
+
+
+def fma_peak_tflops(device: int, bits: int) -> float:
+    """Measured FMA rate (TFLOP/s, 2 flops per FMA) of the CUDA cores of
+    `device` in FP32 (bits=32) or FP64 (bits=64)."""
+    out = ctypes.c_double(0.0)
+    st = lib().blink_probe_fma_peak(int(device), int(bits), ctypes.byref(out))
+    if st != OK:
+        raise BlinkError(st, f"FMA probe ({bits}-bit) failed")
+    return out.value
 
 
 def supported_sizes():
