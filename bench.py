@@ -771,7 +771,8 @@ def measure_uneven(torch, binding, ctx, n_t, steps, warmup):
                                 "err_vs_oracle": err_graph,
                                 "hbm_frac": nbytes / (ms_graph / 1e3) / 1e9 / peak},
             "tuning": [{"n_px": n, "path": ["default", "scheduled fused", "atomic fused",
-                                            "two-kernel"][p_], "wave_bytes": w} for n, p_, w in tuning]}
+                                            "persistent queue", "waves"][p_], "scratch_bytes": w}
+                       for n, p_, w in tuning]}
 
 
 def measure_station512(torch, binding, ctx, n_t, steps, warmup):

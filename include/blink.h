@@ -105,7 +105,7 @@ BLINK_API int blink_supported_sizes(int32_t *sizes, int cap);
 
 /* Creates a context on CUDA device `device` (makes it current for the call).
  * The context owns a device workspace that grows on demand and is freed by
- * blink_ctx_destroy, and an auxiliary stream: large images run half of each
+ * blink_ctx_destroy, and an auxiliary stream: the adjoint runs half of each
  * wave of layers on it, forked from and joined back to the caller's stream
  * with events, so every call stays ordered on the caller's stream (and can
  * be captured in a CUDA graph).  *out is NULL on failure. */
@@ -138,12 +138,12 @@ BLINK_API int blink_grid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, con
 /* Dirty images of every layer (steps 1-5): d_images + out_offset receives the
  * float32 [N][N] FFT-shifted real image, unnormalised unless flags has
  * BLINK_NORMALIZE.  d_wsum (float32 [n_layers], may be NULL) receives the
- * summed weights.  Layers of different sizes may be mixed.  Layers gridded
- * by the fused small-image kernel (sizes up to 256 whose support fits it)
- * give the same bits on every call: every cell sums its visibilities in an
- * order fixed by the array geometry, without atomics; the row pass of larger
- * images grids with shared-memory atomics, whose order may change the last
- * bits from call to call.
+ * summed weights.  Layers of different sizes may be mixed.  Images are the
+ * same bits on every call: every cell sums its visibilities in an order fixed
+ * by the array geometry, without atomics (the fused small-image kernel by its
+ * per-channel register schedule, the large-image row pass by its sorted row
+ * buckets).  Large images run as one persistent launch per image size whose
+ * CTAs take row and column work items from a device queue.
  * This call builds the per-channel tables on `stream` and synchronises that
  * stream once to size the image kernels; use a plan (below) to build the
  * tables once and image many batches asynchronously. */
@@ -242,19 +242,22 @@ BLINK_API void blink_plan_destroy(blink_plan *plan);
 
 /* Autotuner: for every image size of the plan, times the candidate kernel
  * configurations on the given data (the atomic-free scheduled fused kernel,
- * the shared-atomic fused kernel, the two-kernel path with wave budgets of
- * 12, 24, 48 and 96 MB of row-transform scratch) and keeps the fastest for
- * later calls.  Synchronises `stream`; writes images as a side effect.
- * blink_plan_tuning reports the choice for size group `group` (groups are the
- * plan's distinct sizes in increasing order; path 1 scheduled fused, 2
- * atomic fused, 3 two-kernel). */
+ * the shared-atomic fused kernel, and the two-pass large-image path as one
+ * persistent work-queue launch or as waves of two kernels, each with 12, 24
+ * and 48 MB of row-transform scratch) and keeps the fastest for later calls.
+ * Synchronises `stream`; writes images as a side effect.  blink_plan_tuning
+ * reports the choice for size group `group` (groups are the plan's distinct
+ * sizes in increasing order; path 1 scheduled fused, 2 atomic fused, 3
+ * persistent queue, 4 waves). */
 BLINK_API int blink_plan_autotune(blink_plan *plan, const float *d_vis, float *d_images, void *stream);
 BLINK_API int blink_plan_tuning(const blink_plan *plan, int group, int *n_px, int *path, int64_t *wave_bytes);
 /* Sets a size group's kernel choice by hand (e.g. a tuning kept from an
  * earlier run): path 0 default, 1 scheduled fused (sizes <= 256 whose
- * schedule fits), 2 atomic fused (sizes <= 256), 3 two-kernel (any size);
- * wave_bytes 0 = default L2-sized waves.  BLINK_ERR_INVALID for a path the
- * group cannot take; the plan is unchanged then. */
+ * schedule fits), 2 atomic fused (sizes <= 256), 3 persistent work queue,
+ * 4 waves of two kernels (3 and 4: any size); wave_bytes = row-transform
+ * scratch in use (the ring of path 3, a wave of path 4), 0 = default.
+ * BLINK_ERR_INVALID for a path the group cannot take; the plan is unchanged
+ * then. */
 BLINK_API int blink_plan_set_tuning(blink_plan *plan, int group, int path, int64_t wave_bytes);
 
 /* CUDA graph of the plan's image launches: blink_plan_capture runs

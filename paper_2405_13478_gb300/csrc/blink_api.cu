@@ -99,6 +99,8 @@ struct blink_plan {
     size_t gscratch_bytes = 0;
     int *d_status = nullptr;       // device status word (in the table block)
     int64_t out_extent = 0;        // max over layers of out_offset + n_px^2
+    int *d_queue = nullptr;        // work queue of the persistent large-image kernel
+    size_t queue_bytes = 0;
     float2 *d_gprod = nullptr;     // gain-product table of the fused epilogue (on first use)
     size_t gprod_bytes = 0;
     cudaStream_t last_stream = nullptr;
@@ -204,6 +206,9 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     p->d_gscratch = nullptr;
     if (p->d_gprod) cudaFreeAsync(p->d_gprod, st);
     p->d_gprod = nullptr;
+    if (p->d_queue) cudaFreeAsync(p->d_queue, st);
+    p->d_queue = nullptr;
+    p->queue_bytes = 0;
     p->gprod_bytes = 0;
     p->d_block = nullptr;
     p->d_scratch = nullptr;
@@ -408,6 +413,18 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         const size_t per = blink::image_scratch_per_layer(g.n_px, r);
         if (per) scratch = std::max(scratch, std::max(per, std::min(per * size_t(g.count), kScratchCap)));
     }
+    // work queue of the persistent large-image kernel: sized for the largest
+    // group, so every group (also one forced onto that path) can use it
+    {
+        size_t qb = 0;
+        for (const auto &g : p->groups) qb = std::max(qb, blink::image_queue_bytes(g.count));
+        void *q = nullptr;
+        e = cudaMallocFromPoolAsync(&q, qb, ctx->pool, st);
+        if (e != cudaSuccess)
+            return fail(ctx, BLINK_ERR_WORKSPACE, std::string("work-queue allocation: ") + cudaGetErrorString(e));
+        p->d_queue = static_cast<int *>(q);
+        p->queue_bytes = qb;
+    }
     if (scratch) {
         void *s = nullptr;
         e = cudaMallocFromPoolAsync(&s, scratch, ctx->pool, st);
@@ -450,6 +467,8 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.aux = p->ctx->aux;
     a.ev_fork = p->ctx->ev_fork;
     a.ev_join = p->ctx->ev_join;
+    a.queue = p->d_queue;
+    a.queue_bytes = p->queue_bytes;
     return a;
 }
 
@@ -629,7 +648,7 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
         }
     }
     for (const auto &grp : p->groups)
-        if (grp.force_path == 3) {
+        if (grp.force_path >= 3) {
             const int rc = ensure_rows_scratch(p, st);
             if (rc) return rc;
             break;
@@ -703,7 +722,8 @@ int blink_plan_autotune(blink_plan *p, const float *d_vis, float *d_images, void
             if (grp.sched_ok) cands.push_back({1, 0});
             cands.push_back({2, 0});
         }
-        for (size_t mb : {12, 24, 48, 96}) cands.push_back({3, mb << 20});
+        for (size_t mb : {12, 24, 48}) cands.push_back({3, mb << 20});
+        for (size_t mb : {12, 24, 48}) cands.push_back({4, mb << 20});
         float best = 1e30f;
         Cand pick = cands.front();
         for (const Cand &c : cands) {
@@ -756,7 +776,7 @@ int blink_plan_set_tuning(blink_plan *p, int group, int path, int64_t wave_bytes
         return fail(p->ctx, BLINK_ERR_INVALID, "size group out of range");
     auto &grp = p->groups[size_t(group)];
     const bool small = blink::image_small_path(grp.n_px, grp.r_alloc);
-    if (path < 0 || path > 3 || wave_bytes < 0 || (path == 1 && !(small && grp.sched_ok)) ||
+    if (path < 0 || path > 4 || wave_bytes < 0 || (path == 1 && !(small && grp.sched_ok)) ||
         (path == 2 && !small))
         return fail(p->ctx, BLINK_ERR_INVALID, "kernel path not available for this size group");
     grp.force_path = path;

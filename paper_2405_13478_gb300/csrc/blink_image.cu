@@ -114,6 +114,9 @@ bool image_small_path(int n_px, int r_alloc) {
 
 size_t image_rows_scratch_per_layer(int n_px, int r_alloc) { return size_t(r_alloc) * n_px * sizeof(float2); }
 
+// a 64-bit item counter and the abort flag (four words), then two counters per layer
+size_t image_queue_bytes(int n_layers) { return (4 + 2 * size_t(n_layers > 0 ? n_layers : 0)) * sizeof(int); }
+
 size_t image_scratch_per_layer(int n_px, int r_alloc) {
 #define X(N_) if (n_px == N_) return SizeOps<N_>::scratch_per_layer(r_alloc);
     BLINK_FOR_EACH_SIZE(X)

@@ -27,6 +27,7 @@
 #include "blink_kernels.cuh"
 #include "blink_pairs.cuh"
 #include "blink_image_small.cuh"
+#include "blink_sync.cuh"
 
 #include <algorithm>
 
@@ -280,55 +281,209 @@ __device__ __forceinline__ void stage_four_step(float2 *dst, int tid, int nt) {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Pass 1 for a band of RB canonical rows of one layer, written in natural
-// order to scratch[layer_in_wave][r][p].  Grid: (bands, layers in wave).
+// Row items of the image path: a band of RB canonical rows of one layer in
+// shared memory (row stride S) and the four-step twiddle table.  RB is the
+// largest band (at most 32 rows) that keeps an item within kRowsSmemBudget,
+// so three CTAs share an SM.
+constexpr size_t kRowsSmemBudget = 72 * 1024;
 template <int N>
-__global__ void __launch_bounds__(LargeCfg<N>::NT, Plan<N>::N1 == 24 ? 2 : 3) k_rows(ImageArgs a, int l0) {
-    constexpr int NT = LargeCfg<N>::NT, S = LargeCfg<N>::S, RB = LargeCfg<N>::RB;
-    extern __shared__ float2 sm[];
-    const int lw = blockIdx.y;
-    const DevLayer L = a.layers[l0 + lw];
-    const ChanInfo ci = a.chans[L.chan];
-    const int R = ci.rows;
-    const int r0 = blockIdx.x * RB;
-    if (r0 >= R) return;
-    const int nrows = min(RB, R - r0);
-    const int tid = threadIdx.x;
-    float2 *tw = sm + tw_offset<N>();
-    stage_four_step<N>(tw, tid, NT);
-    for (int i = tid; i < nrows * S; i += NT) sm[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    if (a.csr && ci.csr_off >= 0) {
-        // only this band's baselines, from the row buckets
-        const CsrLayout cl(N, a.nb);
-        const int32_t *ptr = reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr);
-        const uint2 *ents = reinterpret_cast<const uint2 *>(a.csr + ci.csr_off + cl.ents);
-        const float2 *vis = a.vis + L.vis_off;
-        const int e1 = ptr[r0 + nrows];
-        const LayerGains gl = layer_gains(a, L);
-        for (int e = ptr[r0] + tid; e < e1; e += NT) {
-            const uint2 en = __ldg(ents + e);
-            float2 v = __ldg(vis + en.x);
-            if (gl) v = apply_gain(v, gl, en.x);
-            if (code_conj(en.y)) v.y = -v.y;
-            float2 *cell = sm + (int(code_row(en.y)) - r0) * S + RowLayout<N>::phys(int(code_col(en.y)));
-            atomicAdd(&cell->x, v.x);
-            atomicAdd(&cell->y, v.y);
-        }
-    } else {
-        grid_rows<NT, N>(sm, S, r0, nrows, a.codes + ci.code_off, a.vis + L.vis_off, a.nb, tid,
-                         layer_gains(a, L));
+struct RowsCfg {
+    static constexpr int NT = 256;
+    static constexpr int S = RowLayout<N>::S;
+    static constexpr int RB = std::max(1, std::min(32, int((kRowsSmemBudget - size_t(N) * 8) / (size_t(S) * 8))));
+    static constexpr int tw = (RB * S + 1) & ~1;  // float2 offset of the twiddles (16-byte aligned)
+    static constexpr size_t smem = (size_t(tw) + N) * sizeof(float2);
+};
+
+// Segmented-sum operator on (partial sum, "a run starts here") pairs:
+// (a, fa) + (b, fb) = (fb ? b : a + b, fa | fb).  Associative, so a scan with a
+// fixed tree of these gives every run's sum in an order set by the chunk
+// layout alone.
+struct SegSum {
+    float2 v;
+    bool head;
+};
+__device__ __forceinline__ SegSum seg_add(const SegSum &a, const SegSum &b) {
+    return SegSum{b.head ? b.v : make_float2(a.v.x + b.v.x, a.v.y + b.v.y), a.head || b.head};
+}
+
+// Deterministic, atomic-free gridding of the canonical rows [r0, r0 + nrows)
+// of one layer from its sorted row buckets (the entries of a cell are
+// contiguous).  Per chunk of 256 x kRowGridU entries, thread t takes entries
+// [kRowGridU t, kRowGridU (t+1)): it loads their baselines and cells and the
+// visibilities (gains applied, conjugated for mirrored baselines), and a
+// block-wide segmented scan (in-thread, warp shuffles, then across warps)
+// gives each run of equal cells its sum at its last entry, which adds it to
+// the cell.  Each cell has one writer per chunk and chunks follow one
+// another, so the image never depends on timing.
+//
+// Latency: the first chunk's loads are issued before `prologue` (which
+// zeroes the band and starts the twiddle copy) and the barrier after it, and
+// every later chunk's baselines and cells are loaded while the chunk before
+// it is summed.
+constexpr int kRowGridU = 8;
+struct GridChunk {
+    uint32_t key[kRowGridU], bl[kRowGridU];
+    uint32_t conj;          // bit u: entry u is a mirrored baseline
+    uint32_t kprev, knext;  // cell keys of the entries just before and after this thread's
+    int n;                  // entries in the chunk (<= 0: none)
+};
+
+__device__ __forceinline__ void grid_load_codes(GridChunk &c, const uint2 *__restrict__ ents, int c0, int n, int r0,
+                                                int tid) {
+    constexpr int U = kRowGridU;
+    constexpr uint32_t kPastEnd = 0xFFFFFFFFu, kBeforeStart = 0xFFFFFFFEu;  // never a cell key
+    auto key_of = [r0](uint32_t code) { return ((code_row(code) - uint32_t(r0)) << 16) | code_col(code); };
+    const int i0 = tid * U;
+    c.n = n;
+    c.conj = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const bool live = i0 + u < n;
+        const uint2 en = live ? __ldg(ents + c0 + i0 + u) : make_uint2(0u, 0u);
+        c.bl[u] = en.x;
+        c.key[u] = live ? key_of(en.y) : kPastEnd;
+        c.conj |= (live && code_conj(en.y)) ? (1u << u) : 0u;
     }
+    c.kprev = (i0 > 0 && i0 <= n) ? key_of(__ldg(ents + c0 + i0 - 1).y) : kBeforeStart;
+    c.knext = i0 + U < n ? key_of(__ldg(ents + c0 + i0 + U).y) : kPastEnd;
+}
+
+__device__ __forceinline__ void grid_load_vis(const GridChunk &c, float2 (&v)[kRowGridU],
+                                              const float2 *__restrict__ vis, const LayerGains &gl, int tid) {
+    const int i0 = tid * kRowGridU;
+#pragma unroll
+    for (int u = 0; u < kRowGridU; ++u) v[u] = i0 + u < c.n ? __ldg(vis + c.bl[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kRowGridU; ++u) {
+        if (i0 + u < c.n) {
+            if (gl) v[u] = apply_gain(v[u], gl, c.bl[u]);
+            if ((c.conj >> u) & 1u) v[u].y = -v[u].y;
+        }
+    }
+}
+
+// Segmented scan of one chunk and its cell updates (two barriers).
+template <int N>
+__device__ __forceinline__ void grid_sum_chunk(float2 *G, const GridChunk &c, const float2 (&v)[kRowGridU],
+                                               int tid) {
+    constexpr int U = kRowGridU, S = RowsCfg<N>::S, NW = RowsCfg<N>::NT / 32;
+    __shared__ float2 s_wv[NW];
+    __shared__ int s_wh[NW];
+    const int lane = tid & 31, warp = tid >> 5, i0 = tid * U;
+    const unsigned full = 0xFFFFFFFFu;
+    SegSum agg{v[0], c.key[0] != c.kprev};
+#pragma unroll
+    for (int u = 1; u < U; ++u) agg = seg_add(agg, SegSum{v[u], c.key[u] != c.key[u - 1]});
+    SegSum inc = agg;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        SegSum up;
+        up.v.x = __shfl_up_sync(full, inc.v.x, d);
+        up.v.y = __shfl_up_sync(full, inc.v.y, d);
+        up.head = __shfl_up_sync(full, int(inc.head), d) != 0;
+        if (lane >= d) inc = seg_add(up, inc);
+    }
+    if (lane == 31) {
+        s_wv[warp] = inc.v;
+        s_wh[warp] = int(inc.head);
+    }
+    SegSum ex;  // everything before this thread's entries, inside the warp
+    ex.v.x = __shfl_up_sync(full, inc.v.x, 1);
+    ex.v.y = __shfl_up_sync(full, inc.v.y, 1);
+    ex.head = __shfl_up_sync(full, int(inc.head), 1) != 0;
     __syncthreads();
+    SegSum pre{make_float2(0.f, 0.f), false};
+    for (int w = 0; w < warp; ++w) pre = seg_add(pre, SegSum{s_wv[w], s_wh[w] != 0});
+    SegSum run = lane == 0 ? pre : seg_add(pre, ex);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        run = seg_add(run, SegSum{v[u], c.key[u] != (u == 0 ? c.kprev : c.key[u - 1])});
+        const bool last = u + 1 < U ? c.key[u + 1] != c.key[u] : c.knext != c.key[u];
+        if (i0 + u < c.n && last) {
+            float2 *cell = G + int(c.key[u] >> 16) * S + RowLayout<N>::phys(int(c.key[u] & 0xFFFFu));
+            cell->x += run.v.x;
+            cell->y += run.v.y;
+        }
+    }
+    __syncthreads();  // cells and warp sums are reused by the next chunk
+}
+
+template <int N, class Prologue>
+__device__ __forceinline__ void grid_band_sorted(float2 *G, int r0, int nrows, const int32_t *__restrict__ ptr,
+                                                 const uint2 *__restrict__ ents, const float2 *__restrict__ vis,
+                                                 const LayerGains &gl, int tid, Prologue &&prologue) {
+    constexpr int CH = RowsCfg<N>::NT * kRowGridU;
+    const int e_begin = __ldg(ptr + r0), e_end = __ldg(ptr + r0 + nrows);
+    GridChunk cur;
+    float2 v[kRowGridU];
+    int c0 = e_begin;
+    grid_load_codes(cur, ents, c0, min(CH, e_end - c0), r0, tid);
+    grid_load_vis(cur, v, vis, gl, tid);
+    prologue();
+    __syncthreads();
+    while (cur.n > 0) {
+        GridChunk nxt;
+        const int c1 = c0 + CH;
+        grid_load_codes(nxt, ents, c1, min(CH, e_end - c1), r0, tid);
+        grid_sum_chunk<N>(G, cur, v, tid);
+        cur = nxt;
+        c0 = c1;
+        if (cur.n > 0) grid_load_vis(cur, v, vis, gl, tid);
+    }
+}
+
+// Pass 1 for the band of canonical rows [r0, r0 + RB) of one layer (r0 below
+// the channel's support R): gridding, weights, Hermitian completion of row 0,
+// the row transforms, written in natural column order to dst[r - r0][p].
+template <int N>
+__device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L, const ChanInfo &ci, int r0,
+                                          float2 *__restrict__ dst, float2 *sm, int tid) {
+    using C = RowsCfg<N>;
+    constexpr int NT = C::NT, S = C::S, RB = C::RB;
+    const int nrows = min(RB, ci.rows - r0);
+    float2 *tw = sm + C::tw;
+    auto prologue = [&]() {
+        stage_four_step<N>(tw, tid, NT);
+        for (int i = tid; i < nrows * S; i += NT) sm[i] = make_float2(0.f, 0.f);
+    };
+    const LayerGains gl = layer_gains(a, L);
+    if (a.csr && ci.csr_off >= 0) {
+        const CsrLayout cl(N, a.nb);
+        grid_band_sorted<N>(sm, r0, nrows, reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr),
+                            reinterpret_cast<const uint2 *>(a.csr + ci.csr_off + cl.ents), a.vis + L.vis_off, gl,
+                            tid, prologue);
+    } else {
+        // a channel without row buckets (its support always fits the fused
+        // kernel; it comes here only when the two-kernel path is forced):
+        // shared-memory atomics over the whole code table
+        prologue();
+        __syncthreads();
+        grid_rows<NT, N>(sm, S, r0, nrows, a.codes + ci.code_off, a.vis + L.vis_off, a.nb, tid, gl);
+        __syncthreads();
+    }
     weight_and_complete<N, true>(sm, S, r0, r0 + nrows, ci, a.wgt, tid, NT);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table in place
     __syncthreads();
     rows_fft<N, +1, true>(sm, S, nrows, tid, NT, tw);
-    float2 *out = a.scratch + (int64_t(lw) * a.r_alloc + r0) * N;
     for (int i = tid; i < nrows * N; i += NT) {
         const int r = i / N, p = i % N;
-        out[int64_t(r) * N + p] = sm[r * S + RowLayout<N>::phys(pos_after_rows<N>(p))];
+        dst[int64_t(r) * N + p] = sm[r * S + RowLayout<N>::phys(pos_after_rows<N>(p))];
     }
+}
+
+// Pass 1 of a wave of layers into scratch[layer_in_wave][r][p] (the wave
+// path: the tensor-core FP16 modes and callers without a work queue).
+// Grid: (bands, layers in wave).
+template <int N>
+__global__ void __launch_bounds__(RowsCfg<N>::NT, Plan<N>::N1 == 24 ? 2 : 3) k_rows(ImageArgs a, int l0) {
+    extern __shared__ float2 sm[];
+    const int lw = blockIdx.y;
+    const DevLayer L = a.layers[l0 + lw];
+    const ChanInfo ci = a.chans[L.chan];
+    const int r0 = blockIdx.x * RowsCfg<N>::RB;
+    if (r0 >= ci.rows) return;
+    rows_item<N>(a, L, ci, r0, a.scratch + (int64_t(lw) * a.r_alloc + r0) * N, sm, threadIdx.x);
 }
 
 // The column pass can stage its scratch columns through shared memory when
@@ -388,30 +543,191 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
         zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], four_step_tw<N, +1>(k1, n2));
 }
 
-// Pass 2 for P column pairs of one layer.  Grid: (ceil(N/2 / P), layers in wave).
+// Pass 2 for the P column pairs j0.. of one layer from its pass-1 rows Hs
+// (scratch written by other CTAs: read through L2, never a stale L1 line).
+template <int N, bool EPI, class Consumed>
+__device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L, const ChanInfo &ci, int j0,
+                                          const float2 *Hs, float *__restrict__ out, const float *__restrict__ ref,
+                                          float2 *sm, int tid, Consumed &&consumed) {
+    constexpr int NT = LargeCfg<N>::NT, P = LargeCfg<N>::P;
+    using ZL = ZLayout<N, P>;
+    const int R = ci.rows;
+    if constexpr (ColsStaged<N>::value) {
+        cols_step_a_staged<N, P, ZL>(sm, R, j0, Hs, tid);
+    } else {
+        auto hrow = [&](int k, int p) { return __ldcg(Hs + int64_t(k) * N + p); };
+        cols_step_a<N, P, ZL>(sm, R, j0, hrow, tid, NT);
+    }
+    __syncthreads();
+    consumed();  // every read of Hs has landed in registers or shared memory
+    const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
+    cols_step_b<N, P, ZL>(sm, j0, out + L.out_off, scale, tid, NT, EPI && ref ? ref + L.out_off : nullptr);
+}
+
+template <int N>
+constexpr size_t cols_smem(int r_alloc) {
+    constexpr int P = LargeCfg<N>::P;
+    size_t smem = size_t(P) * ZLayout<N, P>::S * sizeof(float2);
+    if (ColsStaged<N>::value)  // the staged columns share the buffer
+        smem = std::max(smem, size_t(r_alloc) * 2 * P * sizeof(float2));
+    return smem;
+}
+
+// Pass 2 of a wave of layers.  Grid: (ceil(N/2 / P), layers in wave).
 template <int N, bool EPI>
 __global__ void __launch_bounds__(LargeCfg<N>::NT, EPI ? 1 : 3) k_cols(ImageArgs a, int l0, float *__restrict__ out,
                                                           const float *__restrict__ ref) {
-    constexpr int NT = LargeCfg<N>::NT, P = LargeCfg<N>::P;
-    using ZL = ZLayout<N, P>;
     extern __shared__ float2 sm[];
     const int lw = blockIdx.y;
     const DevLayer L = a.layers[l0 + lw];
     const ChanInfo ci = a.chans[L.chan];
-    const int R = ci.rows;
-    const int j0 = blockIdx.x * P;
-    const float2 *Hs = a.scratch + int64_t(lw) * a.r_alloc * N;
-    if constexpr (ColsStaged<N>::value) {
-        cols_step_a_staged<N, P, ZL>(sm, R, j0, Hs, threadIdx.x);
-    } else {
-        auto hrow = [&](int k, int p) { return Hs[int64_t(k) * N + p]; };
-        cols_step_a<N, P, ZL>(sm, R, j0, hrow, threadIdx.x, NT);
-    }
-    __syncthreads();
-    const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
-    cols_step_b<N, P, ZL>(sm, j0, out + L.out_off, scale, threadIdx.x, NT,
-                      EPI && ref ? ref + L.out_off : nullptr);
+    cols_item<N, EPI>(a, L, ci, blockIdx.x * LargeCfg<N>::P, a.scratch + int64_t(lw) * a.r_alloc * N, out, ref, sm,
+                      threadIdx.x, [] {});
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
+}
+
+// ------------------------------------------------ persistent large-image path
+// One launch per image size: a persistent grid pulls work items from a device
+// queue.  A layer has nR row items (bands of RB rows: gridding + pass 1 into
+// the layer's slot of a ring of `slots` scratch buffers that stays in L2) and
+// nC column items (P column pairs each: pass 2 from that slot, image store).
+// The queue interleaves the layers with a lag: stage s holds the row items of
+// layer s and then the column items of layer s - lag, so a column item's rows
+// were handed out lag stages earlier and are normally done when it starts.
+// Dependencies, each a bounded wait on a per-layer counter:
+//   column item of layer l  needs the nR row items of l   (rows_done[l]),
+//   row item of layer l     needs the nC column items of l - slots, whose
+//                           slot it overwrites             (cols_done[l - slots]).
+// Both point to items earlier in the queue (lag <= slots - 1), and items are
+// handed out only to running CTAs, so the earliest unfinished item can always
+// run: the waits end.  A wait that runs out of time (a fault elsewhere) sets
+// the abort flag and BLINK_ERR_TIMEOUT in the status word; later items then
+// skip their work.
+struct LargeSched {
+    int n;          // layers of the group
+    int nR, nC;     // row and column items per layer
+    int lag;        // stages between a layer's row and column items
+    int slots;      // scratch ring slots (layers)
+    int64_t total;  // n (nR + nC)
+    unsigned long long wait_ns;
+};
+
+// Queue words: a 64-bit item counter, the abort flag, then rows_done[n] and
+// cols_done[n] (32-bit counters).
+struct QueueView {
+    unsigned long long *head;
+    int *abort_flag;
+    int *rows_done, *cols_done;
+    __device__ QueueView(int *q, int n)
+        : head(reinterpret_cast<unsigned long long *>(q)), abort_flag(q + 2), rows_done(q + 4),
+          cols_done(q + 4 + n) {}
+};
+
+__device__ __forceinline__ void decode_item(int64_t i, const LargeSched &q, bool &is_row, int &layer, int &sub) {
+    const int64_t per_r = q.nR, per_c = q.nC, lag = q.lag;
+    const int64_t p1 = lag * per_r;
+    if (i < p1) {
+        is_row = true;
+        layer = int(i / per_r);
+        sub = int(i % per_r);
+        return;
+    }
+    i -= p1;
+    const int64_t stage = per_r + per_c, p2 = (int64_t(q.n) - lag) * stage;
+    if (i < p2) {
+        const int64_t k = i / stage, off = i % stage;
+        is_row = off < per_r;
+        layer = int(is_row ? lag + k : k);
+        sub = int(is_row ? off : off - per_r);
+        return;
+    }
+    i -= p2;
+    is_row = false;
+    layer = int(int64_t(q.n) - lag + i / per_c);
+    sub = int(i % per_c);
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0: waits until *ctr >= target (true) or the abort flag is set or the
+// limit runs out (false; the timeout also raises the flag and the status).
+__device__ __forceinline__ bool wait_count(const int *ctr, int target, int *abort_flag, int *status,
+                                           unsigned long long limit_ns) {
+    if (ld_acquire_gpu(ctr) >= target) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        __nanosleep(256);
+        if (ld_acquire_gpu(ctr) >= target) return true;
+        if (ld_acquire_gpu(abort_flag)) return false;
+        if (global_ns() - t0 >= limit_ns) {
+            atomicExch(abort_flag, 1);
+            if (status) atomicExch(status, -4);  // BLINK_ERR_TIMEOUT
+            return false;
+        }
+    }
+}
+
+template <int N>
+constexpr size_t large_smem(int r_alloc) { return std::max(RowsCfg<N>::smem, cols_smem<N>(r_alloc)); }
+
+template <int N, bool EPI>
+__global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
+    k_large(ImageArgs a, LargeSched q, float *__restrict__ out, const float *__restrict__ ref) {
+    static_assert(RowsCfg<N>::NT == 256 && LargeCfg<N>::NT == 256, "one block shape for both item kinds");
+    extern __shared__ float2 sm[];
+    __shared__ long long s_item[2];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    const QueueView Q(a.queue, q.n);
+    if (tid == 0) s_item[0] = (long long)atomicAdd(Q.head, 1ull);
+    __syncthreads();
+    long long item = s_item[0];
+    for (int it = 0; item < q.total; ++it) {
+        if (tid == 0) s_item[(it + 1) & 1] = (long long)atomicAdd(Q.head, 1ull);  // next item, fetched early
+        bool is_row;
+        int layer, sub;
+        decode_item(item, q, is_row, layer, sub);
+        if (tid == 0) {
+            bool ok = ld_acquire_gpu(Q.abort_flag) == 0;
+            if (ok && is_row && layer >= q.slots)
+                ok = wait_count(Q.cols_done + (layer - q.slots), q.nC, Q.abort_flag, a.status, q.wait_ns);
+            else if (ok && !is_row)
+                ok = wait_count(Q.rows_done + layer, q.nR, Q.abort_flag, a.status, q.wait_ns);
+            s_ok = ok;
+        }
+        __syncthreads();
+        const bool ok = s_ok != 0;
+        if (ok) {
+            const DevLayer L = a.layers[layer];
+            const ChanInfo ci = a.chans[L.chan];
+            float2 *Hs = a.scratch + int64_t(layer % q.slots) * a.r_alloc * N;
+            if (is_row) {
+                // the first row item of a layer pulls the layer's visibilities
+                // into L2 for the band gathers of all its row items
+                if (sub == 0) prefetch_l2(reinterpret_cast<const float *>(a.vis + L.vis_off), 2 * a.nb, tid, 256);
+                const int r0 = sub * RowsCfg<N>::RB;
+                if (r0 < ci.rows) rows_item<N>(a, L, ci, r0, Hs + int64_t(r0) * N, sm, tid);
+                __syncthreads();  // every thread's scratch stores precede the release below
+                if (tid == 0) {
+                    __threadfence();
+                    atomicAdd(Q.rows_done + layer, 1);
+                }
+            } else {
+                // the slot is released as soon as its rows are read: the image
+                // stores do not gate its reuse
+                cols_item<N, EPI>(a, L, ci, sub * LargeCfg<N>::P, Hs, out, ref, sm, tid, [&] {
+                    if (tid == 0) atomicAdd(Q.cols_done + layer, 1);
+                });
+                if (sub == 0 && tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
+            }
+        }
+        __syncthreads();  // shared memory and s_ok are reused by the next item
+        item = s_item[(it + 1) & 1];
+    }
 }
 
 template <int N>
@@ -610,6 +926,40 @@ bool use_small(int r_alloc) {
     return N <= 256 && small_path_fits(N, r_alloc);
 }
 
+// The persistent launch of one size group (a.queue holds queue_bytes(n)).
+template <int N>
+Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
+    const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
+    LargeSched q{};
+    q.n = a.n_layers;
+    q.nR = (a.r_alloc + RowsCfg<N>::RB - 1) / RowsCfg<N>::RB;
+    q.nC = (N / 2 + LargeCfg<N>::P - 1) / LargeCfg<N>::P;
+    q.total = int64_t(q.n) * (q.nR + q.nC);
+    q.wait_ns = a.wait_ns < 0 ? kWaitNs : static_cast<unsigned long long>(a.wait_ns);
+    const size_t ring = a.wave_budget ? std::min(a.scratch_bytes, std::max(a.wave_budget, per_layer)) : a.scratch_bytes;
+    q.slots = int(std::max<size_t>(1, std::min<size_t>(ring / per_layer, size_t(q.n))));
+    const size_t smem = large_smem<N>(a.r_alloc);
+    auto kern = a.ref ? k_large<N, true> : k_large<N, false>;
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int dev = 0, sms = 0, per_sm = 0;
+    BLINK_CUDA_TRY(cudaGetDevice(&dev));
+    BLINK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BLINK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+    if (per_sm < 1) return Error{-2, "persistent image kernel does not fit on an SM for size " + std::to_string(N)};
+    const int64_t grid = std::min<int64_t>(q.total, int64_t(per_sm) * sms);
+    // lag: up to four grids of items between a layer's row and column items
+    // (a dense band of rows takes several times as long as a column item).
+    // A row item also waits for the column items of the layer `slots` back,
+    // which sit slots - lag stages earlier: half the ring each way keeps both
+    // gaps wide (and lag <= slots - 1).
+    const int lag_want = int(4 * grid / int64_t(q.nR + q.nC)) + 1;
+    q.lag = std::max(0, std::min({lag_want, q.slots / 2, q.n}));
+    BLINK_CUDA_TRY(cudaMemsetAsync(a.queue, 0, image_queue_bytes(q.n), st));
+    kern<<<unsigned(grid), 256, smem, st>>>(a, q, static_cast<float *>(a.out), a.ref);
+    BLINK_CUDA_TRY(cudaGetLastError());
+    return Error{0, ""};
+}
+
 template <int N>
 Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     if (a.n_layers == 0) return Error{0, ""};
@@ -621,52 +971,25 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
     if (!a.scratch || a.scratch_bytes < per_layer)
         return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
+    if (a.force_path != 4 && a.queue && a.queue_bytes >= image_queue_bytes(a.n_layers))
+        return launch_large_n<N>(a, st);
+    // wave path (no work queue, or chosen by the autotuner): pass 1 of a wave
+    // of layers, then pass 2
     const int wave = wave_size(a.n_layers, a.scratch_bytes, per_layer, a.wave_budget);
-    const size_t smem_rows = rows_smem<N>();
-    size_t smem_cols = size_t(C::P) * ZLayout<N, C::P>::S * sizeof(float2);
-    if constexpr (ColsStaged<N>::value)  // the staged columns share the buffer
-        smem_cols = std::max(smem_cols, size_t(a.r_alloc) * 2 * C::P * sizeof(float2));
+    const size_t smem_rows = RowsCfg<N>::smem;
+    const size_t smem_cols = cols_smem<N>(a.r_alloc);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         int(smem_rows)));
     auto cols = a.ref ? k_cols<N, true> : k_cols<N, false>;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_cols)));
-    const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
+    const unsigned bands = unsigned((a.r_alloc + RowsCfg<N>::RB - 1) / RowsCfg<N>::RB);
     const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
-    // With an auxiliary stream each wave is split in two halves, one per
-    // stream, each with its own half of the scratch: the row and column passes
-    // of one half fill the launch gaps and partial last waves of CTAs of the
-    // other.  The auxiliary stream is forked from `st` and joined back to it.
-    const bool two = a.aux && a.ev_fork && a.ev_join && wave >= 2;
-    if (two) {
-        BLINK_CUDA_TRY(cudaEventRecord(a.ev_fork, st));
-        BLINK_CUDA_TRY(cudaStreamWaitEvent(a.aux, a.ev_fork, 0));
-    }
-    auto pass = [&](const ImageArgs &b, int l0, int cnt, cudaStream_t s) -> Error {
-        k_rows<N><<<dim3(bands, unsigned(cnt)), C::NT, smem_rows, s>>>(b, l0);
-        BLINK_CUDA_TRY(cudaGetLastError());
-        cols<<<dim3(pchunks, unsigned(cnt)), C::NT, smem_cols, s>>>(b, l0, static_cast<float *>(b.out), b.ref);
-        BLINK_CUDA_TRY(cudaGetLastError());
-        return Error{0, ""};
-    };
-    const int half = wave / 2;  // scratch slots [0, half) on st, [half, wave) on aux
-    ImageArgs hb = a;
-    hb.scratch = a.scratch + size_t(half) * a.r_alloc * N;
     for (int l0 = 0; l0 < a.n_layers; l0 += wave) {
         const int cnt = std::min(wave, a.n_layers - l0);
-        if (two && cnt >= 2) {
-            const int h = std::min(half, cnt - 1);
-            Error e = pass(a, l0, h, st);
-            if (e.status) return e;
-            e = pass(hb, l0 + h, cnt - h, a.aux);
-            if (e.status) return e;
-        } else {
-            Error e = pass(a, l0, cnt, st);
-            if (e.status) return e;
-        }
-    }
-    if (two) {
-        BLINK_CUDA_TRY(cudaEventRecord(a.ev_join, a.aux));
-        BLINK_CUDA_TRY(cudaStreamWaitEvent(st, a.ev_join, 0));
+        k_rows<N><<<dim3(bands, unsigned(cnt)), RowsCfg<N>::NT, smem_rows, st>>>(a, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        cols<<<dim3(pchunks, unsigned(cnt)), C::NT, smem_cols, st>>>(a, l0, static_cast<float *>(a.out), a.ref);
+        BLINK_CUDA_TRY(cudaGetLastError());
     }
     return Error{0, ""};
 }
@@ -685,11 +1008,10 @@ Error SizeOps<N>::image(const ImageArgs &a, cudaStream_t st) { return launch_ima
 
 template <int N>
 Error SizeOps<N>::rows_wave(const ImageArgs &a, int l0, int cnt, cudaStream_t st) {
-    using C = LargeCfg<N>;
-    const size_t smem_rows = rows_smem<N>();
+    const size_t smem_rows = RowsCfg<N>::smem;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_rows)));
-    const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
-    k_rows<N><<<dim3(bands, unsigned(cnt)), C::NT, smem_rows, st>>>(a, l0);
+    const unsigned bands = unsigned((a.r_alloc + RowsCfg<N>::RB - 1) / RowsCfg<N>::RB);
+    k_rows<N><<<dim3(bands, unsigned(cnt)), RowsCfg<N>::NT, smem_rows, st>>>(a, l0);
     BLINK_CUDA_TRY(cudaGetLastError());
     return Error{0, ""};
 }

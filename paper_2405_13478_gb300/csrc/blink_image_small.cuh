@@ -548,7 +548,7 @@ bool launch_fused_n(const ImageArgs &a, cudaStream_t st, Error &err) {
     err = Error{0, ""};
     if constexpr (N <= 256) {
         static_assert(SmallCfg<N>::P == kSmallColPairs, "column-pair buffer of the fused kernels");
-        if (a.force_path == 3 || !small_path_fits(N, a.r_alloc)) return false;
+        if (a.force_path >= 3 || !small_path_fits(N, a.r_alloc)) return false;
         size_t smem = small_smem<N>(a.r_alloc);
         const bool sched = a.sched && a.sched_ok && a.force_path != 2;
         if (sched) smem = std::max(smem, size_t(StageLayout(a.max_chunk, a.max_seg, kSchedSlots).bytes));

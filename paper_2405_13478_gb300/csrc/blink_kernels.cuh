@@ -39,7 +39,7 @@ struct ImageArgs {
     int max_seg;                // longest per-chunk schedule segment (entries)
     int *status;                // device status word (bounded waits report BLINK_ERR_TIMEOUT)
     const unsigned char *csr;   // row buckets of large-image channels (or null)
-    int force_path;             // 0 default, 1 scheduled fused, 2 atomic fused, 3 two-kernel
+    int force_path;             // 0 default, 1 scheduled fused, 2 atomic fused, 3 persistent queue, 4 waves
     size_t wave_budget;         // row-transform scratch per wave (0 = default, L2-sized)
     // fused epilogue (all null/0 when unused)
     const float2 *gains;        // antenna gains; layer l uses row (l mod gain_period, or l)
@@ -51,11 +51,19 @@ struct ImageArgs {
     const float *ref;           // reference images, addressed like the output
     int64_t wait_ns = -1;       // first-wait limit of the tensor-core kernels (< 0: default 1 s)
     int kmax = 0;               // max |k_u| of the group's channels (compact support of pass 1)
-    // optional second stream for the large-image path (forked from and joined
+    // optional second stream for the adjoint's waves (forked from and joined
     // back to the launch stream with these two events); null: one stream
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // work queue of the persistent large-image kernel (device words, zeroed by
+    // the launcher); null: the large-image path runs in waves of two kernels
+    int *queue = nullptr;
+    size_t queue_bytes = 0;
 };
+
+// Device words the persistent large-image kernel needs for a group of
+// n_layers layers (its work queue and per-layer counters).
+size_t image_queue_bytes(int n_layers);
 
 // Per-size launchers (defined in blink_image_impl.cuh, instantiated once per
 // size in the blink_image_<sizes>.cu units).

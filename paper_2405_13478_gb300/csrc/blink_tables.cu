@@ -33,6 +33,10 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
     }
     __shared__ double s_lambda, s_inv_lambda, s_inv_du;
     __shared__ float s_s32;
+    __shared__ int32_t s_hist[kCsrMaxBuckets];  // bucket sizes of this block (row buckets)
+    const bool want_csr = csr && ci0.csr_off >= 0;
+    if (want_csr)
+        for (int r = threadIdx.x; r < g.n_px / 2 + 1; r += blockDim.x) s_hist[r] = 0;
     if (threadIdx.x == 0) {
         s_lambda = __ddiv_rn(kSpeedOfLight, g.freq_hz);  // lambda = c / nu
         s_inv_lambda = __drcp_rn(s_lambda);
@@ -75,11 +79,7 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
         }
         codes[code_off + b] = code;
         if (cells) cells[ch * nb + b] = make_int2(ku, kv);
-        if (csr && ci0.csr_off >= 0) {  // bucket sizes (stored one slot up for the scan)
-            const CsrLayout cl(n, nb);
-            int32_t *cnt_r = reinterpret_cast<int32_t *>(csr + ci0.csr_off + cl.row_ptr);
-            atomicAdd(cnt_r + 1 + (code == kCodeDropped ? n / 2 : int(code_row(code))), 1);
-        }
+        if (want_csr) atomicAdd(&s_hist[code == kCodeDropped ? n / 2 : int(code_row(code))], 1);
     }
     // warp reductions, a block reduction, then one atomic per block and field
     // (per-warp atomics on the channel's three fields serialised in L2)
@@ -96,6 +96,16 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
         s_kept[warp] = wkept;
     }
     __syncthreads();
+    if (want_csr) {  // this block's bucket sizes, and the totals one slot up for the scan
+        const CsrLayout cl(n, nb);
+        int32_t *tot = reinterpret_cast<int32_t *>(csr + ci0.csr_off + cl.row_ptr);
+        int32_t *blk = reinterpret_cast<int32_t *>(csr + ci0.csr_off + cl.blk_off) + int64_t(blockIdx.x) * cl.n_bkt;
+        for (int r = threadIdx.x; r < cl.n_bkt; r += blockDim.x) {
+            const int32_t c = s_hist[r];
+            blk[r] = c;
+            if (c) atomicAdd(tot + 1 + r, c);
+        }
+    }
     if (threadIdx.x == 0) {
         int brow = -1, bk = 0;
         unsigned long long bkept = 0;
@@ -532,36 +542,120 @@ __global__ void k_sched_sort(const ChanInfo *__restrict__ info, unsigned char *_
     }
 }
 
-// Row buckets, step 2 (one CTA per channel): inclusive scan of the bucket
-// sizes into row_ptr and a copy into the fill cursors.
+// Row buckets, step 2 (one CTA per channel): exclusive scan of the bucket
+// totals into row_ptr, then per bucket the running start of every baseline
+// block (blk_off[blk][r] becomes the position of block blk's first entry of
+// bucket r).
 __global__ void k_csr_scan(const ChanInfo *__restrict__ info, unsigned char *__restrict__ csr, int64_t nb) {
     const ChanInfo ci = info[blockIdx.x];
     if (ci.csr_off < 0) return;
     const CsrLayout cl(ci.n_px, nb);
     int32_t *ptr = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.row_ptr);
-    int32_t *cur = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.cursor);
-    const int nbk = ci.n_px / 2 + 1;
+    int32_t *off = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.blk_off);
     if (threadIdx.x == 0) {
-        for (int r = 1; r <= nbk; ++r) ptr[r] += ptr[r - 1];
+        for (int r = 1; r <= cl.n_bkt; ++r) ptr[r] += ptr[r - 1];
     }
     __syncthreads();
-    for (int r = threadIdx.x; r <= nbk; r += blockDim.x) cur[r] = ptr[r];
+    for (int r = threadIdx.x; r < cl.n_bkt; r += blockDim.x) {
+        int32_t run = ptr[r];
+        for (int blk = 0; blk < cl.n_blk; ++blk) {
+            const int32_t t = off[int64_t(blk) * cl.n_bkt + r];
+            off[int64_t(blk) * cl.n_bkt + r] = run;
+            run += t;
+        }
+    }
 }
 
-// Row buckets, step 3: place every baseline in its bucket.
-__global__ void k_csr_fill(const ChanInfo *__restrict__ info, const uint32_t *__restrict__ codes,
-                           unsigned char *__restrict__ csr, int64_t nb) {
+// Row buckets, step 3: place every baseline in its bucket at its stable rank
+// (earlier baselines of the same bucket first).  Blocks of kCsrBlock
+// baselines, the blocks of k_cells.
+__global__ void __launch_bounds__(kCsrBlock) k_csr_fill(const ChanInfo *__restrict__ info,
+                                                       const uint32_t *__restrict__ codes,
+                                                       unsigned char *__restrict__ csr, int64_t nb) {
+    constexpr int W = kCsrBlock / 32;
+    __shared__ int32_t wcnt[W][kCsrMaxBuckets];
     const ChanInfo ci = info[blockIdx.y];
     if (ci.csr_off < 0) return;
-    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
     const CsrLayout cl(ci.n_px, nb);
-    int32_t *cur = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.cursor);
-    uint2 *ents = reinterpret_cast<uint2 *>(csr + ci.csr_off + cl.ents);
-    const uint32_t code = codes[ci.code_off + b];
-    const int bucket = code == kCodeDropped ? ci.n_px / 2 : int(code_row(code));
-    const int pos = atomicAdd(cur + bucket, 1);
-    ents[pos] = make_uint2(uint32_t(b), code);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < W * cl.n_bkt; i += kCsrBlock) wcnt[i / cl.n_bkt][i % cl.n_bkt] = 0;
+    const int64_t b = int64_t(blockIdx.x) * kCsrBlock + threadIdx.x;
+    uint32_t code = kCodeDropped;
+    int bucket = -1;
+    if (b < nb) {
+        code = codes[ci.code_off + b];
+        bucket = code == kCodeDropped ? ci.n_px / 2 : int(code_row(code));
+    }
+    const unsigned same = __match_any_sync(0xFFFFFFFFu, bucket);
+    __syncthreads();
+    if (bucket >= 0 && (__ffs(same) - 1) == lane) wcnt[warp][bucket] = __popc(same);
+    __syncthreads();
+    if (bucket < 0) return;
+    int rank = __popc(same & ((1u << lane) - 1u));
+    for (int w = 0; w < warp; ++w) rank += wcnt[w][bucket];
+    const int32_t *off = reinterpret_cast<const int32_t *>(csr + ci.csr_off + cl.blk_off);
+    uint2 *ents = reinterpret_cast<uint2 *>(csr + ci.csr_off + cl.ents_by_b);
+    ents[off[int64_t(blockIdx.x) * cl.n_bkt + bucket] + rank] = make_uint2(uint32_t(b), code);
+}
+
+// Row buckets, step 4: inside every bucket, a stable counting sort of the
+// baseline-ordered entries by column (one warp per bucket, 32 entries per
+// step; the dropped bucket is copied as it is).  Grid: (ceil(buckets / 8),
+// channels) x 256.
+__global__ void __launch_bounds__(256) k_csr_sort(const ChanInfo *__restrict__ info,
+                                                  unsigned char *__restrict__ csr, int64_t nb) {
+    constexpr int W = 8;
+    __shared__ int32_t start[W][1024];  // per-warp column counts, then running positions
+    const ChanInfo ci = info[blockIdx.y];
+    if (ci.csr_off < 0) return;
+    const CsrLayout cl(ci.n_px, nb);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bk = blockIdx.x * W + warp;
+    if (bk >= cl.n_bkt) return;
+    const int32_t *ptr = reinterpret_cast<const int32_t *>(csr + ci.csr_off + cl.row_ptr);
+    const uint2 *src = reinterpret_cast<const uint2 *>(csr + ci.csr_off + cl.ents_by_b);
+    uint2 *dst = reinterpret_cast<uint2 *>(csr + ci.csr_off + cl.ents);
+    const int p0 = ptr[bk], p1 = ptr[bk + 1];
+    if (bk == cl.n_bkt - 1) {  // dropped baselines: baseline order
+        for (int e = p0 + lane; e < p1; e += 32) dst[e] = src[e];
+        return;
+    }
+    const int n = ci.n_px;
+    int32_t *st = start[warp];
+    for (int c = lane; c < n; c += 32) st[c] = 0;
+    __syncwarp();
+    for (int e = p0 + lane; e < p1; e += 32) atomicAdd(&st[code_col(src[e].y)], 1);
+    __syncwarp();
+    // exclusive scan over the n columns: lane l owns columns [l per, (l+1) per)
+    const int per = (n + 31) / 32;
+    int run = 0;
+    for (int k = 0; k < per; ++k)
+        if (lane * per + k < n) run += st[lane * per + k];
+    int incl = run;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    int acc = p0 + incl - run;
+    for (int k = 0; k < per; ++k) {
+        if (lane * per + k >= n) break;
+        const int c = st[lane * per + k];
+        st[lane * per + k] = acc;
+        acc += c;
+    }
+    __syncwarp();
+    for (int e0 = p0; e0 < p1; e0 += 32) {
+        const int e = e0 + lane;
+        const bool live = e < p1;
+        const uint2 en = live ? src[e] : make_uint2(0u, 0u);
+        const int col = live ? int(code_col(en.y)) : -1;
+        const unsigned same = __match_any_sync(0xFFFFFFFFu, col);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        if (live) dst[st[col] + rank] = en;
+        __syncwarp();
+        if (live && (__ffs(same) - 1) == lane) st[col] += __popc(same);
+        __syncwarp();
+    }
 }
 
 // Per-layer copy of the per-channel signed cells (blink_cells).
@@ -594,7 +688,7 @@ Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, co
                     ChanInfo *info, uint32_t *codes, int2 *cells, float *wgt, bool any_counts,
                     cudaStream_t st, unsigned char *sched, unsigned char *csr) {
     if (n_chan == 0) return Error{0, ""};
-    const int tpb = 256;
+    const int tpb = kCsrBlock;  // k_cells' blocks are the blocks of the row-bucket sort
     dim3 grid(unsigned((nb + tpb - 1) / tpb), unsigned(n_chan));
     k_cells<<<grid, tpb, 0, st>>>(ant_xyz, n_ant, nb, geom, info, codes, cells,
                                   any_counts ? reinterpret_cast<int32_t *>(wgt) : nullptr, sched, csr);
@@ -615,9 +709,12 @@ Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, co
         BLINK_CUDA_TRY(cudaGetLastError());
     }
     if (csr) {
-        k_csr_scan<<<n_chan, 32, 0, st>>>(info, csr, nb);
+        k_csr_scan<<<n_chan, 256, 0, st>>>(info, csr, nb);
         BLINK_CUDA_TRY(cudaGetLastError());
-        k_csr_fill<<<grid, tpb, 0, st>>>(info, codes, csr, nb);
+        k_csr_fill<<<dim3(unsigned((nb + kCsrBlock - 1) / kCsrBlock), unsigned(n_chan)), kCsrBlock, 0, st>>>(
+            info, codes, csr, nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_csr_sort<<<dim3(unsigned((kCsrMaxBuckets + 7) / 8), unsigned(n_chan)), 256, 0, st>>>(info, csr, nb);
         BLINK_CUDA_TRY(cudaGetLastError());
     }
     k_finalize<<<n_chan, 512, 0, st>>>(info, wgt);

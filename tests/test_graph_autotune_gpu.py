@@ -73,7 +73,7 @@ def small_size_workload(seed):
     return ws, layers, vis
 
 
-@pytest.mark.parametrize("path", [1, 2, 3])
+@pytest.mark.parametrize("path", [1, 2, 3, 4])
 def test_every_kernel_path_matches_oracle_small_sizes(torch, ctx, path):
     from paper_2405_13478_gb300 import binding
     ws, layers, vis = small_size_workload(seed=21)
@@ -82,7 +82,7 @@ def test_every_kernel_path_matches_oracle_small_sizes(torch, ctx, path):
     taken = []
     for g in range(len(layers)):
         try:
-            plan.set_tuning(g, path, 4 << 20 if path == 3 else 0)
+            plan.set_tuning(g, path, 4 << 20 if path >= 3 else 0)
             taken.append(path)
         except binding.BlinkError as e:
             # the fused kernels are unavailable where the image's canonical
@@ -100,18 +100,19 @@ def test_every_kernel_path_matches_oracle_small_sizes(torch, ctx, path):
     plan.close()
 
 
+@pytest.mark.parametrize("path", [3, 4])
 @pytest.mark.parametrize("wave_mb", [1, 12, 96])
-def test_wave_budgets_match_oracle_large_sizes(torch, ctx, wave_mb):
+def test_wave_budgets_match_oracle_large_sizes(torch, ctx, wave_mb, path):
     ws = synth.uneven_batch(seed=8, n_times=30)
     layers, total, vis = mixed_layers(ws, [20, 21], [200, 300, 767])   # 512, 1024, 1024
     plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
     for g, _ in enumerate(plan.tuning()):
-        plan.set_tuning(g, 3, wave_mb << 20)
+        plan.set_tuning(g, path, wave_mb << 20)
     out = torch.full((total,), float("nan"), device="cuda")
     plan.image(vis.reshape(-1).cuda(), out)
     torch.cuda.synchronize()
     want, _ = oracle.image_batch(ws.ant_xyz, layers, vis.reshape(-1).numpy(), "fft")
-    assert_close(split(out, layers), want, what=f"wave {wave_mb} MB")
+    assert_close(split(out, layers), want, what=f"path {path}, scratch {wave_mb} MB")
     plan.close()
 
 
@@ -121,7 +122,7 @@ def test_unavailable_paths_are_rejected(torch, ctx):
     layers, total, vis = mixed_layers(ws, [20], [0, 300])   # 128, 1024
     plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
     assert [t[0] for t in plan.tuning()] == [128, 1024]
-    for bad in [(1, 1, 0), (1, 2, 0), (0, 4, 0), (0, 3, -1), (2, 3, 0), (-1, 0, 0)]:
+    for bad in [(1, 1, 0), (1, 2, 0), (0, 5, 0), (0, 3, -1), (2, 3, 0), (-1, 0, 0)]:
         with pytest.raises(binding.BlinkError) as ei:
             plan.set_tuning(*bad)
         assert ei.value.status == binding.ERR_INVALID
@@ -138,7 +139,7 @@ def test_autotune_choice_keeps_parity(torch, ctx):
     plan.autotune(d_vis, out)
     tune = plan.tuning()
     assert [t[0] for t in tune] == [128, 256, 512, 1024]
-    assert all(t[1] in (1, 2, 3) for t in tune)
+    assert all(t[1] in (1, 2, 3, 4) for t in tune)
     out.fill_(float("nan"))
     plan.image(d_vis, out)
     torch.cuda.synchronize()

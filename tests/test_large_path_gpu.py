@@ -1,0 +1,185 @@
+"""GPU tests of the persistent large-image path (row and column items pulled
+from a device work queue, a scratch ring in L2, per-layer counters).
+
+- Images of every large size match the FP64 oracle (1e-5 of the peak) when
+  the group has many more layers than ring slots, with the default ring and
+  with a two-slot ring that forces every dependency wait.
+- The gridding of the large path sums every cell's visibilities in a fixed
+  order (sorted row buckets, one writer per cell), so images are the same
+  bits from run to run, and the same bits whatever the ring size or the
+  kernel path (persistent queue or waves).
+- With the wait limit at zero the dependency waits may give up: the status
+  word then says BLINK_ERR_TIMEOUT, and the same plan images correctly again
+  once the limit is restored.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    from paper_2405_13478_gb300 import binding, build
+    build.build()
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def layers_of(ws, times, chans):
+    """Layers (one per (t, c)) over a compact [T'][C'][B] visibility tensor."""
+    from paper_2405_13478_gb300 import binding
+    B = ws.n_baselines
+    layers = []
+    for t in range(len(times)):
+        for k, c in enumerate(chans):
+            layers.append(dict(n_px=int(ws.n_px[c]), weighting=ws.weighting, freq_hz=float(ws.freqs_hz[c]),
+                               delta_u=float(ws.delta_u[c]), vis_offset=(t * len(chans) + k) * B))
+    layers, total = binding.layer_out_offsets(layers)
+    vis = ws.vis("cpu", times=times)[:, chans, :].contiguous()
+    return layers, total, vis
+
+
+def check_against_oracle(ws, layers, vis_cpu, out, picks):
+    B = ws.n_baselines
+    flat = vis_cpu.reshape(-1)
+    sub = [dict(layers[k], vis_offset=i * B) for i, k in enumerate(picks)]
+    v = np.concatenate([flat[layers[k]["vis_offset"]:layers[k]["vis_offset"] + B].numpy() for k in picks])
+    want, _ = oracle.image_batch(ws.ant_xyz, sub, v, "fft")
+    o = out.cpu().numpy()
+    for k, w in zip(picks, want):
+        n = layers[k]["n_px"]
+        g = o[layers[k]["out_offset"]:layers[k]["out_offset"] + n * n].reshape(n, n)
+        assert np.isfinite(g).all(), f"layer {k}: non-finite"
+        err = np.abs(g.astype(np.float64) - w).max()
+        assert err <= IMG_TOL * np.abs(w).max(), f"layer {k}: err {err:.3e} vs peak {np.abs(w).max():.3e}"
+
+
+def test_many_layers_through_the_ring_match_oracle(torch, ctx):
+    # 24 layers of 1024^2 (4 MB of pass-1 rows each) and 8 of 512^2 in one
+    # call: more layers than the 48 MB ring holds, so slots are reused
+    ws = synth.uneven_batch(seed=21, n_times=8)
+    layers, total, vis = layers_of(ws, list(range(8)), [200, 300, 700, 767])
+    out = torch.full((total,), float("nan"), device="cuda")
+    ctx.image_batch(torch.as_tensor(ws.ant_xyz).cuda(), layers, vis.reshape(-1).cuda(), out)
+    torch.cuda.synchronize()
+    check_against_oracle(ws, layers, vis, out, [0, 2, 3, 22, 29, 31])
+
+
+@pytest.mark.parametrize("path,ring_mb", [(3, 8), (3, 0), (4, 8), (4, 0)])
+def test_ring_size_does_not_change_a_bit(torch, ctx, path, ring_mb):
+    # a two-slot ring (8 MB at 1024^2) makes nearly every row item wait for the
+    # column items of the layer two back; the images must be bit-identical to
+    # the default ring's and match the oracle -- and so must the waves of two
+    # kernels (path 4), which run the same row and column items
+    from paper_2405_13478_gb300 import binding
+    ws = synth.uneven_batch(seed=22, n_times=10)
+    layers, total, vis = layers_of(ws, list(range(10)), [300, 767])
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    d_vis = vis.reshape(-1).cuda()
+    ref = torch.empty(total, device="cuda")
+    ctx.image_batch(d_xyz, layers, d_vis, ref)
+    plan = ctx.plan(d_xyz, layers)
+    plan.set_tuning(0, path, ring_mb << 20)
+    out = torch.full((total,), float("nan"), device="cuda")
+    plan.image(d_vis, out)
+    plan.check()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    check_against_oracle(ws, layers, vis, out, [0, 19])
+    plan.close()
+
+
+@pytest.mark.parametrize("name", ["uneven_1024", "station_1024", "station_512"])
+def test_large_images_are_bit_reproducible(torch, ctx, name):
+    # station rows hold ~700 baselines, so a band's entries span several
+    # staging chunks and cells straddle chunk boundaries
+    if name == "uneven_1024":
+        ws = synth.uneven_batch(seed=23, n_times=3)
+        layers, total, vis = layers_of(ws, [0, 1, 2], [300, 400, 767])
+    elif name == "station_1024":
+        ws = synth.station_gains(seed=24, n_times=2)
+        layers, total, vis = layers_of(ws, [0, 1], [0, 3, 7])
+    else:
+        ws = synth.station_512(seed=25, n_times=2)
+        layers, total, vis = layers_of(ws, [0, 1], [0, 5, 15])
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    d_vis = vis.reshape(-1).cuda()
+    a = torch.empty(total, device="cuda")
+    b = torch.empty(total, device="cuda")
+    ctx.image_batch(d_xyz, layers, d_vis, a)
+    ctx.image_batch(d_xyz, layers, d_vis, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    check_against_oracle(ws, layers, vis, a, [0, len(layers) - 1])
+
+
+def test_gains_and_reference_on_the_persistent_path(torch, ctx):
+    # fused epilogue (gains at gridding, reference subtracted at the store)
+    # on 1024^2 layers of the station
+    ws = synth.station_gains(seed=26, n_times=2)
+    layers, total, vis = layers_of(ws, [0, 1], [1, 6])
+    C = 2  # gain rows, one per channel of the call
+    g = np.stack([ws.gains, 0.9 * np.conj(ws.gains)]).astype(np.complex64)
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    plan = ctx.plan(d_xyz, layers)
+    d_vis = vis.reshape(-1).cuda()
+    ref = torch.empty(total, device="cuda")
+    plan.image(d_vis, ref)
+    ref.mul_(0.25)
+    out = torch.full((total,), float("nan"), device="cuda")
+    d_g = torch.as_tensor(g.reshape(-1)).cuda()
+    plan.image(d_vis, out, gains=d_g, gain_stride=ws.n_ant, gain_period=C, ref=ref)
+    plan.check()
+    torch.cuda.synchronize()
+    B = ws.n_baselines
+    rows = np.stack([g[k % C] for k in range(len(layers))]).astype(np.complex128)
+    want, _ = oracle.image_batch(ws.ant_xyz, [dict(L, vis_offset=i * B) for i, L in enumerate(layers)],
+                                 vis.reshape(-1).numpy(), "fft", gains=rows.reshape(-1), gain_stride=ws.n_ant,
+                                 ref=ref.cpu().double().numpy())
+    o = out.cpu().numpy()
+    r = ref.cpu().numpy()
+    for L, w in zip(layers, want):
+        n2 = L["n_px"] ** 2
+        got = o[L["out_offset"]:L["out_offset"] + n2].reshape(w.shape)
+        rr = r[L["out_offset"]:L["out_offset"] + n2]
+        assert np.abs(got - w).max() <= IMG_TOL * (np.abs(w).max() + np.abs(rr).max())
+    plan.close()
+
+
+def test_dependency_wait_timeout_is_reported_and_the_plan_recovers(torch, ctx):
+    from paper_2405_13478_gb300 import binding
+    ws = synth.uneven_batch(seed=27, n_times=4)
+    layers, total, vis = layers_of(ws, [0, 1, 2, 3], [700, 767])
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    d_vis = vis.reshape(-1).cuda()
+    plan = ctx.plan(d_xyz, layers)
+    out = torch.full((total,), float("nan"), device="cuda")
+    ctx.set_wait_limit(0)
+    try:
+        plan.image(d_vis, out)
+        try:
+            plan.check()       # the waits may or may not have had to wait
+        except binding.BlinkError as e:
+            assert e.status == binding.ERR_TIMEOUT
+    finally:
+        ctx.set_wait_limit(-1)
+    plan.check()               # the status word was cleared
+    out.fill_(float("nan"))
+    plan.image(d_vis, out)
+    plan.check()
+    torch.cuda.synchronize()
+    check_against_oracle(ws, layers, vis, out, [0, 7])
+    plan.close()
