@@ -176,7 +176,10 @@ BLINK_API int blink_apply_gains(blink_ctx *ctx, int n_ant, const blink_layer *h_
 /* Chain rule of blink_degrid's output to the gains, summed over all layers:
  * d_dgains[i] = sum_l [ sum_{j>i} d_dvis(ij) g_j conj(M_ij)
  *                     + sum_{k<i} conj(d_dvis(ki)) g_k M_ki ]
- * (dL/dRe g + i dL/dIm g), accumulated in FP64, overwrites d_dgains. */
+ * (dL/dRe g + i dL/dIm g), overwrites d_dgains.  Products in FP32, sums in
+ * FP64 in a fixed order (the same bits from run to run); every baseline is
+ * read once, row by row of the upper triangle.  At most 1024 antennas
+ * (BLINK_ERR_UNSUPPORTED above). */
 BLINK_API int blink_gain_grad(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int n_layers,
                               const float *d_dvis, const float *d_model, const float *d_gains, float *d_dgains,
                               void *stream);

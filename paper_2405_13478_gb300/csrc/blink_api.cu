@@ -921,6 +921,7 @@ int blink_gain_grad(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int 
     int st = check_gain_args(ctx, n_ant, h_layers, n_layers);
     if (st) return st;
     if (!d_dvis || !d_model || !d_gains || !d_dgains) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    if (n_ant > 1024) return fail(ctx, BLINK_ERR_UNSUPPORTED, "gain gradient: more than 1024 antennas");
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n_layers == 0) {
@@ -930,9 +931,16 @@ int blink_gain_grad(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int 
     int64_t *d_off = nullptr;
     st = upload_offsets(ctx, h_layers, n_layers, s, &d_off);
     if (st) return st;
+    void *d_part = nullptr;
+    if (cudaMallocFromPoolAsync(&d_part, blink::gain_grad_scratch_bytes(n_layers, n_ant), ctx->pool, s) !=
+        cudaSuccess) {
+        cudaFreeAsync(d_off, s);
+        return fail(ctx, BLINK_ERR_WORKSPACE, "gain-gradient scratch allocation failed");
+    }
     Error e = blink::launch_gain_grad(reinterpret_cast<const float2 *>(d_dvis), reinterpret_cast<const float2 *>(d_model),
                                       reinterpret_cast<const float2 *>(d_gains), d_off, n_layers, n_ant,
-                                      reinterpret_cast<float2 *>(d_dgains), s);
+                                      reinterpret_cast<float2 *>(d_dgains), d_part, s);
+    cudaFreeAsync(d_part, s);
     cudaFreeAsync(d_off, s);
     if (e.status) return fail(ctx, e);
     ctx->err.clear();

@@ -55,15 +55,15 @@ struct ChanInfo {
 // row_ptr[r + 1] index ents = {baseline, packed code}; bucket N/2 holds the
 // dropped baselines.  Inside a row bucket the entries are ordered by column,
 // then by baseline; the dropped bucket by baseline.  Both orders come from
-// stable counting sorts (by row over blocks of kCsrBlock baselines, with
-// blk_off holding each block's count and then its first position per bucket,
-// into ents_by_b; then by column inside every row), so the entries of one cell
-// are contiguous and in a fixed order, and the gridding that sums them is
-// deterministic.
+// stable counting sorts -- by row over blocks of kCsrBlock baselines (tot[r]
+// counts bucket r; blk_off[r][blk] holds block blk's count of bucket r, then
+// its first position), into ents_by_b; then by column inside every row --
+// so the entries of one cell are contiguous and in a fixed order, and the
+// gridding that sums them is deterministic.
 constexpr int kCsrBlock = 256;        // baselines per block of the bucket sort
 constexpr int kCsrMaxBuckets = 1024 / 2 + 1;  // largest supported n_px / 2 + 1
 struct CsrLayout {
-    int64_t row_ptr, blk_off, ents_by_b, ents, bytes;
+    int64_t row_ptr, tot, blk_off, ents_by_b, ents, bytes;
     int32_t n_blk, n_bkt;  // baseline blocks, buckets (n_px / 2 rows + dropped)
     __host__ __device__ CsrLayout(int n_px, int64_t nb) {
         auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
@@ -71,6 +71,7 @@ struct CsrLayout {
         n_blk = int32_t((nb + kCsrBlock - 1) / kCsrBlock);
         int64_t o = 0;
         row_ptr = o; o = up(o + 4 * int64_t(n_bkt + 1));
+        tot = o; o = up(o + 4 * int64_t(n_bkt));
         blk_off = o; o = up(o + 4 * int64_t(n_blk) * n_bkt);
         ents_by_b = o; o = up(o + 8 * nb);
         ents = o; o = up(o + 8 * nb);

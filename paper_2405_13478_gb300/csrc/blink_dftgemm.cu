@@ -30,6 +30,7 @@
 #include "blink_common.cuh"
 #include "blink_kernels.cuh"
 #include "blink_sync.cuh"
+#include "blink_grid_sorted.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -41,6 +42,11 @@ namespace blink {
 namespace {
 
 constexpr int kTileM = 128, kTileN = 256;
+// Output columns of a pass-2 tile: 256 for one product; 128 for the split
+// modes, whose four operand tiles then take 96 KB of shared memory (K = 96)
+// so two CTAs share an SM (and their TMEM accumulators fit its 512 columns).
+template <int SPLIT>
+constexpr int tile_n() { return SPLIT == 3 ? 128 : kTileN; }
 
 struct DftArgs {
     const uint16_t *a_hi, *a_lo;  // [N / 128] blocks of 128 x K (tiled)
@@ -116,7 +122,7 @@ __global__ void k_dft_table(int N, int Rp, uint16_t *a_hi, uint16_t *a_lo) {
 // ---------------------------------------------------------------- operand B
 // Per layer: T (FP32 complex [r_alloc][N] in scratch) -> B hi/lo tiles.
 // One CTA per layer.  FP16: scale 2^-e with the largest |entry| below 2^14.
-template <bool FP16>
+template <bool FP16, int SPLIT>
 __global__ void __launch_bounds__(256) k_split(const float2 *__restrict__ T, int r_alloc, int N, int Rp,
                                                const DevLayer *__restrict__ layers,
                                                const ChanInfo *__restrict__ chans, int l0, uint16_t *b_hi,
@@ -158,7 +164,8 @@ __global__ void __launch_bounds__(256) k_split(const float2 *__restrict__ T, int
             h[j] = to_bits<FP16>(x);
             l[j] = to_bits<FP16>((x - from_bits<FP16>(h[j])) * lo_scale);
         }
-        const int64_t o = int64_t(p / kTileN) * kTileN * K + tiled(p % kTileN, 8 * k8, K);
+        constexpr int TN = tile_n<SPLIT>();
+        const int64_t o = int64_t(p / TN) * TN * K + tiled(p % TN, 8 * k8, K);
         uint4 hv, lv;
         hv.x = h[0] | (uint32_t(h[1]) << 16); hv.y = h[2] | (uint32_t(h[3]) << 16);
         hv.z = h[4] | (uint32_t(h[5]) << 16); hv.w = h[6] | (uint32_t(h[7]) << 16);
@@ -191,19 +198,20 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t da, uint64_t db,
 
 // Grid: (N / 128, N / 256, layers of the wave).  128 threads.
 template <bool FP16, int SPLIT>
-__global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__restrict__ out,
+__global__ void __launch_bounds__(128, SPLIT == 3 ? 2 : 1) k_dftgemm(DftArgs d, int l0, float *__restrict__ out,
                                                     const float *__restrict__ ref) {
     constexpr bool CROSS = FP16 && SPLIT == 3;      // separate accumulator for the cross terms
-    constexpr uint32_t NCOL = CROSS ? 512 : 256;    // TMEM columns
-    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int TN = tile_n<SPLIT>();
+    constexpr uint32_t NCOL = CROSS ? 2 * TN : TN;   // TMEM columns
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
     __shared__ uint64_t bar_load, bar_mma;
     __shared__ uint32_t tmem_base;
     const int K = d.K, N = d.n_px, H = N / 2;
     const int mt = blockIdx.x, nt = blockIdx.y, lw = blockIdx.z;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t a_bytes = uint32_t(kTileM) * K * 2, b_bytes = uint32_t(kTileN) * K * 2;
-    unsigned char *sA_hi = sm, *sA_lo = sm + a_bytes;
-    unsigned char *sB_hi = sm + (SPLIT == 3 ? 2 : 1) * a_bytes;
+    const uint32_t a_bytes = uint32_t(kTileM) * K * 2, b_bytes = uint32_t(TN) * K * 2;
+    unsigned char *sA_hi = smem_tc, *sA_lo = smem_tc + a_bytes;
+    unsigned char *sB_hi = smem_tc + (SPLIT == 3 ? 2 : 1) * a_bytes;
     unsigned char *sB_lo = sB_hi + b_bytes;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_load)));
@@ -223,9 +231,9 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__
         const uint32_t total = (SPLIT == 3 ? 2 : 1) * (a_bytes + b_bytes);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&bar_load)), "r"(total)
                      : "memory");
-        const int n_tiles = N / kTileN;
+        const int n_tiles = N / TN;
         const uint16_t *ga[2] = {d.a_hi + int64_t(mt) * kTileM * K, d.a_lo + int64_t(mt) * kTileM * K};
-        const int64_t bo = (int64_t(lw) * n_tiles + nt) * kTileN * K;
+        const int64_t bo = (int64_t(lw) * n_tiles + nt) * TN * K;
         const uint16_t *gb[2] = {d.b_hi + bo, d.b_lo + bo};
         unsigned char *sa[2] = {sA_hi, sA_lo}, *sb[2] = {sB_hi, sB_lo};
         for (int h = 0; h < (SPLIT == 3 ? 2 : 1); ++h) {
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__
     if (tid == 0 && loaded) {
         // D = A B^T over K in steps of 16: M = 128, N = 256, both K-major
         constexpr uint32_t fmt = FP16 ? 0u : 1u;  // 0 FP16, 1 BF16
-        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(kTileN >> 3) << 17) |
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(TN >> 3) << 17) |
                                (uint32_t(kTileM >> 4) << 24);
         const uint32_t sbo = uint32_t(K / 8) * 128;
         for (int s = 0; s < K / 16; ++s) {
@@ -258,7 +266,7 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__
             if constexpr (SPLIT == 3) {
                 const uint64_t al = smem_desc(saddr(sA_lo) + s * 256, 128, sbo);
                 const uint64_t bl = smem_desc(saddr(sB_lo) + s * 256, 128, sbo);
-                const uint32_t tx = CROSS ? tmem + 256 : tmem;
+                const uint32_t tx = CROSS ? tmem + TN : tmem;
                 mma_f16(tx, ah, bl, idesc, CROSS ? uint32_t(s > 0) : 1u);
                 mma_f16(tx, al, bh, idesc, 1u);
             }
@@ -281,40 +289,35 @@ __global__ void __launch_bounds__(128, 1) k_dftgemm(DftArgs d, int l0, float *__
         float scale = ((d.flags & 1u) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
         if (FP16) scale = ldexpf(scale, d.b_exp[lw]);
         const float cross = 1.f / float(1 << lo_shift<FP16>());
-        const int y = mt * kTileM + warp * 32 + lane;
-        float *row = out + L.out_off + int64_t(y) * N;
-        for (int c0 = 0; c0 < kTileN; c0 += 32) {
+        // the operands are consumed: each warp transposes its 32 x 32 blocks
+        // through shared memory, so every store instruction writes one image
+        // row's 32 consecutive columns (128 bytes) instead of 32 rows' pieces
+        float *stg = reinterpret_cast<float *>(smem_tc) + warp * (32 * 33);
+        float *img = out + L.out_off;
+        const float *rimg = ref ? ref + L.out_off : nullptr;
+        const int y0 = mt * kTileM + warp * 32;
+        for (int c0 = 0; c0 < TN; c0 += 32) {
             uint32_t r[32];
             tmem_ld32<32>(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
             uint32_t q[32];
-            if constexpr (CROSS) tmem_ld32<32>(tmem + (uint32_t(warp * 32) << 16) + uint32_t(256 + c0), q);
+            if constexpr (CROSS) tmem_ld32<32>(tmem + (uint32_t(warp * 32) << 16) + uint32_t(TN + c0), q);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int p0 = nt * kTileN + c0;
-            float *o = row + ((p0 + H) % N);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-                float4 v;
-                float e0 = __uint_as_float(r[j]), e1 = __uint_as_float(r[j + 1]);
-                float e2 = __uint_as_float(r[j + 2]), e3 = __uint_as_float(r[j + 3]);
-                if constexpr (CROSS) {
-                    e0 = fmaf(__uint_as_float(q[j]), cross, e0);
-                    e1 = fmaf(__uint_as_float(q[j + 1]), cross, e1);
-                    e2 = fmaf(__uint_as_float(q[j + 2]), cross, e2);
-                    e3 = fmaf(__uint_as_float(q[j + 3]), cross, e3);
-                }
-                v.x = e0 * scale;
-                v.y = e1 * scale;
-                v.z = e2 * scale;
-                v.w = e3 * scale;
-                if (ref) {  // fused epilogue: dirty - reference
-                    const float4 rf = __ldcs(reinterpret_cast<const float4 *>(ref + (o - out) + j));
-                    v.x -= rf.x;
-                    v.y -= rf.y;
-                    v.z -= rf.z;
-                    v.w -= rf.w;
-                }
-                __stcs(reinterpret_cast<float4 *>(o + j), v);
+            for (int j = 0; j < 32; ++j) {
+                float e = __uint_as_float(r[j]);
+                if constexpr (CROSS) e = fmaf(__uint_as_float(q[j]), cross, e);
+                stg[lane * 33 + j] = e * scale;
             }
+            __syncwarp();
+            const int x = (nt * TN + c0 + H) % N + lane;  // 32 contiguous image columns
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                const int64_t o = int64_t(y0 + i) * N + x;
+                float v = stg[i * 33 + lane];
+                if (rimg) v -= __ldcs(rimg + o);  // fused epilogue: dirty - reference
+                __stcs(img + o, v);
+            }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -383,34 +386,41 @@ __global__ void __launch_bounds__(256) k_grid_a1(Grid1Args g, int l0, int pack) 
     // block may hold a larger-support layer of an earlier wave
     const int nrows = max(0, min(8, R - r0));
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < 8 * Kc; i += nt) gc[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    const float2 *vis = g.vis + L.vis_off;
-    auto put = [&](uint32_t cd, float2 v) {
-        const int r = int(code_row(cd)) - r0, col = int(code_col(cd));
-        const int ku = col <= H ? col : col - N;
-        if (r < 0 || r >= nrows || ku < -kmax || ku > kmax) return;
-        if (code_conj(cd)) v.y = -v.y;
-        float2 *cell = gc + r * Kc + (ku + kmax);
-        atomicAdd(&cell->x, v.x);
-        atomicAdd(&cell->y, v.y);
+    auto zero = [&]() {
+        for (int i = tid; i < 8 * Kc; i += nt) gc[i] = make_float2(0.f, 0.f);
     };
+    const float2 *vis = g.vis + L.vis_off;
     if (nrows == 0) {
         // nothing to grid: the rows below are written as zeros
-    } else if (g.csr && ci.csr_off >= 0) {  // only this band's baselines, from the row buckets
+        zero();
+        __syncthreads();
+    } else if (g.csr && ci.csr_off >= 0) {
+        // only this band's baselines, from the sorted row buckets: the same
+        // deterministic, atomic-free sums as the FP32 path
         const CsrLayout cl(N, g.nb);
-        const int32_t *ptr = reinterpret_cast<const int32_t *>(g.csr + ci.csr_off + cl.row_ptr);
-        const uint2 *ents = reinterpret_cast<const uint2 *>(g.csr + ci.csr_off + cl.ents);
-        const int e1 = ptr[r0 + nrows];
-        for (int e = ptr[r0] + tid; e < e1; e += nt) {
-            const uint2 en = __ldg(ents + e);
-            put(en.y, __ldg(vis + en.x));
-        }
+        auto cell = [&](uint32_t key) -> float2 * {
+            const int col = int(key & 0xFFFFu), ku = col <= H ? col : col - N;
+            return (ku < -kmax || ku > kmax) ? nullptr : gc + int(key >> 16) * Kc + (ku + kmax);
+        };
+        grid_band_sorted<256>(r0, nrows, reinterpret_cast<const int32_t *>(g.csr + ci.csr_off + cl.row_ptr),
+                              reinterpret_cast<const uint2 *>(g.csr + ci.csr_off + cl.ents), vis,
+                              LayerGains{nullptr, nullptr, 0}, tid, cell, zero);
     } else {
+        // a channel without row buckets: shared-memory atomics over the code table
+        zero();
+        __syncthreads();
         const uint32_t *code = g.codes + ci.code_off;
         for (int64_t b = tid; b < g.nb; b += nt) {
             const uint32_t cd = __ldg(code + b);
-            if (cd != kCodeDropped) put(cd, __ldcs(vis + b));
+            if (cd == kCodeDropped) continue;
+            const int r = int(code_row(cd)) - r0, col = int(code_col(cd));
+            const int ku = col <= H ? col : col - N;
+            if (r < 0 || r >= nrows || ku < -kmax || ku > kmax) continue;
+            float2 v = __ldcs(vis + b);
+            if (code_conj(cd)) v.y = -v.y;
+            float2 *cell = gc + r * Kc + (ku + kmax);
+            atomicAdd(&cell->x, v.x);
+            atomicAdd(&cell->y, v.y);
         }
     }
     __syncthreads();
@@ -482,15 +492,15 @@ struct Gemm1Args {
 template <int SPLIT>
 __global__ void __launch_bounds__(128, 1) k_gemm1(Gemm1Args d, int l0, int pack, int cnt) {
     constexpr uint32_t NCOL = kTile1N;
-    extern __shared__ __align__(1024) unsigned char sm[];
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
     __shared__ uint64_t bar_load, bar_mma;
     __shared__ uint32_t tmem_base;
     const int K1 = d.K1, N = d.n_px, Rp = d.Rp, K2 = 2 * Rp;
     const int nt = blockIdx.x, blk = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t a_bytes = 128u * K1 * 2, b_bytes = uint32_t(kTile1N) * K1 * 2;
-    unsigned char *sA_hi = sm, *sA_lo = sm + a_bytes;
-    unsigned char *sB_hi = sm + (SPLIT == 3 ? 2 : 1) * a_bytes;
+    unsigned char *sA_hi = smem_tc, *sA_lo = smem_tc + a_bytes;
+    unsigned char *sB_hi = smem_tc + (SPLIT == 3 ? 2 : 1) * a_bytes;
     unsigned char *sB_lo = sB_hi + b_bytes;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar_load)));
@@ -574,7 +584,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm1(Gemm1Args d, int l0, int pack,
                     const int p = (n0 + j) % N;
                     const float x = r < R ? __uint_as_float(v[j]) : 0.f;
                     const uint16_t hb = to_bits<false>(x);
-                    const int64_t o = int64_t(p / kTileN) * kTileN * K2 + tiled(p % kTileN, k2, K2);
+                    constexpr int TN = tile_n<SPLIT>();
+                    const int64_t o = int64_t(p / TN) * TN * K2 + tiled(p % TN, k2, K2);
                     th[o] = hb;
                     tl[o] = to_bits<false>(x - from_bits<false>(hb));
                 }
@@ -605,7 +616,8 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
     uint16_t *b_hi = reinterpret_cast<uint16_t *>(wave_base + size_t(wave) * t_bytes);
     uint16_t *b_lo = b_hi + size_t(wave) * b_elems;
     int *b_exp = reinterpret_cast<int *>(b_lo + size_t(wave) * b_elems);
-    const size_t smem = size_t(SPLIT == 3 ? 2 : 1) * (size_t(kTileM) + kTileN) * K * 2;
+    constexpr int TN = tile_n<SPLIT>();
+    const size_t smem = size_t(SPLIT == 3 ? 2 : 1) * (size_t(kTileM) + TN) * K * 2;
     // both passes on the tensor cores when the compact support fits (BF16)
     const int Kc = (2 * a.kmax + 1 + 7) / 8 * 8, K1 = 2 * Kc;
     const size_t smem1 = size_t(SPLIT == 3 ? 2 : 1) * (128 + kTile1N) * size_t(K1) * 2;
@@ -645,7 +657,7 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
             BLINK_CUDA_TRY(cudaGetLastError());
             DftArgs d{a_hi, a_lo, t_hi, t_lo, nullptr, a.layers, a.chans, static_cast<float *>(a.out), a.flags, N, K,
                       a.status, a.ref, wns};
-            k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / kTileN), unsigned(cnt)), 128, smem, st>>>(
+            k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / TN), unsigned(cnt)), 128, smem, st>>>(
                 d, l0, d.out, d.ref);
             BLINK_CUDA_TRY(cudaGetLastError());
         }
@@ -661,11 +673,11 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
         ra.scratch_bytes = size_t(wave) * t_bytes;
         Error e = launch_rows_wave(N, ra, l0, cnt, st);
         if (e.status) return e;
-        k_split<FP16><<<cnt, 256, 0, st>>>(T, a.r_alloc, N, Rp, a.layers, a.chans, l0, b_hi, b_lo, b_exp);
+        k_split<FP16, SPLIT><<<cnt, 256, 0, st>>>(T, a.r_alloc, N, Rp, a.layers, a.chans, l0, b_hi, b_lo, b_exp);
         BLINK_CUDA_TRY(cudaGetLastError());
         DftArgs d{a_hi, a_lo, b_hi, b_lo, b_exp, a.layers, a.chans, static_cast<float *>(a.out), a.flags, N, K, a.status,
                   a.ref, a.wait_ns < 0 ? kWaitNs : static_cast<unsigned long long>(a.wait_ns)};
-        k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / kTileN), unsigned(cnt)), 128, smem, st>>>(
+        k_dftgemm<FP16, SPLIT><<<dim3(unsigned(N / kTileM), unsigned(N / TN), unsigned(cnt)), 128, smem, st>>>(
             d, l0, d.out, d.ref);
         BLINK_CUDA_TRY(cudaGetLastError());
     }
@@ -676,7 +688,8 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
 
 bool dftgemm_supported(int n_px, int r_alloc, int mode) {
     const int Rp = (r_alloc + 7) / 8 * 8;
-    const size_t smem = size_t(mode == 2 || mode == 4 ? 2 : 1) * (size_t(kTileM) + kTileN) * 2 * Rp * 2;
+    const bool split = mode == 2 || mode == 4;
+    const size_t smem = size_t(split ? 2 : 1) * (size_t(kTileM) + (split ? tile_n<3>() : tile_n<1>())) * 2 * Rp * 2;
     return n_px >= kTileN && n_px % kTileN == 0 && image_size_supported(n_px) && 2 * Rp <= 256 &&
            smem <= 227 * 1024;
 }
@@ -696,7 +709,8 @@ Error launch_dftgemm_group(int n_px, int mode, const ImageArgs &a, cudaStream_t 
     if (a.n_layers == 0) return Error{0, ""};
     if (!dftgemm_supported(n_px, a.r_alloc, mode)) return Error{-2, "tensor-core transform: unsupported size or support"};
     const int Rp = (a.r_alloc + 7) / 8 * 8;
-    const size_t smem = size_t(mode == 2 || mode == 4 ? 2 : 1) * (size_t(kTileM) + kTileN) * 2 * Rp * 2;
+    const bool split = mode == 2 || mode == 4;
+    const size_t smem = size_t(split ? 2 : 1) * (size_t(kTileM) + (split ? tile_n<3>() : tile_n<1>())) * 2 * Rp * 2;
     if (2 * Rp > 256 || smem > 227 * 1024)
         return Error{-2, "tensor-core transform: too many support rows for shared memory"};
     switch (mode) {

@@ -6,7 +6,8 @@
 // visibilities M).  With gamma = dL/dRe V + i dL/dIm V from blink_degrid,
 //   gamma(g_i) = sum_{j>i} gamma(V_ij) g_j conj(M_ij)
 //              + sum_{k<i} conj(gamma(V_ki)) g_k M_ki,
-// summed over all layers.
+// summed over all layers.  Every sum runs in a fixed order (FP64), so the
+// gradient is the same bits from run to run.
 #include "blink_common.cuh"
 #include "blink_kernels.cuh"
 #include "blink_pairs.cuh"
@@ -44,47 +45,105 @@ __global__ void k_gain_products(const float2 *__restrict__ gains, int64_t stride
     out[int64_t(blockIdx.y) * nb + b] = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
 }
 
-// One CTA per antenna; FP64 accumulation, fixed-order block reduction.
-__global__ void __launch_bounds__(256) k_gain_grad(const float2 *__restrict__ dvis, const float2 *__restrict__ model,
-                                                   const float2 *__restrict__ gains,
-                                                   const int64_t *__restrict__ vis_off, int n_layers, int n_ant,
-                                                   float2 *__restrict__ dgains) {
-    const int i = blockIdx.x;
-    double re = 0.0, im = 0.0;
-    const int64_t terms = int64_t(n_layers) * n_ant;
-    for (int64_t t = threadIdx.x; t < terms; t += blockDim.x) {
-        const int l = int(t / n_ant), j = int(t % n_ant);
-        if (j == i) continue;
+// Gain gradient, pass 1.  CTA (t, g) takes the antenna rows i of tile t
+// (kGradTile rows) and the layers of group g; thread j walks the baselines
+// (i, j), j > i, of every such row -- contiguous in the upper-triangle order,
+// so every load is coalesced -- and adds
+//   to row i's partial:     gamma(V_ij) g_j conj(M_ij)        (kept per thread,
+//                                                              reduced at the end)
+//   to column j's partial:  conj(gamma(V_ij)) g_i M_ij.
+// Products in FP32, sums in FP64, all in a fixed order.  Partials:
+// pcol[g][t][j] and prow[g][i].
+constexpr int kGradTile = 16;
+constexpr int kGradThreads = 256;
+constexpr int kGradMaxJ = 4;  // antennas per thread: n_ant <= 1024
+
+__global__ void __launch_bounds__(kGradThreads) k_gain_grad_part(const float2 *__restrict__ dvis,
+                                                                 const float2 *__restrict__ model,
+                                                                 const float2 *__restrict__ gains,
+                                                                 const int64_t *__restrict__ vis_off, int n_layers,
+                                                                 int n_ant, int layers_per_group,
+                                                                 double2 *__restrict__ pcol,
+                                                                 double2 *__restrict__ prow) {
+    const int t = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
+    const int i0 = t * kGradTile;
+    const int l0 = g * layers_per_group, l1 = min(n_layers, l0 + layers_per_group);
+    double2 racc[kGradTile];
+    double2 cacc[kGradMaxJ];
+#pragma unroll
+    for (int k = 0; k < kGradTile; ++k) racc[k] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < kGradMaxJ; ++q) cacc[q] = make_double2(0.0, 0.0);
+    float2 gjv[kGradMaxJ];
+#pragma unroll
+    for (int q = 0; q < kGradMaxJ; ++q) {
+        const int j = tid + q * kGradThreads;
+        gjv[q] = j < n_ant ? gains[j] : make_float2(0.f, 0.f);
+    }
+    for (int l = l0; l < l1; ++l) {
         const int64_t o = vis_off[l];
-        const float2 gj = gains[j];
-        if (j > i) {
-            const int64_t b = o + baseline_index(i, j, n_ant);
-            const float2 gv = dvis[b], m = model[b];
-            const double tr = double(gj.x) * m.x + double(gj.y) * m.y;  // g_j conj(M)
-            const double ti = double(gj.y) * m.x - double(gj.x) * m.y;
-            re += gv.x * tr - gv.y * ti;
-            im += gv.x * ti + gv.y * tr;
-        } else {
-            const int64_t b = o + baseline_index(j, i, n_ant);
-            const float2 gv = dvis[b], m = model[b];
-            const double ur = double(gj.x) * m.x - double(gj.y) * m.y;  // g_j M
-            const double ui = double(gj.x) * m.y + double(gj.y) * m.x;
-            re += gv.x * ur + gv.y * ui;  // conj(gamma) (g_j M)
-            im += gv.x * ui - gv.y * ur;
+#pragma unroll
+        for (int k = 0; k < kGradTile; ++k) {
+            const int i = i0 + k;
+            if (i >= n_ant - 1) break;
+            const float2 gi = gains[i];
+            const int64_t rs = o + pair_row_start(i, n_ant) - i - 1;  // baseline (i, j) at rs + j
+#pragma unroll
+            for (int q = 0; q < kGradMaxJ; ++q) {
+                const int j = tid + q * kGradThreads;
+                if (j <= i || j >= n_ant) continue;
+                const float2 gv = dvis[rs + j], m = model[rs + j], gj = gjv[q];
+                const float tr = gj.x * m.x + gj.y * m.y, ti = gj.y * m.x - gj.x * m.y;  // g_j conj(M)
+                racc[k].x += double(gv.x * tr - gv.y * ti);
+                racc[k].y += double(gv.x * ti + gv.y * tr);
+                const float ur = gi.x * m.x - gi.y * m.y, ui = gi.x * m.y + gi.y * m.x;  // g_i M
+                cacc[q].x += double(gv.x * ur + gv.y * ui);                            // conj(gamma) g_i M
+                cacc[q].y += double(gv.x * ui - gv.y * ur);
+            }
         }
     }
-    __shared__ double sr[256], si[256];
-    sr[threadIdx.x] = re;
-    si[threadIdx.x] = im;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (int(threadIdx.x) < s) {
-            sr[threadIdx.x] += sr[threadIdx.x + s];
-            si[threadIdx.x] += si[threadIdx.x + s];
+    double2 *pc = pcol + (int64_t(g) * gridDim.x + t) * n_ant;
+#pragma unroll
+    for (int q = 0; q < kGradMaxJ; ++q) {
+        const int j = tid + q * kGradThreads;
+        if (j < n_ant) pc[j] = cacc[q];
+    }
+    // row partials: a fixed-order tree over the threads, one row at a time
+    __shared__ double2 red[kGradThreads];
+    for (int k = 0; k < kGradTile; ++k) {
+        const int i = i0 + k;
+        if (i >= n_ant) break;  // CTA-uniform
+        red[tid] = racc[k];
+        __syncthreads();
+        for (int s2 = kGradThreads / 2; s2 > 0; s2 >>= 1) {
+            if (tid < s2) {
+                red[tid].x += red[tid + s2].x;
+                red[tid].y += red[tid + s2].y;
+            }
+            __syncthreads();
         }
+        if (tid == 0) prow[int64_t(g) * n_ant + i] = red[0];
         __syncthreads();
     }
-    if (threadIdx.x == 0) dgains[i] = make_float2(float(sr[0]), float(si[0]));
+}
+
+// Gain gradient, pass 2: per antenna, the partials in a fixed order.
+__global__ void k_gain_grad_sum(const double2 *__restrict__ pcol, const double2 *__restrict__ prow, int groups,
+                                int tiles, int n_ant, float2 *__restrict__ dgains) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_ant) return;
+    double re = 0.0, im = 0.0;
+    for (int g = 0; g < groups; ++g) {
+        const double2 r = prow[int64_t(g) * n_ant + a];
+        re += r.x;
+        im += r.y;
+        for (int t = 0; t < tiles; ++t) {
+            const double2 c = pcol[(int64_t(g) * tiles + t) * n_ant + a];
+            re += c.x;
+            im += c.y;
+        }
+    }
+    dgains[a] = make_float2(float(re), float(im));
 }
 
 }  // namespace
@@ -112,9 +171,29 @@ Error launch_apply_gains(const float2 *model, const float2 *gains, const int64_t
     return Error{0, ""};
 }
 
+// Layer groups of the gain gradient: about four CTAs per SM over all tiles.
+int gain_grad_groups(int n_layers, int n_ant) {
+    const int tiles = (n_ant + kGradTile - 1) / kGradTile;
+    const int want = std::max(1, (4 * 152 + tiles - 1) / tiles);
+    return std::max(1, std::min(n_layers, want));
+}
+
+size_t gain_grad_scratch_bytes(int n_layers, int n_ant) {
+    const int tiles = (n_ant + kGradTile - 1) / kGradTile, groups = gain_grad_groups(n_layers, n_ant);
+    return size_t(groups) * (size_t(tiles) + 1) * size_t(n_ant) * sizeof(double2);
+}
+
 Error launch_gain_grad(const float2 *dvis, const float2 *model, const float2 *gains, const int64_t *vis_off,
-                       int n_layers, int n_ant, float2 *dgains, cudaStream_t st) {
-    k_gain_grad<<<n_ant, 256, 0, st>>>(dvis, model, gains, vis_off, n_layers, n_ant, dgains);
+                       int n_layers, int n_ant, float2 *dgains, void *scratch, cudaStream_t st) {
+    if (n_ant > kGradMaxJ * kGradThreads) return Error{-2, "gain gradient: more than 1024 antennas"};
+    const int tiles = (n_ant + kGradTile - 1) / kGradTile, groups = gain_grad_groups(n_layers, n_ant);
+    const int per = (n_layers + groups - 1) / groups;
+    double2 *pcol = static_cast<double2 *>(scratch);
+    double2 *prow = pcol + size_t(groups) * tiles * n_ant;
+    k_gain_grad_part<<<dim3(unsigned(tiles), unsigned(groups)), kGradThreads, 0, st>>>(
+        dvis, model, gains, vis_off, n_layers, n_ant, per, pcol, prow);
+    BLINK_CUDA_TRY(cudaGetLastError());
+    k_gain_grad_sum<<<(n_ant + 255) / 256, 256, 0, st>>>(pcol, prow, groups, tiles, n_ant, dgains);
     BLINK_CUDA_TRY(cudaGetLastError());
     return Error{0, ""};
 }

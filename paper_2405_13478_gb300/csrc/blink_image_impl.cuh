@@ -27,6 +27,7 @@
 #include "blink_kernels.cuh"
 #include "blink_pairs.cuh"
 #include "blink_image_small.cuh"
+#include "blink_grid_sorted.cuh"
 #include "blink_sync.cuh"
 
 #include <algorithm>
@@ -295,144 +296,6 @@ struct RowsCfg {
     static constexpr size_t smem = (size_t(tw) + N) * sizeof(float2);
 };
 
-// Segmented-sum operator on (partial sum, "a run starts here") pairs:
-// (a, fa) + (b, fb) = (fb ? b : a + b, fa | fb).  Associative, so a scan with a
-// fixed tree of these gives every run's sum in an order set by the chunk
-// layout alone.
-struct SegSum {
-    float2 v;
-    bool head;
-};
-__device__ __forceinline__ SegSum seg_add(const SegSum &a, const SegSum &b) {
-    return SegSum{b.head ? b.v : make_float2(a.v.x + b.v.x, a.v.y + b.v.y), a.head || b.head};
-}
-
-// Deterministic, atomic-free gridding of the canonical rows [r0, r0 + nrows)
-// of one layer from its sorted row buckets (the entries of a cell are
-// contiguous).  Per chunk of 256 x kRowGridU entries, thread t takes entries
-// [kRowGridU t, kRowGridU (t+1)): it loads their baselines and cells and the
-// visibilities (gains applied, conjugated for mirrored baselines), and a
-// block-wide segmented scan (in-thread, warp shuffles, then across warps)
-// gives each run of equal cells its sum at its last entry, which adds it to
-// the cell.  Each cell has one writer per chunk and chunks follow one
-// another, so the image never depends on timing.
-//
-// Latency: the first chunk's loads are issued before `prologue` (which
-// zeroes the band and starts the twiddle copy) and the barrier after it, and
-// every later chunk's baselines and cells are loaded while the chunk before
-// it is summed.
-constexpr int kRowGridU = 8;
-struct GridChunk {
-    uint32_t key[kRowGridU], bl[kRowGridU];
-    uint32_t conj;          // bit u: entry u is a mirrored baseline
-    uint32_t kprev, knext;  // cell keys of the entries just before and after this thread's
-    int n;                  // entries in the chunk (<= 0: none)
-};
-
-__device__ __forceinline__ void grid_load_codes(GridChunk &c, const uint2 *__restrict__ ents, int c0, int n, int r0,
-                                                int tid) {
-    constexpr int U = kRowGridU;
-    constexpr uint32_t kPastEnd = 0xFFFFFFFFu, kBeforeStart = 0xFFFFFFFEu;  // never a cell key
-    auto key_of = [r0](uint32_t code) { return ((code_row(code) - uint32_t(r0)) << 16) | code_col(code); };
-    const int i0 = tid * U;
-    c.n = n;
-    c.conj = 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const bool live = i0 + u < n;
-        const uint2 en = live ? __ldg(ents + c0 + i0 + u) : make_uint2(0u, 0u);
-        c.bl[u] = en.x;
-        c.key[u] = live ? key_of(en.y) : kPastEnd;
-        c.conj |= (live && code_conj(en.y)) ? (1u << u) : 0u;
-    }
-    c.kprev = (i0 > 0 && i0 <= n) ? key_of(__ldg(ents + c0 + i0 - 1).y) : kBeforeStart;
-    c.knext = i0 + U < n ? key_of(__ldg(ents + c0 + i0 + U).y) : kPastEnd;
-}
-
-__device__ __forceinline__ void grid_load_vis(const GridChunk &c, float2 (&v)[kRowGridU],
-                                              const float2 *__restrict__ vis, const LayerGains &gl, int tid) {
-    const int i0 = tid * kRowGridU;
-#pragma unroll
-    for (int u = 0; u < kRowGridU; ++u) v[u] = i0 + u < c.n ? __ldg(vis + c.bl[u]) : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int u = 0; u < kRowGridU; ++u) {
-        if (i0 + u < c.n) {
-            if (gl) v[u] = apply_gain(v[u], gl, c.bl[u]);
-            if ((c.conj >> u) & 1u) v[u].y = -v[u].y;
-        }
-    }
-}
-
-// Segmented scan of one chunk and its cell updates (two barriers).
-template <int N>
-__device__ __forceinline__ void grid_sum_chunk(float2 *G, const GridChunk &c, const float2 (&v)[kRowGridU],
-                                               int tid) {
-    constexpr int U = kRowGridU, S = RowsCfg<N>::S, NW = RowsCfg<N>::NT / 32;
-    __shared__ float2 s_wv[NW];
-    __shared__ int s_wh[NW];
-    const int lane = tid & 31, warp = tid >> 5, i0 = tid * U;
-    const unsigned full = 0xFFFFFFFFu;
-    SegSum agg{v[0], c.key[0] != c.kprev};
-#pragma unroll
-    for (int u = 1; u < U; ++u) agg = seg_add(agg, SegSum{v[u], c.key[u] != c.key[u - 1]});
-    SegSum inc = agg;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        SegSum up;
-        up.v.x = __shfl_up_sync(full, inc.v.x, d);
-        up.v.y = __shfl_up_sync(full, inc.v.y, d);
-        up.head = __shfl_up_sync(full, int(inc.head), d) != 0;
-        if (lane >= d) inc = seg_add(up, inc);
-    }
-    if (lane == 31) {
-        s_wv[warp] = inc.v;
-        s_wh[warp] = int(inc.head);
-    }
-    SegSum ex;  // everything before this thread's entries, inside the warp
-    ex.v.x = __shfl_up_sync(full, inc.v.x, 1);
-    ex.v.y = __shfl_up_sync(full, inc.v.y, 1);
-    ex.head = __shfl_up_sync(full, int(inc.head), 1) != 0;
-    __syncthreads();
-    SegSum pre{make_float2(0.f, 0.f), false};
-    for (int w = 0; w < warp; ++w) pre = seg_add(pre, SegSum{s_wv[w], s_wh[w] != 0});
-    SegSum run = lane == 0 ? pre : seg_add(pre, ex);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        run = seg_add(run, SegSum{v[u], c.key[u] != (u == 0 ? c.kprev : c.key[u - 1])});
-        const bool last = u + 1 < U ? c.key[u + 1] != c.key[u] : c.knext != c.key[u];
-        if (i0 + u < c.n && last) {
-            float2 *cell = G + int(c.key[u] >> 16) * S + RowLayout<N>::phys(int(c.key[u] & 0xFFFFu));
-            cell->x += run.v.x;
-            cell->y += run.v.y;
-        }
-    }
-    __syncthreads();  // cells and warp sums are reused by the next chunk
-}
-
-template <int N, class Prologue>
-__device__ __forceinline__ void grid_band_sorted(float2 *G, int r0, int nrows, const int32_t *__restrict__ ptr,
-                                                 const uint2 *__restrict__ ents, const float2 *__restrict__ vis,
-                                                 const LayerGains &gl, int tid, Prologue &&prologue) {
-    constexpr int CH = RowsCfg<N>::NT * kRowGridU;
-    const int e_begin = __ldg(ptr + r0), e_end = __ldg(ptr + r0 + nrows);
-    GridChunk cur;
-    float2 v[kRowGridU];
-    int c0 = e_begin;
-    grid_load_codes(cur, ents, c0, min(CH, e_end - c0), r0, tid);
-    grid_load_vis(cur, v, vis, gl, tid);
-    prologue();
-    __syncthreads();
-    while (cur.n > 0) {
-        GridChunk nxt;
-        const int c1 = c0 + CH;
-        grid_load_codes(nxt, ents, c1, min(CH, e_end - c1), r0, tid);
-        grid_sum_chunk<N>(G, cur, v, tid);
-        cur = nxt;
-        c0 = c1;
-        if (cur.n > 0) grid_load_vis(cur, v, vis, gl, tid);
-    }
-}
-
 // Pass 1 for the band of canonical rows [r0, r0 + RB) of one layer (r0 below
 // the channel's support R): gridding, weights, Hermitian completion of row 0,
 // the row transforms, written in natural column order to dst[r - r0][p].
@@ -450,9 +313,10 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
     const LayerGains gl = layer_gains(a, L);
     if (a.csr && ci.csr_off >= 0) {
         const CsrLayout cl(N, a.nb);
-        grid_band_sorted<N>(sm, r0, nrows, reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr),
-                            reinterpret_cast<const uint2 *>(a.csr + ci.csr_off + cl.ents), a.vis + L.vis_off, gl,
-                            tid, prologue);
+        auto cell = [sm](uint32_t key) { return sm + int(key >> 16) * S + RowLayout<N>::phys(int(key & 0xFFFFu)); };
+        grid_band_sorted<NT>(r0, nrows, reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr),
+                             reinterpret_cast<const uint2 *>(a.csr + ci.csr_off + cl.ents), a.vis + L.vis_off, gl,
+                             tid, cell, prologue);
     } else {
         // a channel without row buckets (its support always fits the fused
         // kernel; it comes here only when the two-kernel path is forced):
@@ -608,6 +472,7 @@ struct LargeSched {
     int nR, nC;     // row and column items per layer
     int lag;        // stages between a layer's row and column items
     int slots;      // scratch ring slots (layers)
+    int ahead;      // layers between a layer and the one whose inputs it prefetches
     int64_t total;  // n (nR + nC)
     unsigned long long wait_ns;
 };
@@ -707,8 +572,22 @@ __global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
             float2 *Hs = a.scratch + int64_t(layer % q.slots) * a.r_alloc * N;
             if (is_row) {
                 // the first row item of a layer pulls the layer's visibilities
-                // into L2 for the band gathers of all its row items
-                if (sub == 0) prefetch_l2(reinterpret_cast<const float *>(a.vis + L.vis_off), 2 * a.nb, tid, 256);
+                // into L2 for the band gathers of all its row items, and the
+                // row buckets of the layer about one grid of items ahead (with
+                // many channels the buckets do not stay in L2 between a
+                // channel's time steps)
+                if (sub == 0) {
+                    prefetch_l2_bytes(a.vis + L.vis_off, 8 * a.nb, tid, 256);
+                    const int la = layer + q.ahead;
+                    if (a.csr && la < q.n) {
+                        const ChanInfo cp = a.chans[a.layers[la].chan];
+                        if (cp.csr_off >= 0) {
+                            const CsrLayout cl(N, a.nb);
+                            prefetch_l2_bytes(a.csr + cp.csr_off + cl.row_ptr, 4 * int64_t(cl.n_bkt + 1), tid, 256);
+                            prefetch_l2_bytes(a.csr + cp.csr_off + cl.ents, 8 * a.nb, tid, 256);
+                        }
+                    }
+                }
                 const int r0 = sub * RowsCfg<N>::RB;
                 if (r0 < ci.rows) rows_item<N>(a, L, ci, r0, Hs + int64_t(r0) * N, sm, tid);
                 __syncthreads();  // every thread's scratch stores precede the release below
@@ -954,6 +833,7 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     // gaps wide (and lag <= slots - 1).
     const int lag_want = int(4 * grid / int64_t(q.nR + q.nC)) + 1;
     q.lag = std::max(0, std::min({lag_want, q.slots / 2, q.n}));
+    q.ahead = int(std::min<int64_t>(64, std::max<int64_t>(1, grid / int64_t(q.nR + q.nC))));
     BLINK_CUDA_TRY(cudaMemsetAsync(a.queue, 0, image_queue_bytes(q.n), st));
     kern<<<unsigned(grid), 256, smem, st>>>(a, q, static_cast<float *>(a.out), a.ref);
     BLINK_CUDA_TRY(cudaGetLastError());

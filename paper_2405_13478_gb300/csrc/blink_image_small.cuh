@@ -297,6 +297,18 @@ __device__ __forceinline__ void prefetch_l2(const float *p, int64_t n_floats, in
     }
 }
 
+// L2 prefetch of [p, p + bytes) with the default eviction priority (the
+// 16-byte aligned interior; a hint, never a fault outside the range).
+__device__ __forceinline__ void prefetch_l2_bytes(const void *p, int64_t bytes, int tid, int nt) {
+    const uintptr_t a0 = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+    const uintptr_t a1 = (reinterpret_cast<uintptr_t>(p) + uintptr_t(bytes)) & ~uintptr_t(15);
+    constexpr uintptr_t kPiece = 16384;
+    for (uintptr_t s0 = a0 + uintptr_t(tid) * kPiece; s0 < a1; s0 += uintptr_t(nt) * kPiece) {
+        const uint32_t n = uint32_t(a1 - s0 < kPiece ? a1 - s0 : kPiece);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s0), "r"(n) : "memory");
+    }
+}
+
 // Fused layer with shared-memory float atomics for the gridding (used when a
 // channel has no register-accumulation schedule).
 template <int N, bool EPI>

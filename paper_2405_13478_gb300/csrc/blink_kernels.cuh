@@ -113,7 +113,9 @@ Error launch_gain_products(const float2 *gains, int64_t stride, int rows, int n_
                            cudaStream_t st);
 Error launch_apply_gains(const float2 *model, const float2 *gains, const int64_t *vis_off, int n_layers, int n_ant,
                          int64_t nb, float2 *vis, cudaStream_t st);
+// Device scratch of launch_gain_grad (per-tile and per-row FP64 partials).
+size_t gain_grad_scratch_bytes(int n_layers, int n_ant);
 Error launch_gain_grad(const float2 *dvis, const float2 *model, const float2 *gains, const int64_t *vis_off,
-                       int n_layers, int n_ant, float2 *dgains, cudaStream_t st);
+                       int n_layers, int n_ant, float2 *dgains, void *scratch, cudaStream_t st);
 
 }  // namespace blink

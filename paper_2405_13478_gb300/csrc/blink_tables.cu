@@ -96,14 +96,14 @@ __global__ void k_cells(const double *__restrict__ ant_xyz, int n_ant, int64_t n
         s_kept[warp] = wkept;
     }
     __syncthreads();
-    if (want_csr) {  // this block's bucket sizes, and the totals one slot up for the scan
+    if (want_csr) {  // this block's bucket sizes (bucket-major) and the bucket totals
         const CsrLayout cl(n, nb);
-        int32_t *tot = reinterpret_cast<int32_t *>(csr + ci0.csr_off + cl.row_ptr);
-        int32_t *blk = reinterpret_cast<int32_t *>(csr + ci0.csr_off + cl.blk_off) + int64_t(blockIdx.x) * cl.n_bkt;
+        int32_t *tot = reinterpret_cast<int32_t *>(csr + ci0.csr_off + cl.tot);
+        int32_t *blk = reinterpret_cast<int32_t *>(csr + ci0.csr_off + cl.blk_off);
         for (int r = threadIdx.x; r < cl.n_bkt; r += blockDim.x) {
             const int32_t c = s_hist[r];
-            blk[r] = c;
-            if (c) atomicAdd(tot + 1 + r, c);
+            blk[int64_t(r) * cl.n_blk + blockIdx.x] = c;
+            if (c) atomicAdd(tot + r, c);
         }
     }
     if (threadIdx.x == 0) {
@@ -542,27 +542,40 @@ __global__ void k_sched_sort(const ChanInfo *__restrict__ info, unsigned char *_
     }
 }
 
-// Row buckets, step 2 (one CTA per channel): exclusive scan of the bucket
-// totals into row_ptr, then per bucket the running start of every baseline
-// block (blk_off[blk][r] becomes the position of block blk's first entry of
-// bucket r).
-__global__ void k_csr_scan(const ChanInfo *__restrict__ info, unsigned char *__restrict__ csr, int64_t nb) {
-    const ChanInfo ci = info[blockIdx.x];
+// Row buckets, step 2: one warp per bucket.  The bucket's start is the sum of
+// the totals of the buckets before it (row_ptr[r]; the last bucket's warp also
+// writes row_ptr[n_bkt]); then an exclusive scan over the baseline blocks
+// turns blk_off[r][blk] into the position of block blk's first entry of the
+// bucket.  Grid: (ceil(buckets / 8), channels) x 256.
+__global__ void __launch_bounds__(256) k_csr_scan(const ChanInfo *__restrict__ info, unsigned char *__restrict__ csr,
+                                                  int64_t nb) {
+    const ChanInfo ci = info[blockIdx.y];
     if (ci.csr_off < 0) return;
     const CsrLayout cl(ci.n_px, nb);
+    const int lane = threadIdx.x & 31, r = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= cl.n_bkt) return;
+    const unsigned full = 0xFFFFFFFFu;
     int32_t *ptr = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.row_ptr);
-    int32_t *off = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.blk_off);
-    if (threadIdx.x == 0) {
-        for (int r = 1; r <= cl.n_bkt; ++r) ptr[r] += ptr[r - 1];
+    const int32_t *tot = reinterpret_cast<const int32_t *>(csr + ci.csr_off + cl.tot);
+    int32_t *off = reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.blk_off) + int64_t(r) * cl.n_blk;
+    int32_t before = 0;
+    for (int k = lane; k < r; k += 32) before += tot[k];
+    before = __reduce_add_sync(full, before);
+    if (lane == 0) {
+        ptr[r] = before;
+        if (r == cl.n_bkt - 1) ptr[r + 1] = before + tot[r];
     }
-    __syncthreads();
-    for (int r = threadIdx.x; r < cl.n_bkt; r += blockDim.x) {
-        int32_t run = ptr[r];
-        for (int blk = 0; blk < cl.n_blk; ++blk) {
-            const int32_t t = off[int64_t(blk) * cl.n_bkt + r];
-            off[int64_t(blk) * cl.n_bkt + r] = run;
-            run += t;
+    int32_t run = before;
+    for (int b0 = 0; b0 < cl.n_blk; b0 += 32) {
+        const int b = b0 + lane;
+        const int32_t c = b < cl.n_blk ? off[b] : 0;
+        int32_t inc = c;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t t = __shfl_up_sync(full, inc, d);
+            if (lane >= d) inc += t;
         }
+        if (b < cl.n_blk) off[b] = run + inc - c;
+        run += __shfl_sync(full, inc, 31);
     }
 }
 
@@ -595,13 +608,14 @@ __global__ void __launch_bounds__(kCsrBlock) k_csr_fill(const ChanInfo *__restri
     for (int w = 0; w < warp; ++w) rank += wcnt[w][bucket];
     const int32_t *off = reinterpret_cast<const int32_t *>(csr + ci.csr_off + cl.blk_off);
     uint2 *ents = reinterpret_cast<uint2 *>(csr + ci.csr_off + cl.ents_by_b);
-    ents[off[int64_t(blockIdx.x) * cl.n_bkt + bucket] + rank] = make_uint2(uint32_t(b), code);
+    ents[off[int64_t(bucket) * cl.n_blk + blockIdx.x] + rank] = make_uint2(uint32_t(b), code);
 }
 
-// Row buckets, step 4: inside every bucket, a stable counting sort of the
-// baseline-ordered entries by column (one warp per bucket, 32 entries per
-// step; the dropped bucket is copied as it is).  Grid: (ceil(buckets / 8),
-// channels) x 256.
+// Row buckets, step 4: inside every bucket, order the baseline-ordered
+// entries by (column, baseline): up to 32 entries by a bitonic sort across the
+// warp's lanes, more by a stable counting sort by column (32 entries per
+// step); the dropped bucket is copied as it is.  One warp per bucket.
+// Grid: (ceil(buckets / 8), channels) x 256.
 __global__ void __launch_bounds__(256) k_csr_sort(const ChanInfo *__restrict__ info,
                                                   unsigned char *__restrict__ csr, int64_t nb) {
     constexpr int W = 8;
@@ -618,6 +632,27 @@ __global__ void __launch_bounds__(256) k_csr_sort(const ChanInfo *__restrict__ i
     const int p0 = ptr[bk], p1 = ptr[bk + 1];
     if (bk == cl.n_bkt - 1) {  // dropped baselines: baseline order
         for (int e = p0 + lane; e < p1; e += 32) dst[e] = src[e];
+        return;
+    }
+    if (p1 - p0 <= 32) {
+        const unsigned full = 0xFFFFFFFFu;
+        const bool live = p0 + lane < p1;
+        uint2 en = live ? src[p0 + lane] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+        uint32_t kc = live ? code_col(en.y) : 0xFFFFFFFFu;  // key: (column, baseline)
+        for (int k = 2; k <= 32; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const uint32_t okc = __shfl_xor_sync(full, kc, j);
+                const uint32_t ob = __shfl_xor_sync(full, en.x, j);
+                const uint32_t oc = __shfl_xor_sync(full, en.y, j);
+                const bool other_less = okc < kc || (okc == kc && ob < en.x);
+                const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
+                if (keep_min == other_less) {
+                    kc = okc;
+                    en = make_uint2(ob, oc);
+                }
+            }
+        }
+        if (live) dst[p0 + lane] = en;
         return;
     }
     const int n = ci.n_px;
@@ -709,7 +744,7 @@ Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, co
         BLINK_CUDA_TRY(cudaGetLastError());
     }
     if (csr) {
-        k_csr_scan<<<n_chan, 256, 0, st>>>(info, csr, nb);
+        k_csr_scan<<<dim3(unsigned((kCsrMaxBuckets + 7) / 8), unsigned(n_chan)), 256, 0, st>>>(info, csr, nb);
         BLINK_CUDA_TRY(cudaGetLastError());
         k_csr_fill<<<dim3(unsigned((nb + kCsrBlock - 1) / kCsrBlock), unsigned(n_chan)), kCsrBlock, 0, st>>>(
             info, codes, csr, nb);

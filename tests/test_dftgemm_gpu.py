@@ -126,3 +126,20 @@ def test_wide_support_falls_back_to_the_fft_row_pass(env):
     vis = ws.vis("cpu", times=[0])[0, [0, 15], :].contiguous().reshape(-1)
     worst = _run_modes(torch, binding, ctx, ws.ant_xyz, layers, vis, (0x10, 0x20))
     assert worst[0x10] <= BOUNDS[0x10] and worst[0x20] <= BOUNDS[0x20], worst
+
+
+@pytest.mark.parametrize("mode", sorted(BOUNDS))
+def test_transform_modes_are_bit_reproducible(env, mode):
+    # every mode grids from the sorted row buckets without atomics and sums
+    # in fixed orders: two calls give the same bits
+    torch, binding, ctx, ws, layers, total, vis, want = env
+    plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
+    d_vis = vis.reshape(-1).cuda()
+    a = torch.empty(total, device="cuda")
+    b = torch.empty(total, device="cuda")
+    plan.image(d_vis, a, None, mode)
+    plan.image(d_vis, b, None, mode)
+    plan.check()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    plan.close()
