@@ -309,18 +309,25 @@ BLINK_API int blink_probe_fma_peak(int device, int bits, double *tflops);
  *
  * Same result as blink_image_batch (steps 1-5 on every layer), but it allocates
  * nothing: no cudaMalloc, no cudaFree, no memory pool, no context.  All of
- * its scratch -- channel tables, layer descriptors and the row-transform
- * buffer of large images -- lives in one static device array of
+ * its scratch -- channel tables, layer descriptors, the gridding schedule of
+ * sizes up to 256, the row buckets of large sizes, the work queue and the
+ * row-transform ring of large images -- lives in one static device array of
  * BLINK_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
- * until the process exits.
+ * until the process exits.  When all of that fits, the call runs the kernels
+ * blink_image_batch runs and gives the same bits; a schedule or bucket set
+ * that does not fit is left out for that call, and its images then come from
+ * the shared-atomic gridding fallback (equal within FP32 rounding, not bit
+ * for bit).  A 256-antenna station with 32 channels of 180^2 takes about
+ * 31 MB of tables.
  *
  * Limits: all layers of a call share one n_px; at most
  * BLINK_NOALLOC_MAX_CHANNELS distinct (freq_hz, delta_u, weighting) channels;
  * the tables (4 bytes per baseline per channel, plus N*N/2 floats per
- * uniform-weighted channel, plus 56 bytes per layer) and one layer's
- * row-transform buffer (large images only) must fit in the static array.
- * A request beyond a limit returns BLINK_ERR_WORKSPACE (or BLINK_ERR_INVALID
- * for mixed sizes) before any launch, with a message in err_msg.
+ * uniform-weighted or scheduled channel, plus 56 bytes per layer) and one
+ * layer's row-transform buffer (large images only) must fit in the static
+ * array.  A request beyond a limit returns BLINK_ERR_WORKSPACE (or
+ * BLINK_ERR_INVALID for mixed sizes) before any launch, with a message in
+ * err_msg.
  *
  * Runs on the calling thread's current device and on `stream`, which it
  * synchronises once (like blink_image_batch).  The first call on each device

@@ -93,6 +93,7 @@ struct blink_plan {
     size_t scratch_bytes = 0;
     unsigned char *d_sched = nullptr;
     unsigned char *d_csr = nullptr;  // row buckets per channel
+    size_t csr_bytes = 0;
     float2 *d_dscratch = nullptr;  // adjoint column-transform scratch (allocated on first use)
     size_t dscratch_bytes = 0;
     float2 *d_gscratch = nullptr;  // tensor-core transform scratch (allocated on first use)
@@ -201,6 +202,7 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     if (p->d_sched) cudaFreeAsync(p->d_sched, st);
     if (p->d_csr) cudaFreeAsync(p->d_csr, st);
     p->d_csr = nullptr;
+    p->csr_bytes = 0;
     if (p->d_dscratch) cudaFreeAsync(p->d_dscratch, st);
     if (p->d_gscratch) cudaFreeAsync(p->d_gscratch, st);
     p->d_gscratch = nullptr;
@@ -384,6 +386,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         if (e != cudaSuccess)
             return fail(ctx, BLINK_ERR_WORKSPACE, std::string("row-bucket allocation: ") + cudaGetErrorString(e));
         p->d_csr = static_cast<unsigned char *>(cb);
+        p->csr_bytes = size_t(csr_total);
         TRY(cudaMemsetAsync(p->d_csr, 0, size_t(csr_total), st));
     }
     Error er = blink::launch_tables(d_ant_xyz, n_ant, p->nb, p->n_chan, p->d_geom, p->d_info,
@@ -469,6 +472,7 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.ev_join = p->ctx->ev_join;
     a.queue = p->d_queue;
     a.queue_bytes = p->queue_bytes;
+    a.csr_bytes = p->csr_bytes;
     return a;
 }
 

@@ -472,7 +472,7 @@ struct LargeSched {
     int nR, nC;     // row and column items per layer
     int lag;        // stages between a layer's row and column items
     int slots;      // scratch ring slots (layers)
-    int ahead;      // layers between a layer and the one whose inputs it prefetches
+    int ahead;      // layers between a layer and the one whose row buckets it prefetches (0: none)
     int64_t total;  // n (nR + nC)
     unsigned long long wait_ns;
 };
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
                 if (sub == 0) {
                     prefetch_l2_bytes(a.vis + L.vis_off, 8 * a.nb, tid, 256);
                     const int la = layer + q.ahead;
-                    if (a.csr && la < q.n) {
+                    if (q.ahead > 0 && a.csr && la < q.n) {
                         const ChanInfo cp = a.chans[a.layers[la].chan];
                         if (cp.csr_off >= 0) {
                             const CsrLayout cl(N, a.nb);
@@ -833,7 +833,10 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     // gaps wide (and lag <= slots - 1).
     const int lag_want = int(4 * grid / int64_t(q.nR + q.nC)) + 1;
     q.lag = std::max(0, std::min({lag_want, q.slots / 2, q.n}));
-    q.ahead = int(std::min<int64_t>(64, std::max<int64_t>(1, grid / int64_t(q.nR + q.nC))));
+    // look-ahead prefetch of row buckets: only when they do not all stay in L2
+    q.ahead = a.csr_bytes > (size_t(32) << 20)
+                  ? int(std::min<int64_t>(64, std::max<int64_t>(1, grid / int64_t(q.nR + q.nC))))
+                  : 0;
     BLINK_CUDA_TRY(cudaMemsetAsync(a.queue, 0, image_queue_bytes(q.n), st));
     kern<<<unsigned(grid), 256, smem, st>>>(a, q, static_cast<float *>(a.out), a.ref);
     BLINK_CUDA_TRY(cudaGetLastError());

@@ -59,6 +59,8 @@ struct ImageArgs {
     // the launcher); null: the large-image path runs in waves of two kernels
     int *queue = nullptr;
     size_t queue_bytes = 0;
+    size_t csr_bytes = 0;       // row buckets of all channels (the large kernel looks ahead
+                                // for them only when they cannot all stay in L2)
 };
 
 // Device words the persistent large-image kernel needs for a group of

@@ -4,11 +4,12 @@
 // telescope pipeline that reserves all GPU memory when an observation starts
 // and forbids allocation (and its latency) afterwards, or a host framework
 // whose own allocator already owns the whole device.  For them this file
-// provides blink_image_batch_noalloc: the same imaging kernels as
+// provides blink_image_batch_noalloc: the imaging kernels of
 // blink_image_batch, with every piece of scratch (channel tables, layer
-// descriptors, the row-transform buffer of large images) carved out of one
-// file-scope static device array of BLINK_NOALLOC_SCRATCH_BYTES bytes.  It
-// calls no cudaMalloc, cudaFree or allocating library routine.
+// descriptors, gridding schedules and row buckets, the work queue, the
+// row-transform ring of large images) carved out of one file-scope static
+// device array of BLINK_NOALLOC_SCRATCH_BYTES bytes.  It calls no cudaMalloc,
+// cudaFree or allocating library routine.
 //
 // The array exists once per GPU that loads the library and lives until the
 // process exits.  Every call reuses it: what must start at zero is cleared on
@@ -120,19 +121,63 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
         }
         prev = c;
     }
-    // layout of the static scratch
-    int64_t wgt_total = 0;
-    bool any_uniform = false;
+    // layout of the static scratch: the tables blink_image_batch builds (cell
+    // codes, weights, the register schedule of sizes <= 256, the row buckets
+    // of large sizes), the work queue and status word, then the row-transform
+    // ring of large images.  A schedule or bucket set that does not fit is
+    // left out and the kernels take their atomic fallback for that call.
+    const bool want_sched = n_px <= 256;
+    const bool want_csr = !blink::image_small_path(n_px, n_px / 2 + 1);
+    const int q_chunks = int((nb + blink::kSchedMaxChunk - 1) / blink::kSchedMaxChunk);
+    int k_chunk = int((nb + q_chunks - 1) / q_chunks);
+    k_chunk += k_chunk & 1;
+    const size_t sched_per = want_sched ? size_t(blink::SchedLayout(n_px, nb, q_chunks).bytes) : 0;
+    const size_t csr_per = want_csr ? size_t(blink::CsrLayout(n_px, nb).bytes) : 0;
+    auto tables_end = [&](bool sched, bool csr) {
+        const int64_t wgt_cells = int64_t(n_px / 2) * n_px;
+        int64_t w = 0;
+        for (int c = 0; c < n_chan; ++c)
+            if (geoms[c].weighting == BLINK_UNIFORM || sched) w += wgt_cells;
+        size_t o = 0;
+        o = up(o + sizeof(ChanGeom) * n_chan);
+        o = up(o + sizeof(ChanInfo) * n_chan);
+        o = up(o + sizeof(blink_layer) * size_t(n_layers));
+        o = up(o + sizeof(DevLayer) * size_t(n_layers));
+        o = up(o + sizeof(uint32_t) * size_t(n_chan) * size_t(nb));
+        o = up(o + sizeof(float) * size_t(w > 0 ? w : 1));
+        o = up(o + sizeof(int));                                   // status word
+        o = up(o + blink::image_queue_bytes(n_layers));
+        if (csr) o = up(o + csr_per * n_chan);
+        if (sched) o = up(o + sched_per * n_chan);
+        return o;
+    };
+    bool use_sched = want_sched, use_csr = want_csr;
+    if (use_sched && tables_end(true, use_csr) > kBytes) use_sched = false;
+    if (use_csr && tables_end(use_sched, true) > kBytes) use_csr = false;
+    int64_t wgt_total = 0, sched_total = 0, csr_total = 0;
+    bool any_counts = false;
     for (int c = 0; c < n_chan; ++c) {
         ChanInfo ci{};
         ci.n_px = geoms[c].n_px;
         ci.weighting = geoms[c].weighting;
         ci.code_off = int64_t(c) * nb;
         ci.wgt_off = -1;
-        if (ci.weighting == BLINK_UNIFORM) {
+        ci.sched_off = -1;
+        ci.csr_off = -1;
+        if (use_sched) {
+            ci.n_chunks = q_chunks;
+            ci.chunk = k_chunk;
+            ci.sched_off = sched_total;
+            sched_total += int64_t(sched_per);
+        }
+        if (use_csr) {
+            ci.csr_off = csr_total;
+            csr_total += int64_t(csr_per);
+        }
+        if (ci.weighting == BLINK_UNIFORM || use_sched) {
             ci.wgt_off = wgt_total;
             wgt_total += int64_t(n_px / 2) * n_px;
-            any_uniform = true;
+            any_counts = true;
         }
         infos[c] = ci;
     }
@@ -143,6 +188,10 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     const size_t o_layers = off; off = up(off + sizeof(DevLayer) * size_t(n_layers));
     const size_t o_codes = off; off = up(off + sizeof(uint32_t) * size_t(n_chan) * size_t(nb));
     const size_t o_wgt = off; off = up(off + sizeof(float) * size_t(wgt_total > 0 ? wgt_total : 1));
+    const size_t o_status = off; off = up(off + sizeof(int));
+    const size_t o_queue = off; off = up(off + blink::image_queue_bytes(n_layers));
+    const size_t o_csr = off; off = up(off + size_t(csr_total));
+    const size_t o_sched = off; off = up(off + size_t(sched_total));
     const size_t o_rows = off;
     if (off > kBytes)
         return say(err_msg, err_cap, BLINK_ERR_WORKSPACE,
@@ -160,6 +209,10 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     DevLayer *d_layers = reinterpret_cast<DevLayer *>(base + o_layers);
     uint32_t *d_codes = reinterpret_cast<uint32_t *>(base + o_codes);
     float *d_wgt = reinterpret_cast<float *>(base + o_wgt);
+    int *d_status = reinterpret_cast<int *>(base + o_status);
+    int *d_queue = reinterpret_cast<int *>(base + o_queue);
+    unsigned char *d_csr = csr_total ? base + o_csr : nullptr;
+    unsigned char *d_sched = sched_total ? base + o_sched : nullptr;
     float2 *d_rows = reinterpret_cast<float2 *>(base + o_rows);
 #define NA_TRY(call)                                                                      \
     do {                                                                                  \
@@ -170,15 +223,26 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     NA_TRY(cudaMemcpyAsync(d_raw, h_layers, sizeof(blink_layer) * size_t(n_layers), cudaMemcpyHostToDevice, s));
     k_layers<<<(n_layers + 255) / 256, 256, 0, s>>>(d_raw, n_layers, d_geom, n_chan, d_layers);
     NA_TRY(cudaGetLastError());
-    if (any_uniform) NA_TRY(cudaMemsetAsync(d_wgt, 0, sizeof(float) * size_t(wgt_total), s));
+    // the array keeps the last call's contents: clear everything that is accumulated
+    if (any_counts) NA_TRY(cudaMemsetAsync(d_wgt, 0, sizeof(float) * size_t(wgt_total), s));
+    NA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+    if (d_csr) NA_TRY(cudaMemsetAsync(d_csr, 0, size_t(csr_total), s));
+    if (d_sched) NA_TRY(cudaMemsetAsync(d_sched, 0, size_t(sched_total), s));
     blink::Error e = blink::launch_tables(d_ant_xyz, n_ant, nb, n_chan, d_geom, d_info, d_codes, nullptr,
-                                          d_wgt, any_uniform, s);
+                                          d_wgt, any_counts, s, d_sched, d_csr);
     if (e.status) return say(err_msg, err_cap, e.status, e.msg.c_str());
     NA_TRY(cudaMemcpyAsync(infos, d_info, sizeof(ChanInfo) * n_chan, cudaMemcpyDeviceToHost, s));
     NA_TRY(cudaStreamSynchronize(s));
 #undef NA_TRY
-    int r_alloc = 1;
-    for (int c = 0; c < n_chan; ++c) r_alloc = infos[c].rows > r_alloc ? infos[c].rows : r_alloc;
+    int r_alloc = 1, max_chunk = 0, max_seg = 0, kmax = 0;
+    bool sched_ok = d_sched != nullptr;
+    for (int c = 0; c < n_chan; ++c) {
+        r_alloc = infos[c].rows > r_alloc ? infos[c].rows : r_alloc;
+        sched_ok = sched_ok && infos[c].sched_off >= 0 && infos[c].sched == 1;
+        max_chunk = infos[c].chunk > max_chunk ? infos[c].chunk : max_chunk;
+        max_seg = infos[c].max_seg > max_seg ? infos[c].max_seg : max_seg;
+        kmax = infos[c].kmax_u > kmax ? infos[c].kmax_u : kmax;
+    }
     const size_t per_layer = blink::image_scratch_per_layer(n_px, r_alloc);
     const size_t rows_bytes = kBytes - o_rows;
     if (per_layer > rows_bytes)
@@ -198,6 +262,17 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     a.r_alloc = r_alloc;
     a.scratch = per_layer ? d_rows : nullptr;
     a.scratch_bytes = per_layer ? rows_bytes : 0;
+    a.sched = d_sched;
+    a.sched_ok = sched_ok ? 1 : 0;
+    a.max_chunk = max_chunk;
+    a.max_seg = max_seg;
+    a.status = d_status;
+    a.csr = d_csr;
+    a.csr_bytes = size_t(csr_total);
+    a.kmax = kmax;
+    a.n_ant = n_ant;
+    a.queue = d_queue;
+    a.queue_bytes = blink::image_queue_bytes(n_layers);
     e = blink::launch_image_group(n_px, a, s);
     if (e.status) return say(err_msg, err_cap, e.status, e.msg.c_str());
     return BLINK_OK;
