@@ -612,86 +612,113 @@ __global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
 template <int N>
 struct DegridCfg {
     static constexpr int NT = 256;
-    static constexpr int S = N + 1;
-    // column pairs per CTA: keep strip + exchange buffer near 64 KB
-    static constexpr int P = std::max(1, std::min({32, NT / Plan<N>::N1, int(65536 / (16 * S))}));
-    static constexpr int SW = 2 * P + 1;  // strip row stride in floats (odd)
+    static constexpr int P = 8;           // column pairs per CTA: 16 adjacent image columns
+    static constexpr int W = 2 * P + 1;   // strip row stride in floats (odd)
     static constexpr int RB = LargeCfg<N>::RB;
+    using ZL = ZLayout<N, P>;
+    static_assert(P * Plan<N>::N2 <= NT && P * Plan<N>::N1 <= NT, "one four-step task per thread");
 };
 
 template <int N>
 size_t degrid_cols_smem() {
     using C = DegridCfg<N>;
-    return std::max(size_t(N) * C::SW / 2 + 1, size_t(C::P) * N) * sizeof(float2) +
-           size_t(C::P) * C::S * sizeof(float2);
+    return std::max({size_t(N) * C::W * sizeof(float), size_t(C::P) * C::ZL::S * sizeof(float2),
+                     size_t(C::P) * N * sizeof(float2)});
 }
 
-// Grid: (ceil(N/2 / P), layers in wave).  R (float [N][N]) is read at
-// out_off; rows k < R of the column transforms go to scratch[lw][k][n].
+// Forward column transforms of the image gradient (the first half of the
+// adjoint's forward 2-D FFT).  CTA x of a layer takes the 16 adjacent image
+// columns [16 x, 16 x + 16) -- one 64-byte piece of every image row, read
+// once -- as 8 pairs of real columns, each pair one complex N-point transform
+// (z = R_a + i R_b).  The strip, the four-step intermediate and the
+// natural-order result share one buffer: every task holds its inputs in
+// registers across a barrier before the buffer is overwritten.  Rows k < R of
+// the two real columns' transforms go to scratch[lw][k][j] (FFT-order column
+// j = image column + N/2 mod N), 16 adjacent columns per row.
+// Grid: (N / 16, layers in wave).
 template <int N>
 __global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, const float *resid, int l0) {
     using C = DegridCfg<N>;
-    constexpr int NT = C::NT, S = C::S, P = C::P, SW = C::SW, H = N / 2;
+    using ZL = typename C::ZL;
+    constexpr int NT = C::NT, P = C::P, W = C::W, H = N / 2;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     extern __shared__ float2 sm[];
-    float *strip = reinterpret_cast<float *>(sm);          // [N][SW], FFT-order rows
-    float2 *zn = sm;                                        // [P][N] natural order (aliases strip)
-    float2 *Z = sm + std::max(size_t(N) * SW / 2 + 1, size_t(P) * N);  // [P][S]
+    float *strip = reinterpret_cast<float *>(sm);  // [N][W]: FFT-order row n = image row (n + H) mod N
+    float2 *Z = sm;                                // [P][ZL::S] four-step intermediate
+    float2 *zn = sm;                               // [P][N] natural order
     const int lw = blockIdx.y;
     const DevLayer L = a.layers[l0 + lw];
     const ChanInfo ci = a.chans[L.chan];
     const int R = ci.rows;
-    const int j0 = blockIdx.x * P;
+    const int x0 = blockIdx.x * 2 * P;             // first image column
+    const int nc = min(2 * P, N - x0);             // columns of this CTA (the last may be partial)
     const int tid = threadIdx.x;
     const float *img = resid + L.out_off;
-    // strip: FFT-order row n holds image row (n + H) mod N; column jj is FFT
-    // column j0 + jj (image column j0 + jj + H), column P + jj is FFT column
-    // j0 + jj + H (image column j0 + jj)
-    for (int i = tid; i < N * 2 * P; i += NT) {
-        const int n = i / (2 * P), c = i % (2 * P);
-        const int jj = c < P ? c : c - P;
-        const int j = j0 + jj;
-        float v = 0.f;
-        if (j < H) v = __ldg(img + int64_t((n + H) % N) * N + (c < P ? j + H : j));
-        strip[n * SW + c] = v;
+    if (nc == 2 * P && (reinterpret_cast<uintptr_t>(img) & 15) == 0 && (N % 4) == 0) {
+        for (int i = tid; i < N * (2 * P / 4); i += NT) {
+            const int y = i / (2 * P / 4), q = i % (2 * P / 4);
+            const float4 v = __ldcs(reinterpret_cast<const float4 *>(img + int64_t(y) * N + x0) + q);
+            float *d = strip + ((y + H) % N) * W + 4 * q;
+            d[0] = v.x;
+            d[1] = v.y;
+            d[2] = v.z;
+            d[3] = v.w;
+        }
+    } else {
+        for (int i = tid; i < N * 2 * P; i += NT) {
+            const int y = i / (2 * P), c = i % (2 * P);
+            strip[((y + H) % N) * W + c] = c < nc ? __ldcs(img + int64_t(y) * N + x0 + c) : 0.f;
+        }
     }
     __syncthreads();
-    // step A: z = R_a + i R_b along stride N2, forward twiddles
-    for (int t = tid; t < P * N2; t += NT) {
-        const int jj = t % P, n2 = t / P;
-        float2 x[N1];
+    // step A: pair p, n2; z = R_a + i R_b along stride N2, forward twiddles
+    const int pa = tid % P, n2 = tid / P;
+    const bool task_a = n2 < N2;
+    float2 x[N1];
+    if (task_a) {
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
-            const int n = N2 * n1 + n2;
-            x[n1] = make_float2(strip[n * SW + jj], strip[n * SW + P + jj]);
+            const float *r = strip + (N2 * n1 + n2) * W + 2 * pa;
+            x[n1] = make_float2(r[0], r[1]);
         }
+    }
+    __syncthreads();  // the strip is in registers: the buffer becomes Z
+    if (task_a) {
         dft<N1, -1>(x);
-        float2 *zp = Z + jj * S + n2;
+        float2 *zp = Z + pa * ZL::S;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) zp[N2 * k1] = k1 == 0 ? x[0] : cmulc(x[k1], four_step_tw<N, -1>(k1, n2));
+        for (int k1 = 0; k1 < N1; ++k1)
+            zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], four_step_tw<N, -1>(k1, n2));
     }
     __syncthreads();
-    // step B: outputs in natural order to zn (the strip is no longer read)
-    for (int t = tid; t < P * N1; t += NT) {
-        const int jj = t % P, k1 = t / P;
-        const float2 *zp = Z + jj * S + N2 * k1;
-        float2 y[N2];
+    // step B: pair p, k1; results to natural order (in registers first)
+    const int pb = tid % P, k1 = tid / P;
+    const bool task_b = k1 < N1;
+    float2 y[N2];
+    if (task_b) {
+        const float2 *zp = Z + pb * ZL::S;
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[n2];
+        for (int m = 0; m < N2; ++m) y[m] = zp[ZL::phys(N2 * k1 + m)];
         dft<N2, -1>(y);
+    }
+    __syncthreads();  // Z is in registers: the buffer becomes zn
+    if (task_b) {
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) zn[jj * N + k1 + N1 * k2] = y[k2];
+        for (int k2 = 0; k2 < N2; ++k2) zn[pb * N + k1 + N1 * k2] = y[k2];
     }
     __syncthreads();
-    // unpack the two real columns and keep rows k < R
+    // unpack the two real columns of each pair and keep rows k < R; image
+    // column x goes to FFT-order column (x + N/2) mod N
     float2 *out = a.scratch + int64_t(lw) * a.r_alloc * N;
     for (int i = tid; i < R * P; i += NT) {
-        const int k = i / P, jj = i % P, j = j0 + jj;
-        if (j >= H) continue;
-        const float2 za = zn[jj * N + k], zb = zn[jj * N + (N - k) % N];
+        const int k = i / P, p = i % P;
+        const int xa = x0 + 2 * p;
+        if (xa >= N) continue;
+        const float2 za = zn[p * N + k], zb = zn[p * N + (N - k) % N];
         // C_a = (Z[k] + conj Z[N-k]) / 2, C_b = (Z[k] - conj Z[N-k]) / (2 i)
-        out[int64_t(k) * N + j] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-        out[int64_t(k) * N + j + H] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+        out[int64_t(k) * N + (xa + H) % N] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+        if (xa + 1 < N)
+            out[int64_t(k) * N + (xa + 1 + H) % N] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
     }
 }
 
@@ -762,7 +789,7 @@ Error launch_degrid_n(const ImageArgs &a, const float *resid, float2 *dvis, cuda
     const size_t smem_r = rows_smem<N>();
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_c)));
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_r)));
-    const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
+    const unsigned pchunks = unsigned((N + 2 * C::P - 1) / (2 * C::P));
     const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
     // waves split over the auxiliary stream as in the forward path
     const bool two = a.aux && a.ev_fork && a.ev_join && wave >= 2;

@@ -178,3 +178,24 @@ def test_gain_gradient_kernels_match_oracle_chain_rule(torch, ctx, n_ant):
     assert torch.equal(got, again)
     g = got.cpu().numpy()
     assert np.abs(g - want).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n_px", [180, 256])
+def test_degrid_unaligned_image_gradient(torch, ctx, n_px):
+    """The image gradient at an odd float offset (the column pass then reads
+    its strips element by element instead of in 16-byte pieces)."""
+    from paper_2405_13478_gb300 import binding
+    ws = synth.single_image(seed=n_px + 31)
+    du = synth.max_uv(ws.ant_xyz, ws.freqs_hz[0]) / (n_px / 2 - 1)
+    L = dict(n_px=n_px, weighting=0, freq_hz=float(ws.freqs_hz[0]), delta_u=du, vis_offset=0,
+             out_offset=1)
+    resid = np.random.default_rng(n_px).normal(size=(n_px, n_px))
+    r = torch.zeros(n_px * n_px + 1, dtype=torch.float32)
+    r[1:] = torch.as_tensor(resid.reshape(-1), dtype=torch.float32)
+    dvis = torch.empty(ws.n_baselines, dtype=torch.complex64, device="cuda")
+    ctx.degrid(torch.as_tensor(ws.ant_xyz).cuda(), [L], r.cuda(), dvis)
+    torch.cuda.synchronize()
+    ku, kv = layer_cells(ws.ant_xyz, L)
+    want = oracle.degrid(ku, kv, resid.astype(np.float32).astype(np.float64), 0, "fft")
+    got = dvis.cpu().numpy()
+    assert np.abs(got - want).max() <= TOL * np.abs(want).max()
