@@ -158,18 +158,24 @@ struct ZLayout {
     __device__ __forceinline__ static int phys(int q) { return pad ? q + (q >> 5) : q; }
 };
 
-// Pass 2, step A for column pairs (j0 + jj, j0 + jj + N/2), jj < P.  `hrow(k,
-// p)` returns row k (< R) of the pass-1 output at frequency column p.  Writes
-// the four-step intermediate of pair jj to Z + jj * S.
-template <int N, int P, class ZL, class HRow>
-__device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow hrow, int tid,
+// Pass 2 of the two-kernel path pairs adjacent frequency columns: pair q
+// (< N/2) is the FFT-order columns 2q and 2q + 1, whose real transforms are
+// image columns (2q + N/2) mod N and the next one (N/2 is even for every
+// supported size, so the two never wrap apart).  A CTA's P pairs are thus 2P
+// adjacent columns: one contiguous piece of every pass-1 row read, and of
+// every image row written.
+//
+// Pass 2, step A for pairs j0 + jj, jj < P.  `hrow2(k, c)` returns row k (< R)
+// of the pass-1 output at the frequency columns c and c + 1.  Writes the
+// four-step intermediate of pair jj to Z + jj * S.
+template <int N, int P, class ZL, class HRow2>
+__device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow2 hrow2, int tid,
                                             int nt) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
     for (int t = tid; t < P * N2; t += nt) {
         const int jj = t % P, n2 = t / P;
-        const int ja = j0 + jj;
-        if (ja >= H) continue;
-        const int jb = ja + H;
+        const int q = j0 + jj;
+        if (q >= H) continue;
         float2 x[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
@@ -177,14 +183,14 @@ __device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow hrow,
             float2 z = make_float2(0.f, 0.f);
             if (k < H) {
                 if (k < R) {
-                    const float2 a = hrow(k, ja), b = hrow(k, jb);
-                    z = make_float2(a.x - b.y, a.y + b.x);  // H_a + i H_b
+                    const float4 ab = hrow2(k, 2 * q);
+                    z = make_float2(ab.x - ab.w, ab.y + ab.z);  // H_a + i H_b
                 }
             } else if (k > H) {
                 const int m = N - k;
                 if (m < R) {
-                    const float2 a = hrow(m, ja), b = hrow(m, jb);
-                    z = make_float2(a.x + b.y, b.x - a.y);  // conj(H_a) + i conj(H_b)
+                    const float4 ab = hrow2(m, 2 * q);
+                    z = make_float2(ab.x + ab.w, ab.z - ab.y);  // conj(H_a) + i conj(H_b)
                 }
             }
             x[n1] = z;
@@ -197,24 +203,26 @@ __device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow hrow,
     }
 }
 
-// Pass 2, step B: N2-point transforms, then the two real image columns with
-// the fftshift folded into the addresses.
+// Pass 2, step B: N2-point transforms, then the two real image columns of
+// each pair (adjacent) with the fftshift folded into the addresses.
 template <int N, int P, class ZL>
 __device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img, float scale,
                                             int tid, int nt, const float *ref) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
+    const bool pair_store = ((reinterpret_cast<uintptr_t>(img) | reinterpret_cast<uintptr_t>(ref)) & 7) == 0;
     for (int t = tid; t < P * N1; t += nt) {
         const int jj = t % P, k1 = t / P;
-        const int ja = j0 + jj;
-        if (ja >= H) continue;
+        const int q = j0 + jj;
+        if (q >= H) continue;
+        const int xa = (2 * q + H) % N;  // image column of the pair's first column; the second is xa + 1
         const float2 *zp = Z + jj * ZL::S;
         float2 rf[N2];  // fused epilogue: reference values requested before the transform
         if (ref) {
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) {
-                const int q = k1 + N1 * k2;
-                const float *rp = ref + (q < H ? q + H : q - H) * N;  // 32-bit: N * N < 2^31
-                rf[k2] = make_float2(__ldcs(rp + ja + H), __ldcs(rp + ja));
+                const int qq = k1 + N1 * k2;
+                const float *rp = ref + (qq < H ? qq + H : qq - H) * N + xa;  // 32-bit: N * N < 2^31
+                rf[k2] = pair_store ? __ldcs(reinterpret_cast<const float2 *>(rp)) : make_float2(__ldcs(rp), __ldcs(rp + 1));
             }
         }
         float2 y[N2];
@@ -223,16 +231,20 @@ __device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img,
         dft<N2, +1>(y);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
-            const int q = k1 + N1 * k2;               // FFT-order row
-            const int row = q < H ? q + H : q - H;    // fftshift
-            const int o = row * N;  // offsets inside one image fit 32 bits
-            float va = y[k2].x * scale, vb = y[k2].y * scale;
+            const int qq = k1 + N1 * k2;              // FFT-order row
+            const int row = qq < H ? qq + H : qq - H; // fftshift
+            float *o = img + row * N + xa;            // offsets inside one image fit 32 bits
+            float2 v = make_float2(y[k2].x * scale, y[k2].y * scale);
             if (ref) {
-                va -= rf[k2].x;
-                vb -= rf[k2].y;
+                v.x -= rf[k2].x;
+                v.y -= rf[k2].y;
             }
-            __stcs(img + o + ja + H, va);             // column ja   -> ja + N/2
-            __stcs(img + o + ja, vb);                 // column ja+H -> ja
+            if (pair_store) {
+                __stcs(reinterpret_cast<float2 *>(o), v);
+            } else {
+                __stcs(o, v.x);
+                __stcs(o + 1, v.y);
+            }
         }
     }
 }
@@ -355,25 +367,23 @@ __global__ void __launch_bounds__(RowsCfg<N>::NT, Plan<N>::N1 == 24 ? 2 : 3) k_r
 template <int N>
 struct ColsStaged {
     static constexpr int P = LargeCfg<N>::P, N2 = Plan<N>::N2;
-    static constexpr bool value = P * N2 == LargeCfg<N>::NT && (N / 2) % P == 0 && P % 2 == 0;
+    static constexpr bool value = P * N2 == LargeCfg<N>::NT && (N / 2) % P == 0;
 };
 
-// Pass 2, step A from shared memory: all of the CTA's scratch columns (pairs
-// j0..j0+P and their partners + N/2, rows k < R) are copied with cp.async at
+// Pass 2, step A from shared memory: the CTA's 2P adjacent scratch columns of
+// rows k < R (one contiguous piece of each row) are copied with cp.async at
 // once into the buffer Z later holds; each thread reads its N1 inputs into
-// registers, the CTA synchronises, then the intermediate overwrites the buffer.
+// registers (one 16-byte load per pair and row), the CTA synchronises, then
+// the intermediate overwrites the buffer.
 template <int N, int P, class ZL>
 __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, const float2 *Hs, int tid) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2, NT = LargeCfg<N>::NT;
-    float2 *stg = Z;  // [R][2P]: columns j0.. then j0 + N/2..
-    // with P = 8 a staged row is one 16-bank row; column c of row k sits at
-    // c ^ 8 (k & 1) so the two rows a half-warp reads fall in distinct banks
-    auto sw = [](int k, int c) { return P == 8 ? c ^ ((k & 1) << 3) : c; };
+    float2 *stg = Z;  // [R][2P]: frequency columns 2 j0 ..
     for (int i = tid; i < R * P; i += NT) {  // P 16-byte pieces per row
-        const int k = i / P, piece = i % P, half = piece / (P / 2), q = piece % (P / 2);
-        const float2 *src = Hs + int64_t(k) * N + (half ? j0 + H : j0) + 2 * q;
+        const int k = i / P, pc = i % P;
+        const float2 *src = Hs + int64_t(k) * N + 2 * (j0 + pc);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(uint32_t(__cvta_generic_to_shared(
-                         stg + k * 2 * P + sw(k, half * P + 2 * q)))),
+                         stg + k * 2 * P + 2 * pc))),
                      "l"(src)
                      : "memory");
     }
@@ -387,14 +397,14 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
         float2 z = make_float2(0.f, 0.f);
         if (k < H) {
             if (k < R) {
-                const float2 a = stg[k * 2 * P + sw(k, jj)], b = stg[k * 2 * P + sw(k, P + jj)];
-                z = make_float2(a.x - b.y, a.y + b.x);  // H_a + i H_b
+                const float4 ab = *reinterpret_cast<const float4 *>(stg + k * 2 * P + 2 * jj);
+                z = make_float2(ab.x - ab.w, ab.y + ab.z);  // H_a + i H_b
             }
         } else if (k > H) {
             const int m = N - k;
             if (m < R) {
-                const float2 a = stg[m * 2 * P + sw(m, jj)], b = stg[m * 2 * P + sw(m, P + jj)];
-                z = make_float2(a.x + b.y, b.x - a.y);  // conj(H_a) + i conj(H_b)
+                const float4 ab = *reinterpret_cast<const float4 *>(stg + m * 2 * P + 2 * jj);
+                z = make_float2(ab.x + ab.w, ab.z - ab.y);  // conj(H_a) + i conj(H_b)
             }
         }
         x[n1] = z;
@@ -419,8 +429,8 @@ __device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L,
     if constexpr (ColsStaged<N>::value) {
         cols_step_a_staged<N, P, ZL>(sm, R, j0, Hs, tid);
     } else {
-        auto hrow = [&](int k, int p) { return __ldcg(Hs + int64_t(k) * N + p); };
-        cols_step_a<N, P, ZL>(sm, R, j0, hrow, tid, NT);
+        auto hrow2 = [&](int k, int c) { return __ldcg(reinterpret_cast<const float4 *>(Hs + int64_t(k) * N + c)); };
+        cols_step_a<N, P, ZL>(sm, R, j0, hrow2, tid, NT);
     }
     __syncthreads();
     consumed();  // every read of Hs has landed in registers or shared memory
