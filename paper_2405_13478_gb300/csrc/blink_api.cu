@@ -79,6 +79,7 @@ struct blink_plan {
         int force_path = 0;       // autotuned kernel choice (0 = default)
         size_t wave_budget = 0;   // autotuned wave size of the two-kernel path
         int kmax = 0;             // max |k_u| over the group's channels
+        int row_entries = 0;      // max kept baselines per support row over the group's channels
     };
     std::vector<Group> groups;
     // device memory (one pool allocation for the tables, one for scratch)
@@ -411,6 +412,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
             g.max_chunk = std::max(g.max_chunk, ci.chunk);
             g.max_seg = std::max(g.max_seg, ci.max_seg);
             g.kmax = std::max(g.kmax, ci.kmax_u);
+            g.row_entries = std::max(g.row_entries, int(ci.n_kept / std::max(1, ci.rows)));
         }
         g.r_alloc = r;
         const size_t per = blink::image_scratch_per_layer(g.n_px, r);
@@ -473,6 +475,7 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.queue = p->d_queue;
     a.queue_bytes = p->queue_bytes;
     a.csr_bytes = p->csr_bytes;
+    a.row_entries = g.row_entries;
     return a;
 }
 

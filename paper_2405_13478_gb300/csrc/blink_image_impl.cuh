@@ -313,10 +313,10 @@ struct RowsCfg {
 // the row transforms, written in natural column order to dst[r - r0][p].
 template <int N>
 __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L, const ChanInfo &ci, int r0,
-                                          float2 *__restrict__ dst, float2 *sm, int tid) {
+                                          int nrows, float2 *__restrict__ dst, float2 *sm, int tid) {
     using C = RowsCfg<N>;
-    constexpr int NT = C::NT, S = C::S, RB = C::RB;
-    const int nrows = min(RB, ci.rows - r0);
+    constexpr int NT = C::NT, S = C::S;
+    __builtin_assume(nrows >= 1 && nrows <= C::RB);
     float2 *tw = sm + C::tw;
     auto prologue = [&]() {
         stage_four_step<N>(tw, tid, NT);
@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(RowsCfg<N>::NT, Plan<N>::N1 == 24 ? 2 : 3) k_r
     const ChanInfo ci = a.chans[L.chan];
     const int r0 = blockIdx.x * RowsCfg<N>::RB;
     if (r0 >= ci.rows) return;
-    rows_item<N>(a, L, ci, r0, a.scratch + (int64_t(lw) * a.r_alloc + r0) * N, sm, threadIdx.x);
+    rows_item<N>(a, L, ci, r0, min(RowsCfg<N>::RB, ci.rows - r0), a.scratch + (int64_t(lw) * a.r_alloc + r0) * N, sm,
+                 threadIdx.x);
 }
 
 // The column pass can stage its scratch columns through shared memory when
@@ -479,6 +480,7 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT, EPI ? 1 : 3) k_cols(ImageArgs
 // skip their work.
 struct LargeSched {
     int n;          // layers of the group
+    int rb;         // rows per row item (<= RowsCfg<N>::RB)
     int nR, nC;     // row and column items per layer
     int lag;        // stages between a layer's row and column items
     int slots;      // scratch ring slots (layers)
@@ -598,8 +600,9 @@ __global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
                         }
                     }
                 }
-                const int r0 = sub * RowsCfg<N>::RB;
-                if (r0 < ci.rows) rows_item<N>(a, L, ci, r0, Hs + int64_t(r0) * N, sm, tid);
+                const int r0 = sub * q.rb;
+                const int nrows = min(RowsCfg<N>::RB, min(q.rb, ci.rows - r0));
+                if (r0 < ci.rows) rows_item<N>(a, L, ci, r0, nrows, Hs + int64_t(r0) * N, sm, tid);
                 __syncthreads();  // every thread's scratch stores precede the release below
                 if (tid == 0) {
                     __threadfence();
@@ -848,7 +851,11 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
     LargeSched q{};
     q.n = a.n_layers;
-    q.nR = (a.r_alloc + RowsCfg<N>::RB - 1) / RowsCfg<N>::RB;
+    // band height: at most RB rows, and about kBandEntries gridding entries
+    // per row item, so a dense band does not hold up its layer's column items
+    constexpr int kBandEntries = 4096;
+    q.rb = a.row_entries > 0 ? std::max(1, std::min(RowsCfg<N>::RB, kBandEntries / a.row_entries)) : RowsCfg<N>::RB;
+    q.nR = (a.r_alloc + q.rb - 1) / q.rb;
     q.nC = (N / 2 + LargeCfg<N>::P - 1) / LargeCfg<N>::P;
     q.total = int64_t(q.n) * (q.nR + q.nC);
     q.wait_ns = a.wait_ns < 0 ? kWaitNs : static_cast<unsigned long long>(a.wait_ns);
@@ -863,12 +870,12 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     BLINK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
     if (per_sm < 1) return Error{-2, "persistent image kernel does not fit on an SM for size " + std::to_string(N)};
     const int64_t grid = std::min<int64_t>(q.total, int64_t(per_sm) * sms);
-    // lag: up to four grids of items between a layer's row and column items
+    // lag: up to eight grids of items between a layer's row and column items
     // (a dense band of rows takes several times as long as a column item).
     // A row item also waits for the column items of the layer `slots` back,
     // which sit slots - lag stages earlier: half the ring each way keeps both
     // gaps wide (and lag <= slots - 1).
-    const int lag_want = int(4 * grid / int64_t(q.nR + q.nC)) + 1;
+    const int lag_want = int(8 * grid / int64_t(q.nR + q.nC)) + 1;
     q.lag = std::max(0, std::min({lag_want, q.slots / 2, q.n}));
     // look-ahead prefetch of row buckets: only when they do not all stay in L2
     q.ahead = a.csr_bytes > (size_t(32) << 20)

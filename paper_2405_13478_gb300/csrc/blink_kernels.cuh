@@ -61,6 +61,8 @@ struct ImageArgs {
     size_t queue_bytes = 0;
     size_t csr_bytes = 0;       // row buckets of all channels (the large kernel looks ahead
                                 // for them only when they cannot all stay in L2)
+    int row_entries = 0;        // largest kept baselines per support row among the group's
+                                // channels (sets the band height of large-image row items)
 };
 
 // Device words the persistent large-image kernel needs for a group of

@@ -234,7 +234,7 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     NA_TRY(cudaMemcpyAsync(infos, d_info, sizeof(ChanInfo) * n_chan, cudaMemcpyDeviceToHost, s));
     NA_TRY(cudaStreamSynchronize(s));
 #undef NA_TRY
-    int r_alloc = 1, max_chunk = 0, max_seg = 0, kmax = 0;
+    int r_alloc = 1, max_chunk = 0, max_seg = 0, kmax = 0, row_entries = 0;
     bool sched_ok = d_sched != nullptr;
     for (int c = 0; c < n_chan; ++c) {
         r_alloc = infos[c].rows > r_alloc ? infos[c].rows : r_alloc;
@@ -242,6 +242,8 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
         max_chunk = infos[c].chunk > max_chunk ? infos[c].chunk : max_chunk;
         max_seg = infos[c].max_seg > max_seg ? infos[c].max_seg : max_seg;
         kmax = infos[c].kmax_u > kmax ? infos[c].kmax_u : kmax;
+        const int per_row = int(infos[c].n_kept / (infos[c].rows > 1 ? infos[c].rows : 1));
+        row_entries = per_row > row_entries ? per_row : row_entries;
     }
     const size_t per_layer = blink::image_scratch_per_layer(n_px, r_alloc);
     const size_t rows_bytes = kBytes - o_rows;
@@ -270,6 +272,7 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     a.csr = d_csr;
     a.csr_bytes = size_t(csr_total);
     a.kmax = kmax;
+    a.row_entries = row_entries;
     a.n_ant = n_ant;
     a.queue = d_queue;
     a.queue_bytes = blink::image_queue_bytes(n_layers);
