@@ -127,23 +127,27 @@ __global__ void __launch_bounds__(kGradThreads) k_gain_grad_part(const float2 *_
     }
 }
 
-// Gain gradient, pass 2: per antenna, the partials in a fixed order.
+// Gain gradient, pass 2: one warp per antenna.  Lane l takes the partials
+// l, l + 32, ... of the antenna (row partials of every group, then the column
+// partials of every (group, tile)), and a fixed shuffle tree adds the 32
+// lane sums: the order never changes, so neither does the result.
 __global__ void k_gain_grad_sum(const double2 *__restrict__ pcol, const double2 *__restrict__ prow, int groups,
                                 int tiles, int n_ant, float2 *__restrict__ dgains) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = blockIdx.x * (blockDim.x / 32) + int(threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (a >= n_ant) return;
     double re = 0.0, im = 0.0;
-    for (int g = 0; g < groups; ++g) {
-        const double2 r = prow[int64_t(g) * n_ant + a];
-        re += r.x;
-        im += r.y;
-        for (int t = 0; t < tiles; ++t) {
-            const double2 c = pcol[(int64_t(g) * tiles + t) * n_ant + a];
-            re += c.x;
-            im += c.y;
-        }
+    const int terms = groups * (tiles + 1);
+    for (int k = lane; k < terms; k += 32) {
+        const int g = k / (tiles + 1), t = k % (tiles + 1);
+        const double2 v = t == tiles ? prow[int64_t(g) * n_ant + a] : pcol[(int64_t(g) * tiles + t) * n_ant + a];
+        re += v.x;
+        im += v.y;
     }
-    dgains[a] = make_float2(float(re), float(im));
+    for (int d = 16; d > 0; d >>= 1) {
+        re += __shfl_down_sync(0xFFFFFFFFu, re, d);
+        im += __shfl_down_sync(0xFFFFFFFFu, im, d);
+    }
+    if (lane == 0) dgains[a] = make_float2(float(re), float(im));
 }
 
 }  // namespace
@@ -193,7 +197,7 @@ Error launch_gain_grad(const float2 *dvis, const float2 *model, const float2 *ga
     k_gain_grad_part<<<dim3(unsigned(tiles), unsigned(groups)), kGradThreads, 0, st>>>(
         dvis, model, gains, vis_off, n_layers, n_ant, per, pcol, prow);
     BLINK_CUDA_TRY(cudaGetLastError());
-    k_gain_grad_sum<<<(n_ant + 255) / 256, 256, 0, st>>>(pcol, prow, groups, tiles, n_ant, dgains);
+    k_gain_grad_sum<<<(n_ant + 7) / 8, 256, 0, st>>>(pcol, prow, groups, tiles, n_ant, dgains);
     BLINK_CUDA_TRY(cudaGetLastError());
     return Error{0, ""};
 }
