@@ -23,10 +23,13 @@
 // Operands sit in shared memory in the K-major core-matrix layout of the
 // tensor cores (8 rows x 16 bytes per core matrix, no swizzle); global memory
 // holds them already in that layout so each tile arrives with one 1-D TMA
-// bulk copy.  One CTA computes one 128 x 256 output tile: 4 warps, thread 0
-// issues the MMAs, TMEM holds the FP32 accumulators, tcgen05.ld reads them
-// back for the epilogue.  Every wait is bounded; a timeout sets the status
-// word and the CTA still releases its tensor memory.
+// bulk copy.  One CTA computes one 128-row output tile, 256 columns wide for
+// a single product and 128 wide for the split modes (two CTAs per SM): 4
+// warps, thread 0 issues the MMAs, TMEM holds the FP32 accumulators, and
+// tcgen05.ld reads them back for the epilogue, which transposes each warp's
+// 32 x 32 block through shared memory so every image store covers 128
+// contiguous bytes of a row.  Every wait is bounded; a timeout sets the
+// status word and the CTA still releases its tensor memory.
 #include "blink_common.cuh"
 #include "blink_kernels.cuh"
 #include "blink_sync.cuh"
