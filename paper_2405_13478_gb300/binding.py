@@ -383,7 +383,7 @@ class Plan:
             g += 1
 
     def set_tuning(self, group, path, wave_bytes=0):
-        """Force size group `group` onto kernel path 0-3 (see blink_plan_set_tuning)."""
+        """Force size group `group` onto kernel path 0-4 (see blink_plan_set_tuning)."""
         self.ctx._raise(self.ctx._lib.blink_plan_set_tuning(self.handle, int(group), int(path),
                                                             int(wave_bytes)))
 

@@ -80,6 +80,7 @@ struct blink_plan {
         size_t wave_budget = 0;   // autotuned wave size of the two-kernel path
         int kmax = 0;             // max |k_u| over the group's channels
         int row_entries = 0;      // max kept baselines per support row over the group's channels
+        int64_t cg_stride = 0;    // compact grid per layer (complex elements), 0 if not used
     };
     std::vector<Group> groups;
     // device memory (one pool allocation for the tables, one for scratch)
@@ -103,6 +104,8 @@ struct blink_plan {
     int64_t out_extent = 0;        // max over layers of out_offset + n_px^2
     int *d_queue = nullptr;        // work queue of the persistent large-image kernel
     size_t queue_bytes = 0;
+    float2 *d_cg = nullptr;        // compact grids of a wave of large-image layers
+    size_t cg_bytes = 0;
     float2 *d_gprod = nullptr;     // gain-product table of the fused epilogue (on first use)
     size_t gprod_bytes = 0;
     cudaStream_t last_stream = nullptr;
@@ -113,6 +116,8 @@ struct blink_plan {
 namespace {
 
 constexpr size_t kScratchCap = size_t(48) << 20;
+// Compact grids of large-image layers per plan: one wave of the large path.
+constexpr size_t kCgCap = size_t(128) << 20;
 // Tensor-core transform scratch per plan: its waves trade L2 residency of the
 // pass-1 output for fewer, fuller launches (each wave is three kernels).
 constexpr size_t kTensorScratchCap = size_t(512) << 20;
@@ -212,6 +217,9 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     if (p->d_queue) cudaFreeAsync(p->d_queue, st);
     p->d_queue = nullptr;
     p->queue_bytes = 0;
+    if (p->d_cg) cudaFreeAsync(p->d_cg, st);
+    p->d_cg = nullptr;
+    p->cg_bytes = 0;
     p->gprod_bytes = 0;
     p->d_block = nullptr;
     p->d_scratch = nullptr;
@@ -399,7 +407,7 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     TRY(cudaStreamSynchronize(st));
     std::copy(h_info, h_info + p->infos.size(), p->infos.begin());
     // support rows per size group, scratch for the large-image path
-    size_t scratch = 0;
+    size_t scratch = 0, cg_need = 0;
     for (auto &g : p->groups) {
         int r = 1;
         g.sched_ok = p->d_sched != nullptr;
@@ -417,6 +425,15 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         g.r_alloc = r;
         const size_t per = blink::image_scratch_per_layer(g.n_px, r);
         if (per) scratch = std::max(scratch, std::max(per, std::min(per * size_t(g.count), kScratchCap)));
+        // compact gridding: every channel has its sorted chunk tables and the
+        // group's largest compact grid fits the kernel's shared memory
+        bool cg_ok = p->d_csr != nullptr && blink::cg_fits(r, g.kmax);
+        for (int k = g.first; k < g.first + g.count && cg_ok; ++k)
+            cg_ok = p->infos[size_t(dl[size_t(k)].chan)].csr_off >= 0;
+        g.cg_stride = cg_ok ? (blink::cg_cells(r, g.kmax) + 1) & ~int64_t(1) : 0;
+        if (cg_ok)
+            cg_need = std::max(cg_need, std::min(size_t(g.count), std::max<size_t>(1, kCgCap / size_t(8 * g.cg_stride))) *
+                                            size_t(8 * g.cg_stride));
     }
     // work queue of the persistent large-image kernel: sized for the largest
     // group, so every group (also one forced onto that path) can use it
@@ -429,6 +446,14 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
             return fail(ctx, BLINK_ERR_WORKSPACE, std::string("work-queue allocation: ") + cudaGetErrorString(e));
         p->d_queue = static_cast<int *>(q);
         p->queue_bytes = qb;
+    }
+    if (cg_need) {
+        void *c = nullptr;
+        e = cudaMallocFromPoolAsync(&c, cg_need, ctx->pool, st);
+        if (e != cudaSuccess)
+            return fail(ctx, BLINK_ERR_WORKSPACE, std::string("compact-grid allocation: ") + cudaGetErrorString(e));
+        p->d_cg = static_cast<float2 *>(c);
+        p->cg_bytes = cg_need;
     }
     if (scratch) {
         void *s = nullptr;
@@ -476,6 +501,11 @@ blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, con
     a.queue_bytes = p->queue_bytes;
     a.csr_bytes = p->csr_bytes;
     a.row_entries = g.row_entries;
+    if (g.cg_stride > 0 && p->d_cg) {
+        a.cg = p->d_cg;
+        a.cg_stride = g.cg_stride;
+        a.cg_cap = int(std::min<size_t>(size_t(g.count), p->cg_bytes / size_t(8 * g.cg_stride)));
+    }
     return a;
 }
 

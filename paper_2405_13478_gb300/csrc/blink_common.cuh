@@ -60,24 +60,46 @@ struct ChanInfo {
 // its first position), into ents_by_b; then by column inside every row --
 // so the entries of one cell are contiguous and in a fixed order, and the
 // gridding that sums them is deterministic.
+//
+// The same block also holds the chunk-sorted entries of the compact gridding
+// (k_grid_compact): the baselines in chunks of kCgChunk, and inside chunk q
+// its kept baselines ordered by compact cell, then baseline, one 32-bit word
+// each: cell << 12 | conj << 11 | (baseline - q kCgChunk), where the compact
+// cell of row r and column k_u is r (2 kmax + 1) + k_u + kmax (kmax: the
+// channel's largest |k_u|).  cg_ents[q][i], i < cg_cnt[q]; the rest of a
+// chunk's kCgChunk words are 0xFFFFFFFF.
 constexpr int kCsrBlock = 256;        // baselines per block of the bucket sort
 constexpr int kCsrMaxBuckets = 1024 / 2 + 1;  // largest supported n_px / 2 + 1
+constexpr int kCgChunk = 2048;        // baselines per chunk of the compact gridding
 struct CsrLayout {
-    int64_t row_ptr, tot, blk_off, ents_by_b, ents, bytes;
+    int64_t row_ptr, tot, blk_off, ents_by_b, ents, cg_ents, cg_cnt, bytes;
     int32_t n_blk, n_bkt;  // baseline blocks, buckets (n_px / 2 rows + dropped)
+    int32_t n_cg;          // chunks of the compact gridding
     __host__ __device__ CsrLayout(int n_px, int64_t nb) {
         auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
         n_bkt = n_px / 2 + 1;
         n_blk = int32_t((nb + kCsrBlock - 1) / kCsrBlock);
+        n_cg = int32_t((nb + kCgChunk - 1) / kCgChunk);
         int64_t o = 0;
         row_ptr = o; o = up(o + 4 * int64_t(n_bkt + 1));
         tot = o; o = up(o + 4 * int64_t(n_bkt));
         blk_off = o; o = up(o + 4 * int64_t(n_blk) * n_bkt);
         ents_by_b = o; o = up(o + 8 * nb);
         ents = o; o = up(o + 8 * nb);
+        cg_ents = o; o = up(o + 4 * int64_t(n_cg) * kCgChunk);
+        cg_cnt = o; o = up(o + 4 * int64_t(n_cg));
         bytes = o;
     }
 };
+
+// Compact grid of a large-image layer: its support rows r < R and columns
+// |k_u| <= kmax only, row-major [R][2 kmax + 1] (complex64), weighted and
+// with row 0 Hermitian-complete.  The group's layers take the compact
+// gridding when that grid, for the group's largest R and kmax, fits
+// kCgGridBytes (it is built in shared memory next to two staging chunks).
+constexpr size_t kCgGridBytes = 40 * 1024;
+__host__ __device__ inline int64_t cg_cells(int rows, int kmax) { return int64_t(rows) * (2 * kmax + 1); }
+__host__ __device__ inline bool cg_fits(int rows, int kmax) { return cg_cells(rows, kmax) * 8 <= int64_t(kCgGridBytes); }
 
 // Register-accumulation gridding schedule (one block per channel).
 //

@@ -1,0 +1,180 @@
+// blink_compact.cu -- compact gridding of large-image layers (Sec. 5.2.1
+// steps 2-3, and the weighting of Sec. 4.4.2).
+//
+// The support of a large image is often a small part of its grid: a station
+// imaged at 512^2 or 1024^2 with the cell size of its all-sky image touches
+// only rows r < R and columns |k_u| <= kmax.  Where that compact grid fits in
+// shared memory, one CTA per layer grids the whole layer there: the layer's
+// visibilities pass through shared memory in chunks of kCgChunk baselines
+// (coalesced 16-byte copies, two chunks in flight), and the chunk's entries,
+// sorted by cell at plan time (k_cg_sort), are summed by the block-wide
+// segmented scan of blink_grid_sorted.cuh -- every random read is a
+// shared-memory read, every cell gets one add per chunk, chunks in order, so
+// the result does not depend on timing.  The CTA then applies the weights,
+// completes row 0 with its Hermitian mirror and writes the compact grid; the
+// row items of the large-image path expand its rows, so they no longer gather
+// visibilities from global memory.
+#include "blink_common.cuh"
+#include "blink_grid_sorted.cuh"
+#include "blink_kernels.cuh"
+
+#include <algorithm>
+
+namespace blink {
+
+namespace {
+
+constexpr int kCgThreads = 256;
+static_assert(kCgThreads * kRowGridU == kCgChunk, "one segmented-scan pass per staging chunk");
+
+// Entries [8 tid, 8 tid + 8) of chunk q (n kept entries) into registers: the
+// cell as the scan key, the index in the chunk as `bl`.
+__device__ __forceinline__ void cg_load_ents(GridChunk &c, const uint32_t *__restrict__ e, int n, int tid) {
+    constexpr int U = kRowGridU;
+    constexpr uint32_t kPastEnd = 0xFFFFFFFFu, kBeforeStart = 0xFFFFFFFEu;  // never a cell
+    const int i0 = tid * U;
+    c.n = n;
+    c.conj = 0;
+    uint32_t w[U];
+    if (i0 < n) {  // the chunk's words are 16-byte aligned: two vector loads
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(e + i0));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(e + i0 + 4));
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+        w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const bool live = i0 + u < n;
+        c.key[u] = live ? w[u] >> 12 : kPastEnd;
+        c.bl[u] = w[u] & 0x7FFu;
+        c.conj |= (live && ((w[u] >> 11) & 1u)) ? (1u << u) : 0u;
+    }
+    c.kprev = (i0 > 0 && i0 <= n) ? __ldg(e + i0 - 1) >> 12 : kBeforeStart;
+    c.knext = i0 + U < n ? __ldg(e + i0 + U) >> 12 : kPastEnd;
+}
+
+// cp.async of baselines [b0, b0 + n) of a layer's visibilities into dst
+// (16-byte pieces when the source is 16-byte aligned), one commit group.
+__device__ __forceinline__ void cg_stage(float2 *dst, const float2 *src, int n, int tid, uint64_t pol) {
+    const uint32_t d = uint32_t(__cvta_generic_to_shared(dst));
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        for (int i = tid; i < n / 2; i += kCgThreads)
+            asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(d + 16 * i),
+                         "l"(src + 2 * i), "l"(pol)
+                         : "memory");
+        if ((n & 1) && tid == 0)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d + 8 * (n - 1)), "l"(src + n - 1)
+                         : "memory");
+    } else {
+        for (int i = tid; i < n; i += kCgThreads)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d + 8 * i), "l"(src + i) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// One CTA per layer l0 + blockIdx.x of a.layers; its compact grid goes to
+// a.cg + blockIdx.x * a.cg_stride.  Shared memory: the compact grid of the
+// group's largest support, then two staging chunks.
+__global__ void __launch_bounds__(kCgThreads, 3) k_grid_compact(ImageArgs a, int l0) {
+    extern __shared__ float2 sm[];
+    const int tid = threadIdx.x;
+    const DevLayer L = a.layers[l0 + blockIdx.x];
+    const ChanInfo ci = a.chans[L.chan];
+    const int N = ci.n_px, R = ci.rows, km = ci.kmax_u, kc = 2 * km + 1;
+    const int ncell = R * kc;
+    float2 *G = sm;
+    float2 *stg = sm + ((a.cg_stride + 1) & ~int64_t(1));  // 16-byte aligned
+    const CsrLayout cl(N, a.nb);
+    const uint32_t *ents = reinterpret_cast<const uint32_t *>(a.csr + ci.csr_off + cl.cg_ents);
+    const int32_t *cnt = reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.cg_cnt);
+    const float2 *vis = a.vis + L.vis_off;
+    const LayerGains gl = layer_gains(a, L);
+    const uint64_t pol = l2_evict_first();
+    const int Q = cl.n_cg;
+    auto chunk_n = [&](int q) { return int(a.nb - int64_t(q) * kCgChunk < kCgChunk ? a.nb - int64_t(q) * kCgChunk
+                                                                                   : int64_t(kCgChunk)); };
+    GridChunk cur;
+    if (Q > 0) {
+        cg_stage(stg, vis, chunk_n(0), tid, pol);
+        cg_load_ents(cur, ents, __ldg(cnt), tid);
+    }
+    for (int i = tid; i < ncell; i += kCgThreads) G[i] = make_float2(0.f, 0.f);
+    auto cell = [G](uint32_t key) { return G + key; };
+    for (int q = 0; q < Q; ++q) {
+        GridChunk nxt;
+        const bool more = q + 1 < Q;
+        if (more) {
+            // the other buffer was last read in chunk q - 1, before the
+            // barrier that ended its scan
+            cg_stage(stg + ((q + 1) & 1) * kCgChunk, vis + int64_t(q + 1) * kCgChunk, chunk_n(q + 1), tid, pol);
+            cg_load_ents(nxt, ents + int64_t(q + 1) * kCgChunk, __ldg(cnt + q + 1), tid);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();  // chunk q staged by every thread; the grid zeroed
+        const float2 *buf = stg + (q & 1) * kCgChunk;
+        float2 v[kRowGridU];
+        const int i0 = tid * kRowGridU;
+#pragma unroll
+        for (int u = 0; u < kRowGridU; ++u) {
+            v[u] = make_float2(0.f, 0.f);
+            if (i0 + u < cur.n) {
+                v[u] = buf[cur.bl[u]];
+                if (gl) v[u] = apply_gain(v[u], gl, int64_t(q) * kCgChunk + cur.bl[u]);
+                if ((cur.conj >> u) & 1u) v[u].y = -v[u].y;
+            }
+        }
+        grid_sum_chunk<kCgThreads>(cur, v, tid, cell);  // ends with a barrier
+        if (more) cur = nxt;
+    }
+    // weights (rows >= 1), then row 0: weight, origin 2 Re(V) w, mirror
+    // G[0][-k_u] = conj G[0][k_u] (row 0 was gridded at k_u >= 0 only)
+    const float *w = ci.weighting == 1 ? a.wgt + ci.wgt_off : nullptr;
+    if (w)
+        for (int i = kc + tid; i < ncell; i += kCgThreads) {
+            const int r = i / kc, ku = i % kc - km;
+            const float wv = w[r * N + (ku < 0 ? ku + N : ku)];
+            G[i].x *= wv;
+            G[i].y *= wv;
+        }
+    for (int ku = tid; ku <= km; ku += kCgThreads) {
+        const float wv = w ? w[ku] : 1.f;
+        const float2 g = G[km + ku];
+        if (ku == 0) {
+            G[km] = make_float2(2.f * g.x * wv, 0.f);
+        } else {
+            G[km + ku] = make_float2(g.x * wv, g.y * wv);
+            G[km - ku] = make_float2(g.x * wv, -g.y * wv);
+        }
+    }
+    __syncthreads();
+    float2 *dst = a.cg + int64_t(blockIdx.x) * a.cg_stride;
+    for (int i = tid; i < ncell; i += kCgThreads) dst[i] = G[i];
+}
+
+}  // namespace
+
+size_t grid_compact_smem(int64_t cg_stride) {
+    return size_t((cg_stride + 1) & ~int64_t(1)) * sizeof(float2) + 2 * size_t(kCgChunk) * sizeof(float2);
+}
+
+Error launch_grid_compact(const ImageArgs &a, int l0, int cnt, cudaStream_t st) {
+    if (cnt <= 0) return Error{0, ""};
+    if (!a.cg || !a.csr || cnt > a.cg_cap) return Error{-3, "compact gridding without its buffer or tables"};
+    const size_t smem = grid_compact_smem(a.cg_stride);
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_grid_compact, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    for (int k = 0; k < cnt; k += 1 << 30) {
+        const int c = std::min(cnt - k, 1 << 30);
+        ImageArgs b = a;
+        b.cg = a.cg + int64_t(k) * a.cg_stride;
+        k_grid_compact<<<unsigned(c), kCgThreads, smem, st>>>(b, l0 + k);
+        BLINK_CUDA_TRY(cudaGetLastError());
+    }
+    return Error{0, ""};
+}
+
+}  // namespace blink

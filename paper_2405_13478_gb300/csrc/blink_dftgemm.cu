@@ -372,6 +372,8 @@ struct Grid1Args {
     int64_t nb;
     int n_px, kmax, Kc;
     uint16_t *a_hi, *a_lo;  // [wave] blocks of 128 x 2 Kc (tiled)
+    const float2 *cg;       // compact grids of the wave's layers (k_grid_compact), or null
+    int64_t cg_stride;
 };
 
 // Grid: (bands of 8 rows, layers of the wave).  Compact gridding of rows
@@ -393,7 +395,18 @@ __global__ void __launch_bounds__(256) k_grid_a1(Grid1Args g, int l0, int pack) 
         for (int i = tid; i < 8 * Kc; i += nt) gc[i] = make_float2(0.f, 0.f);
     };
     const float2 *vis = g.vis + L.vis_off;
-    if (nrows == 0) {
+    if (g.cg) {
+        // the layer's compact grid, already weighted and complete: copy the
+        // band's rows (its columns |k_u| <= kmax of the channel)
+        const int km = ci.kmax_u, kc = 2 * km + 1;
+        const float2 *src = g.cg + int64_t(lw) * g.cg_stride + int64_t(r0) * kc;
+        zero();
+        __syncthreads();
+        for (int i = tid; i < nrows * kc; i += nt) {
+            const int r = i / kc, c = i % kc;
+            gc[r * Kc + (c - km + kmax)] = __ldcs(src + i);
+        }
+    } else if (nrows == 0) {
         // nothing to grid: the rows below are written as zeros
         zero();
         __syncthreads();
@@ -427,7 +440,7 @@ __global__ void __launch_bounds__(256) k_grid_a1(Grid1Args g, int l0, int pack) 
         }
     }
     __syncthreads();
-    const float *w = ci.weighting == 1 ? g.wgt + ci.wgt_off : nullptr;
+    const float *w = ci.weighting == 1 && !g.cg ? g.wgt + ci.wgt_off : nullptr;
     if (w)
         for (int i = tid; i < nrows * Kc; i += nt) {
             const int r = i / Kc, kk = i % Kc, ku = kk - kmax;
@@ -439,7 +452,7 @@ __global__ void __launch_bounds__(256) k_grid_a1(Grid1Args g, int l0, int pack) 
     __syncthreads();
     // row 0: k_u >= 0 was gridded; weight it and mirror the conjugate to -k_u;
     // the origin carries V and conj V of its baselines: 2 Re * w
-    if (r0 == 0)
+    if (r0 == 0 && !g.cg)
         for (int ku = tid; ku <= kmax; ku += nt) {
             const float wv = w ? w[ku] : 1.f;
             const float2 v = gc[kmax + ku];
@@ -629,7 +642,8 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
         const size_t fixed1 = 2 * a_elems * 2 + 2 * b1_elems * 2 + 512;
         const size_t per1 = 2 * a1_elems * 2 + 2 * b_elems * 2;
         if (a.scratch_bytes < fixed1 + per1) return Error{-5, "tensor-core transform scratch too small"};
-        const int wave1 = int(std::min<size_t>(size_t(a.n_layers), std::min<size_t>(65535, (a.scratch_bytes - fixed1) / per1)));
+        int wave1 = int(std::min<size_t>(size_t(a.n_layers), std::min<size_t>(65535, (a.scratch_bytes - fixed1) / per1)));
+        if (a.cg) wave1 = std::min(wave1, a.cg_cap);
         uint16_t *b1_hi = a_lo + a_elems, *b1_lo = b1_hi + b1_elems;
         unsigned char *wb = base + ((fixed1 + 255) / 256) * 256;
         uint16_t *a1_hi = reinterpret_cast<uint16_t *>(wb), *a1_lo = a1_hi + size_t(wave1) * a1_elems;
@@ -651,7 +665,12 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
                 BLINK_CUDA_TRY(cudaMemsetAsync(a1_hi + size_t(cnt / 2) * a1_elems, 0, a1_elems * sizeof(uint16_t), st));
                 BLINK_CUDA_TRY(cudaMemsetAsync(a1_lo + size_t(cnt / 2) * a1_elems, 0, a1_elems * sizeof(uint16_t), st));
             }
-            Grid1Args g1{a.vis, a.layers, a.chans, a.codes, a.wgt, a.csr, a.nb, N, a.kmax, Kc, a1_hi, a1_lo};
+            if (a.cg) {
+                Error e = launch_grid_compact(a, l0, cnt, st);
+                if (e.status) return e;
+            }
+            Grid1Args g1{a.vis, a.layers, a.chans, a.codes, a.wgt, a.csr, a.nb, N, a.kmax, Kc, a1_hi, a1_lo,
+                         a.cg, a.cg_stride};
             k_grid_a1<<<dim3(unsigned((a.r_alloc + 7) / 8), unsigned(cnt)), 256, smem_g, st>>>(g1, l0, pack);
             BLINK_CUDA_TRY(cudaGetLastError());
             Gemm1Args d1{a1_hi, a1_lo, b1_hi, b1_lo, t_hi, t_lo, a.layers, a.chans, N, K1, Rp, a.status, wns};
@@ -669,11 +688,17 @@ Error run_mode(int N, const ImageArgs &a, int Rp, cudaStream_t st) {
     k_dft_table<FP16><<<256, 256, 0, st>>>(N, Rp, a_hi, a_lo);
     BLINK_CUDA_TRY(cudaGetLastError());
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_dftgemm<FP16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    for (int l0 = 0; l0 < a.n_layers; l0 += wave) {
-        const int cnt = std::min(wave, a.n_layers - l0);
+    const int wave_r = a.cg ? std::min(wave, a.cg_cap) : wave;
+    for (int l0 = 0; l0 < a.n_layers; l0 += wave_r) {
+        const int cnt = std::min(wave_r, a.n_layers - l0);
         ImageArgs ra = a;
         ra.scratch = T;
         ra.scratch_bytes = size_t(wave) * t_bytes;
+        if (ra.cg) {
+            Error e = launch_grid_compact(ra, l0, cnt, st);
+            if (e.status) return e;
+            ra.cg_l0 = l0;
+        }
         Error e = launch_rows_wave(N, ra, l0, cnt, st);
         if (e.status) return e;
         k_split<FP16, SPLIT><<<cnt, 256, 0, st>>>(T, a.r_alloc, N, Rp, a.layers, a.chans, l0, b_hi, b_lo, b_exp);

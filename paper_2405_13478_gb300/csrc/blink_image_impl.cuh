@@ -312,8 +312,8 @@ struct RowsCfg {
 // the channel's support R): gridding, weights, Hermitian completion of row 0,
 // the row transforms, written in natural column order to dst[r - r0][p].
 template <int N>
-__device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L, const ChanInfo &ci, int r0,
-                                          int nrows, float2 *__restrict__ dst, float2 *sm, int tid) {
+__device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L, const ChanInfo &ci, int lidx,
+                                          int r0, int nrows, float2 *__restrict__ dst, float2 *sm, int tid) {
     using C = RowsCfg<N>;
     constexpr int NT = C::NT, S = C::S;
     __builtin_assume(nrows >= 1 && nrows <= C::RB);
@@ -322,23 +322,36 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
         stage_four_step<N>(tw, tid, NT);
         for (int i = tid; i < nrows * S; i += NT) sm[i] = make_float2(0.f, 0.f);
     };
-    const LayerGains gl = layer_gains(a, L);
-    if (a.csr && ci.csr_off >= 0) {
-        const CsrLayout cl(N, a.nb);
-        auto cell = [sm](uint32_t key) { return sm + int(key >> 16) * S + RowLayout<N>::phys(int(key & 0xFFFFu)); };
-        grid_band_sorted<NT>(r0, nrows, reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr),
-                             reinterpret_cast<const uint2 *>(a.csr + ci.csr_off + cl.ents), a.vis + L.vis_off, gl,
-                             tid, cell, prologue);
-    } else {
-        // a channel without row buckets (its support always fits the fused
-        // kernel; it comes here only when the two-kernel path is forced):
-        // shared-memory atomics over the whole code table
+    if (a.cg) {
+        // the layer's compact grid (weighted, row 0 complete): expand the
+        // band's rows, columns |k_u| <= kmax, into FFT order
+        const int km = ci.kmax_u, kc = 2 * km + 1;
+        const float2 *cg = a.cg + int64_t(lidx - a.cg_l0) * a.cg_stride + int64_t(r0) * kc;
         prologue();
         __syncthreads();
-        grid_rows<NT, N>(sm, S, r0, nrows, a.codes + ci.code_off, a.vis + L.vis_off, a.nb, tid, gl);
-        __syncthreads();
+        for (int i = tid; i < nrows * kc; i += NT) {
+            const int r = i / kc, ku = i % kc - km;
+            sm[r * S + RowLayout<N>::phys(ku < 0 ? ku + N : ku)] = __ldcs(cg + i);
+        }
+    } else {
+        const LayerGains gl = layer_gains(a, L);
+        if (a.csr && ci.csr_off >= 0) {
+            const CsrLayout cl(N, a.nb);
+            auto cell = [sm](uint32_t key) { return sm + int(key >> 16) * S + RowLayout<N>::phys(int(key & 0xFFFFu)); };
+            grid_band_sorted<NT>(r0, nrows, reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr),
+                                 reinterpret_cast<const uint2 *>(a.csr + ci.csr_off + cl.ents), a.vis + L.vis_off, gl,
+                                 tid, cell, prologue);
+        } else {
+            // a channel without row buckets (its support always fits the fused
+            // kernel; it comes here only when the two-kernel path is forced):
+            // shared-memory atomics over the whole code table
+            prologue();
+            __syncthreads();
+            grid_rows<NT, N>(sm, S, r0, nrows, a.codes + ci.code_off, a.vis + L.vis_off, a.nb, tid, gl);
+            __syncthreads();
+        }
+        weight_and_complete<N, true>(sm, S, r0, r0 + nrows, ci, a.wgt, tid, NT);
     }
-    weight_and_complete<N, true>(sm, S, r0, r0 + nrows, ci, a.wgt, tid, NT);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table in place
     __syncthreads();
     rows_fft<N, +1, true>(sm, S, nrows, tid, NT, tw);
@@ -359,8 +372,8 @@ __global__ void __launch_bounds__(RowsCfg<N>::NT, Plan<N>::N1 == 24 ? 2 : 3) k_r
     const ChanInfo ci = a.chans[L.chan];
     const int r0 = blockIdx.x * RowsCfg<N>::RB;
     if (r0 >= ci.rows) return;
-    rows_item<N>(a, L, ci, r0, min(RowsCfg<N>::RB, ci.rows - r0), a.scratch + (int64_t(lw) * a.r_alloc + r0) * N, sm,
-                 threadIdx.x);
+    rows_item<N>(a, L, ci, l0 + lw, r0, min(RowsCfg<N>::RB, ci.rows - r0),
+                 a.scratch + (int64_t(lw) * a.r_alloc + r0) * N, sm, threadIdx.x);
 }
 
 // The column pass can stage its scratch columns through shared memory when
@@ -588,7 +601,7 @@ __global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
                 // row buckets of the layer about one grid of items ahead (with
                 // many channels the buckets do not stay in L2 between a
                 // channel's time steps)
-                if (sub == 0) {
+                if (sub == 0 && !a.cg) {
                     prefetch_l2_bytes(a.vis + L.vis_off, 8 * a.nb, tid, 256);
                     const int la = layer + q.ahead;
                     if (q.ahead > 0 && a.csr && la < q.n) {
@@ -602,7 +615,7 @@ __global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
                 }
                 const int r0 = sub * q.rb;
                 const int nrows = min(RowsCfg<N>::RB, min(q.rb, ci.rows - r0));
-                if (r0 < ci.rows) rows_item<N>(a, L, ci, r0, nrows, Hs + int64_t(r0) * N, sm, tid);
+                if (r0 < ci.rows) rows_item<N>(a, L, ci, layer, r0, nrows, Hs + int64_t(r0) * N, sm, tid);
                 __syncthreads();  // every thread's scratch stores precede the release below
                 if (tid == 0) {
                     __threadfence();
@@ -853,8 +866,10 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     q.n = a.n_layers;
     // band height: at most RB rows, and about kBandEntries gridding entries
     // per row item, so a dense band does not hold up its layer's column items
+    // (row items that read compact grids gather nothing: full bands)
     constexpr int kBandEntries = 4096;
-    q.rb = a.row_entries > 0 ? std::max(1, std::min(RowsCfg<N>::RB, kBandEntries / a.row_entries)) : RowsCfg<N>::RB;
+    q.rb = a.row_entries > 0 && !a.cg ? std::max(1, std::min(RowsCfg<N>::RB, kBandEntries / a.row_entries))
+                                      : RowsCfg<N>::RB;
     q.nR = (a.r_alloc + q.rb - 1) / q.rb;
     q.nC = (N / 2 + LargeCfg<N>::P - 1) / LargeCfg<N>::P;
     q.total = int64_t(q.n) * (q.nR + q.nC);
@@ -878,7 +893,7 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     const int lag_want = int(8 * grid / int64_t(q.nR + q.nC)) + 1;
     q.lag = std::max(0, std::min({lag_want, q.slots / 2, q.n}));
     // look-ahead prefetch of row buckets: only when they do not all stay in L2
-    q.ahead = a.csr_bytes > (size_t(32) << 20)
+    q.ahead = a.csr_bytes > (size_t(32) << 20) && !a.cg
                   ? int(std::min<int64_t>(64, std::max<int64_t>(1, grid / int64_t(q.nR + q.nC))))
                   : 0;
     BLINK_CUDA_TRY(cudaMemsetAsync(a.queue, 0, image_queue_bytes(q.n), st));
@@ -887,17 +902,11 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     return Error{0, ""};
 }
 
+// The large-image path of a group (or of one wave of compact grids).
 template <int N>
-Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
-    if (a.n_layers == 0) return Error{0, ""};
-    {
-        Error e;
-        if (launch_fused_n<N>(a, st, e)) return e;
-    }
+Error launch_large_body(const ImageArgs &a, cudaStream_t st) {
     using C = LargeCfg<N>;
     const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
-    if (!a.scratch || a.scratch_bytes < per_layer)
-        return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
     if (a.force_path != 4 && a.queue && a.queue_bytes >= image_queue_bytes(a.n_layers))
         return launch_large_n<N>(a, st);
     // wave path (no work queue, or chosen by the autotuner): pass 1 of a wave
@@ -917,6 +926,32 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
         BLINK_CUDA_TRY(cudaGetLastError());
         cols<<<dim3(pchunks, unsigned(cnt)), C::NT, smem_cols, st>>>(a, l0, static_cast<float *>(a.out), a.ref);
         BLINK_CUDA_TRY(cudaGetLastError());
+    }
+    return Error{0, ""};
+}
+
+template <int N>
+Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
+    if (a.n_layers == 0) return Error{0, ""};
+    {
+        Error e;
+        if (launch_fused_n<N>(a, st, e)) return e;
+    }
+    const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
+    if (!a.scratch || a.scratch_bytes < per_layer)
+        return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
+    if (!a.cg) return launch_large_body<N>(a, st);
+    // compact gridding, one wave of the compact-grid buffer at a time, each
+    // wave followed by its rows and columns
+    for (int l0 = 0; l0 < a.n_layers; l0 += a.cg_cap) {
+        ImageArgs b = a;
+        b.layers = a.layers + l0;
+        b.n_layers = std::min(a.cg_cap, a.n_layers - l0);
+        b.cg_l0 = 0;
+        Error e = launch_grid_compact(b, 0, b.n_layers, st);
+        if (e.status) return e;
+        e = launch_large_body<N>(b, st);
+        if (e.status) return e;
     }
     return Error{0, ""};
 }

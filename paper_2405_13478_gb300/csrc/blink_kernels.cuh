@@ -63,7 +63,21 @@ struct ImageArgs {
                                 // for them only when they cannot all stay in L2)
     int row_entries = 0;        // largest kept baselines per support row among the group's
                                 // channels (sets the band height of large-image row items)
+    // compact grids of large-image layers (k_grid_compact): when set, the row
+    // items read their rows from cg instead of gathering visibilities.  cg
+    // holds cg_cap layers of cg_stride complex elements; slot s is layer
+    // cg_l0 + s of `layers` (the launchers fill it wave by wave)
+    float2 *cg = nullptr;
+    int64_t cg_stride = 0;
+    int cg_cap = 0;
+    int cg_l0 = 0;
 };
+
+// Compact gridding (blink_compact.cu) of layers [l0, l0 + cnt) of a.layers
+// into a.cg slots 0 .. cnt - 1 (cnt <= a.cg_cap; the group's channels need
+// row buckets and cg_fits), and the shared memory it takes.
+Error launch_grid_compact(const ImageArgs &a, int l0, int cnt, cudaStream_t st);
+size_t grid_compact_smem(int64_t cg_stride);
 
 // Device words the persistent large-image kernel needs for a group of
 // n_layers layers (its work queue and per-layer counters).

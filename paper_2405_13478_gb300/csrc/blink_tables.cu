@@ -693,6 +693,64 @@ __global__ void __launch_bounds__(256) k_csr_sort(const ChanInfo *__restrict__ i
     }
 }
 
+// Compact gridding tables: one CTA per chunk of kCgChunk baselines of a
+// channel with row buckets.  Every kept baseline of the chunk becomes the key
+// cell << 12 | conj << 11 | (index in the chunk), unique inside the chunk; a
+// bitonic sort in shared memory orders them by cell, then baseline (dropped
+// baselines sort last as 0xFFFFFFFF).  Grid: (chunks, channels) x 256.
+__global__ void __launch_bounds__(256) k_cg_sort(const ChanInfo *__restrict__ info,
+                                                 const uint32_t *__restrict__ codes,
+                                                 unsigned char *__restrict__ csr, int64_t nb) {
+    constexpr int NT = 256;
+    __shared__ uint32_t key[kCgChunk];
+    __shared__ int s_cnt;
+    const ChanInfo ci = info[blockIdx.y];
+    if (ci.csr_off < 0) return;
+    const CsrLayout cl(ci.n_px, nb);
+    const int q = blockIdx.x;
+    if (q >= cl.n_cg) return;
+    const int64_t b0 = int64_t(q) * kCgChunk;
+    const int n = int(nb - b0 < kCgChunk ? nb - b0 : int64_t(kCgChunk));
+    const int N = ci.n_px, km = ci.kmax_u, kc = 2 * km + 1;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    int cnt = 0;
+    for (int i = threadIdx.x; i < kCgChunk; i += NT) {
+        uint32_t k = 0xFFFFFFFFu;
+        if (i < n) {
+            const uint32_t code = codes[ci.code_off + b0 + i];
+            if (code != kCodeDropped) {
+                const int c = int(code_col(code)), ku = c <= N / 2 ? c : c - N;
+                if (ku >= -km && ku <= km) {
+                    const uint32_t cell = uint32_t(int(code_row(code)) * kc + ku + km);
+                    k = (cell << 12) | (code_conj(code) << 11) | uint32_t(i);
+                    ++cnt;
+                }
+            }
+        }
+        key[i] = k;
+    }
+    cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    for (int k = 2; k <= kCgChunk; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < kCgChunk / 2; t += NT) {
+                const int i = 2 * t - (t & (j - 1)), l = i + j;  // i has bit j clear
+                const uint32_t x = key[i], y = key[l];
+                if ((x > y) == ((i & k) == 0)) {
+                    key[i] = y;
+                    key[l] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    uint32_t *dst = reinterpret_cast<uint32_t *>(csr + ci.csr_off + cl.cg_ents) + int64_t(q) * kCgChunk;
+    for (int i = threadIdx.x; i < kCgChunk; i += NT) dst[i] = key[i];
+    if (threadIdx.x == 0) reinterpret_cast<int32_t *>(csr + ci.csr_off + cl.cg_cnt)[q] = s_cnt;
+}
+
 // Per-layer copy of the per-channel signed cells (blink_cells).
 __global__ void k_expand_cells(const int2 *__restrict__ cells, const DevLayer *__restrict__ layers,
                                int n_layers, int64_t nb, int2 *__restrict__ out) {
@@ -750,6 +808,9 @@ Error launch_tables(const double *ant_xyz, int n_ant, int64_t nb, int n_chan, co
             info, codes, csr, nb);
         BLINK_CUDA_TRY(cudaGetLastError());
         k_csr_sort<<<dim3(unsigned((kCsrMaxBuckets + 7) / 8), unsigned(n_chan)), 256, 0, st>>>(info, csr, nb);
+        BLINK_CUDA_TRY(cudaGetLastError());
+        k_cg_sort<<<dim3(unsigned((nb + kCgChunk - 1) / kCgChunk), unsigned(n_chan)), 256, 0, st>>>(info, codes, csr,
+                                                                                                  nb);
         BLINK_CUDA_TRY(cudaGetLastError());
     }
     k_finalize<<<n_chan, 512, 0, st>>>(info, wgt);

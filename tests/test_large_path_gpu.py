@@ -183,3 +183,81 @@ def test_dependency_wait_timeout_is_reported_and_the_plan_recovers(torch, ctx):
     torch.cuda.synchronize()
     check_against_oracle(ws, layers, vis, out, [0, 7])
     plan.close()
+
+
+def _station_layers(ws, times, chans, weighting, shift=0):
+    B = ws.n_baselines
+    layers = []
+    for t in range(len(times)):
+        for k, c in enumerate(chans):
+            layers.append(dict(n_px=int(ws.n_px[c]), weighting=weighting, freq_hz=float(ws.freqs_hz[c]),
+                               delta_u=float(ws.delta_u[c]), vis_offset=(t * len(chans) + k) * B + shift))
+    return layers
+
+
+@pytest.mark.parametrize("weighting,shift", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_compact_gridding_matches_oracle(torch, ctx, weighting, shift):
+    # station layers at 512^2 and 1024^2: their support (about 46 rows by 91
+    # columns) takes the compact gridding -- whole layer per CTA, visibilities
+    # staged in 2048-baseline chunks (32640 = 15 x 2048 + 1920: a ragged last
+    # chunk), 8-byte staging copies when the layer's visibilities are not
+    # 16-byte aligned (shift = 1), uniform weights applied on the compact grid
+    from paper_2405_13478_gb300 import binding
+    w512 = synth.station_512(seed=31, n_times=2)
+    w1k = synth.station_gains(seed=31, n_times=2)  # same seed: the same antennas
+    B = w512.n_baselines
+    l512 = _station_layers(w512, [0, 1], [0, 9], weighting, shift)
+    l1k = _station_layers(w1k, [0, 1], [2, 7], weighting, shift)
+    for L in l1k:
+        L["vis_offset"] += len(l512) * B
+    layers, total = binding.layer_out_offsets(l512 + l1k)
+    v = torch.cat([torch.zeros(shift, dtype=torch.complex64),
+                   w512.vis("cpu", times=[0, 1])[:, [0, 9], :].reshape(-1),
+                   w1k.vis("cpu", times=[0, 1])[:, [2, 7], :].reshape(-1)])
+    out = torch.full((total,), float("nan"), device="cuda")
+    d_v = v.cuda()
+    ctx.image_batch(torch.as_tensor(w512.ant_xyz).cuda(), layers, d_v, out)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.as_tensor(w512.ant_xyz), torch.as_tensor(w1k.ant_xyz))
+    flat = v.numpy()
+    for k in range(len(layers)):
+        L = layers[k]
+        one = [dict(L, vis_offset=0)]
+        want, _ = oracle.image_batch(w512.ant_xyz, one, flat[L["vis_offset"]:L["vis_offset"] + B], "fft")
+        n = L["n_px"]
+        g = out[L["out_offset"]:L["out_offset"] + n * n].cpu().numpy().reshape(n, n)
+        err = np.abs(g.astype(np.float64) - want[0]).max()
+        assert err <= IMG_TOL * np.abs(want[0]).max(), f"layer {k}: err {err:.3e}"
+
+
+def test_compact_grid_waves_and_paths_agree(torch, ctx):
+    # 4112 layers of 512^2: more than one wave of the 128 MB compact-grid
+    # buffer (about 4000 station grids), so the compact gridding and the
+    # large path run twice; the waves of two kernels (path 4) read the same
+    # compact grids and must give the same bits
+    from paper_2405_13478_gb300 import binding
+    ws = synth.station_512(seed=33, n_times=257)
+    B = ws.n_baselines
+    layers = _station_layers(ws, list(range(257)), list(range(16)), 0)
+    layers, total = binding.layer_out_offsets(layers)
+    d_vis = ws.vis("cuda").reshape(-1)
+    d_xyz = torch.as_tensor(ws.ant_xyz).cuda()
+    plan = ctx.plan(d_xyz, layers)
+    a = torch.full((total,), float("nan"), device="cuda")
+    plan.image(d_vis, a)
+    plan.check()
+    plan.set_tuning(0, 4, 0)
+    b = torch.full((total,), float("nan"), device="cuda")
+    plan.image(d_vis, b)
+    plan.check()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    picks = [0, 3999, 4000, 4001, 4111]
+    sub = [dict(layers[k], vis_offset=i * B) for i, k in enumerate(picks)]
+    v = torch.cat([d_vis[layers[k]["vis_offset"]:layers[k]["vis_offset"] + B] for k in picks]).cpu().numpy()
+    want, _ = oracle.image_batch(ws.ant_xyz, sub, v, "fft")
+    for k, w in zip(picks, want):
+        g = a[layers[k]["out_offset"]:layers[k]["out_offset"] + 512 * 512].cpu().numpy().reshape(512, 512)
+        err = np.abs(g.astype(np.float64) - w).max()
+        assert err <= IMG_TOL * np.abs(w).max(), f"layer {k}: err {err:.3e}"
+    plan.close()
