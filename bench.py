@@ -843,11 +843,26 @@ def measure_gains(torch, binding, ctx, n_t, steps, warmup):
     g0 = torch.as_tensor(ws.gains.astype(np.complex64)).cuda()
     box = {}
 
+    class SquaredError(torch.autograd.Function):
+        """sum (image - model image)^2 with one residual pass, a dot product
+        and one in-place scaling for the gradient 2 (image - model image)."""
+
+        @staticmethod
+        def forward(fctx, x, y):
+            r = x - y
+            fctx.save_for_backward(r)
+            return torch.dot(r, r)
+
+        @staticmethod
+        def backward(fctx, gout):
+            (r,) = fctx.saved_tensors
+            return r.mul_(2.0 * gout), None
+
     def step():
         g = g0.clone().requires_grad_(True)
         vis = autograd.apply_gains(g, model, ctx, n_ant, layers)
         img = autograd.dirty_images(vis, plan, total)
-        loss = ((img - target) ** 2).sum()
+        loss = SquaredError.apply(img, target)
         loss.backward()
         box["vis"], box["img"] = vis, img
         return g.grad

@@ -142,8 +142,12 @@ BLINK_API int blink_grid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, con
  * same bits on every call: every cell sums its visibilities in an order fixed
  * by the array geometry, without atomics (the fused small-image kernel by its
  * per-channel register schedule, the large-image row pass by its sorted row
- * buckets).  Large images run as one persistent launch per image size whose
- * CTAs take row and column work items from a device queue.
+ * buckets, or -- when a group's support fits 40 KB as a compact grid of rows
+ * r < R and columns |k_u| <= kmax -- by one CTA per layer summing per-chunk
+ * cell-sorted entries in shared memory).  Large images run as one persistent
+ * launch per image size whose CTAs take row and column work items from a
+ * device queue; groups with compact grids run the same row and column passes
+ * as waves of two kernels after the compact gridding.
  * This call builds the per-channel tables on `stream` and synchronises that
  * stream once to size the image kernels; use a plan (below) to build the
  * tables once and image many batches asynchronously. */
@@ -176,9 +180,10 @@ BLINK_API int blink_apply_gains(blink_ctx *ctx, int n_ant, const blink_layer *h_
 /* Chain rule of blink_degrid's output to the gains, summed over all layers:
  * d_dgains[i] = sum_l [ sum_{j>i} d_dvis(ij) g_j conj(M_ij)
  *                     + sum_{k<i} conj(d_dvis(ki)) g_k M_ki ]
- * (dL/dRe g + i dL/dIm g), overwrites d_dgains.  Products in FP32, sums in
- * FP64 in a fixed order (the same bits from run to run); every baseline is
- * read once, row by row of the upper triangle.  At most 1024 antennas
+ * (dL/dRe g + i dL/dIm g), overwrites d_dgains.  Products in FP32; each
+ * thread's sums compensated FP32 (Kahan), their reduction FP64, all in a
+ * fixed order (the same bits from run to run); every baseline is read once,
+ * row by row of the upper triangle.  At most 1024 antennas
  * (BLINK_ERR_UNSUPPORTED above). */
 BLINK_API int blink_gain_grad(blink_ctx *ctx, int n_ant, const blink_layer *h_layers, int n_layers,
                               const float *d_dvis, const float *d_model, const float *d_gains, float *d_dgains,

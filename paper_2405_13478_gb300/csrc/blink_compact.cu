@@ -7,10 +7,10 @@
 // shared memory, one CTA per layer grids the whole layer there: the layer's
 // visibilities pass through shared memory in chunks of kCgChunk baselines
 // (coalesced 16-byte copies, two chunks in flight), and the chunk's entries,
-// sorted by cell at plan time (k_cg_sort), are summed by the block-wide
-// segmented scan of blink_grid_sorted.cuh -- every random read is a
-// shared-memory read, every cell gets one add per chunk, chunks in order, so
-// the result does not depend on timing.  The CTA then applies the weights,
+// sorted by cell at plan time (k_cg_sort), are summed run by run, each run
+// (cell) by one thread in entry order -- every random read is a shared-memory
+// read, every cell gets one add per chunk, chunks in order, so the result
+// does not depend on timing.  The CTA then applies the weights,
 // completes row 0 with its Hermitian mirror and writes the compact grid; the
 // row items of the large-image path expand its rows, so they no longer gather
 // visibilities from global memory.
@@ -25,35 +25,32 @@ namespace blink {
 namespace {
 
 constexpr int kCgThreads = 256;
-static_assert(kCgThreads * kRowGridU == kCgChunk, "one segmented-scan pass per staging chunk");
+static_assert(kCgThreads * kRowGridU == kCgChunk, "eight entries per thread cover a staging chunk");
 
-// Entries [8 tid, 8 tid + 8) of chunk q (n kept entries) into registers: the
-// cell as the scan key, the index in the chunk as `bl`.
-__device__ __forceinline__ void cg_load_ents(GridChunk &c, const uint32_t *__restrict__ e, int n, int tid) {
+// Entries [8 tid, 8 tid + 8) of a chunk with n kept entries, as packed words
+// (cell << 12 | conj << 11 | index in the chunk), and the cells of the entries
+// just before and after them.
+struct CgChunk {
+    uint32_t w[kRowGridU];
+    uint32_t kprev, knext;  // cells of entries 8 tid - 1 and 8 tid + 8 (sentinels outside)
+    int n;
+};
+
+__device__ __forceinline__ void cg_load_ents(CgChunk &c, const uint32_t *__restrict__ e, int n, int tid) {
     constexpr int U = kRowGridU;
-    constexpr uint32_t kPastEnd = 0xFFFFFFFFu, kBeforeStart = 0xFFFFFFFEu;  // never a cell
     const int i0 = tid * U;
     c.n = n;
-    c.conj = 0;
-    uint32_t w[U];
     if (i0 < n) {  // the chunk's words are 16-byte aligned: two vector loads
         const uint4 a = __ldg(reinterpret_cast<const uint4 *>(e + i0));
         const uint4 b = __ldg(reinterpret_cast<const uint4 *>(e + i0 + 4));
-        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-        w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+        c.w[0] = a.x; c.w[1] = a.y; c.w[2] = a.z; c.w[3] = a.w;
+        c.w[4] = b.x; c.w[5] = b.y; c.w[6] = b.z; c.w[7] = b.w;
     } else {
 #pragma unroll
-        for (int u = 0; u < U; ++u) w[u] = 0xFFFFFFFFu;
+        for (int u = 0; u < U; ++u) c.w[u] = 0xFFFFFFFFu;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const bool live = i0 + u < n;
-        c.key[u] = live ? w[u] >> 12 : kPastEnd;
-        c.bl[u] = w[u] & 0x7FFu;
-        c.conj |= (live && ((w[u] >> 11) & 1u)) ? (1u << u) : 0u;
-    }
-    c.kprev = (i0 > 0 && i0 <= n) ? __ldg(e + i0 - 1) >> 12 : kBeforeStart;
-    c.knext = i0 + U < n ? __ldg(e + i0 + U) >> 12 : kPastEnd;
+    c.kprev = (i0 > 0 && i0 <= n) ? __ldg(e + i0 - 1) >> 12 : 0xFFFFFFFEu;  // never a cell
+    c.knext = i0 + U < n ? __ldg(e + i0 + U) >> 12 : 0xFFFFFFFFu;
 }
 
 // cp.async of baselines [b0, b0 + n) of a layer's visibilities into dst
@@ -73,6 +70,60 @@ __device__ __forceinline__ void cg_stage(float2 *dst, const float2 *src, int n, 
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d + 8 * i), "l"(src + i) : "memory");
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Sums of one chunk.  The entries are sorted by cell, so each cell is one run;
+// the thread whose window [8 tid, 8 tid + 8) holds a run's first entry sums
+// the whole run in order -- past the window's end when the run goes on -- and
+// adds it to the cell.  A cell therefore has one writer per chunk and one
+// fixed summation order: no scan, no atomics.  buf holds the chunk's staged
+// visibilities (baselines b0 ..).
+__device__ __forceinline__ void cg_sum_chunk(float2 *G, const CgChunk &c, const uint32_t *__restrict__ e,
+                                             const float2 *buf, int64_t b0, const LayerGains &gl, int tid) {
+    constexpr int U = kRowGridU;
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
+    const int i0 = tid * U;
+    if (i0 >= c.n) return;
+    auto value = [&](uint32_t w) {
+        float2 x = buf[w & 0x7FFu];
+        if (gl) x = apply_gain(x, gl, b0 + (w & 0x7FFu));
+        if ((w >> 11) & 1u) x.y = -x.y;
+        return x;
+    };
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = i0 + u < c.n ? value(c.w[u]) : make_float2(0.f, 0.f);
+    uint32_t cur = kNone;
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t k = c.w[u] >> 12;
+        if (i0 + u < c.n && k != c.kprev) {  // leading entries equal to kprev continue an earlier run
+            if (k == cur) {
+                s.x += v[u].x;
+                s.y += v[u].y;
+            } else {
+                if (cur != kNone) {
+                    G[cur].x += s.x;
+                    G[cur].y += s.y;
+                }
+                cur = k;
+                s = v[u];
+            }
+        }
+    }
+    if (cur == kNone) return;
+    if (c.knext == cur) {  // the last run goes on past the window
+        for (int j = i0 + U; j < c.n; ++j) {
+            const uint32_t w = __ldg(e + j);
+            if ((w >> 12) != cur) break;
+            const float2 x = value(w);
+            s.x += x.x;
+            s.y += x.y;
+        }
+    }
+    G[cur].x += s.x;
+    G[cur].y += s.y;
 }
 
 // One CTA per layer l0 + blockIdx.x of a.layers; its compact grid goes to
@@ -96,19 +147,18 @@ __global__ void __launch_bounds__(kCgThreads, 3) k_grid_compact(ImageArgs a, int
     const int Q = cl.n_cg;
     auto chunk_n = [&](int q) { return int(a.nb - int64_t(q) * kCgChunk < kCgChunk ? a.nb - int64_t(q) * kCgChunk
                                                                                    : int64_t(kCgChunk)); };
-    GridChunk cur;
+    CgChunk cur;
     if (Q > 0) {
         cg_stage(stg, vis, chunk_n(0), tid, pol);
         cg_load_ents(cur, ents, __ldg(cnt), tid);
     }
     for (int i = tid; i < ncell; i += kCgThreads) G[i] = make_float2(0.f, 0.f);
-    auto cell = [G](uint32_t key) { return G + key; };
     for (int q = 0; q < Q; ++q) {
-        GridChunk nxt;
+        CgChunk nxt;
         const bool more = q + 1 < Q;
         if (more) {
             // the other buffer was last read in chunk q - 1, before the
-            // barrier that ended its scan
+            // barrier that ended its sums
             cg_stage(stg + ((q + 1) & 1) * kCgChunk, vis + int64_t(q + 1) * kCgChunk, chunk_n(q + 1), tid, pol);
             cg_load_ents(nxt, ents + int64_t(q + 1) * kCgChunk, __ldg(cnt + q + 1), tid);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
@@ -117,18 +167,8 @@ __global__ void __launch_bounds__(kCgThreads, 3) k_grid_compact(ImageArgs a, int
         }
         __syncthreads();  // chunk q staged by every thread; the grid zeroed
         const float2 *buf = stg + (q & 1) * kCgChunk;
-        float2 v[kRowGridU];
-        const int i0 = tid * kRowGridU;
-#pragma unroll
-        for (int u = 0; u < kRowGridU; ++u) {
-            v[u] = make_float2(0.f, 0.f);
-            if (i0 + u < cur.n) {
-                v[u] = buf[cur.bl[u]];
-                if (gl) v[u] = apply_gain(v[u], gl, int64_t(q) * kCgChunk + cur.bl[u]);
-                if ((cur.conj >> u) & 1u) v[u].y = -v[u].y;
-            }
-        }
-        grid_sum_chunk<kCgThreads>(cur, v, tid, cell);  // ends with a barrier
+        cg_sum_chunk(G, cur, ents + int64_t(q) * kCgChunk, buf, int64_t(q) * kCgChunk, gl, tid);
+        __syncthreads();  // the chunk's adds precede the next chunk's; its buffer is free
         if (more) cur = nxt;
     }
     // weights (rows >= 1), then row 0: weight, origin 2 Re(V) w, mirror

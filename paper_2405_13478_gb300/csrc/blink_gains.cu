@@ -6,8 +6,11 @@
 // visibilities M).  With gamma = dL/dRe V + i dL/dIm V from blink_degrid,
 //   gamma(g_i) = sum_{j>i} gamma(V_ij) g_j conj(M_ij)
 //              + sum_{k<i} conj(gamma(V_ki)) g_k M_ki,
-// summed over all layers.  Every sum runs in a fixed order (FP64), so the
-// gradient is the same bits from run to run.
+// summed over all layers.  Every sum runs in a fixed order, so the gradient
+// is the same bits from run to run: per thread a compensated FP32 sum
+// (Kahan 1965: the running error of each add is carried into the next), the
+// partials then in FP64.  This part runs FP64 at about 1/75 of its FP32
+// rate, so FP64 adds per baseline would bound the kernel.
 #include "blink_common.cuh"
 #include "blink_kernels.cuh"
 #include "blink_pairs.cuh"
@@ -45,6 +48,26 @@ __global__ void k_gain_products(const float2 *__restrict__ gains, int64_t stride
     out[int64_t(blockIdx.y) * nb + b] = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
 }
 
+// Compensated FP32 sum of a complex series (Kahan summation per component).
+struct KSum {
+    float2 s, c;  // running sum, running compensation (the negated lost low part)
+    __device__ __forceinline__ void zero() {
+        s = make_float2(0.f, 0.f);
+        c = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void add(float x, float y) {
+        const float ax = x - c.x, ay = y - c.y;
+        const float tx = s.x + ax, ty = s.y + ay;
+        c.x = (tx - s.x) - ax;
+        c.y = (ty - s.y) - ay;
+        s.x = tx;
+        s.y = ty;
+    }
+    __device__ __forceinline__ double2 value() const {
+        return make_double2(double(s.x) - double(c.x), double(s.y) - double(c.y));
+    }
+};
+
 // Gain gradient, pass 1.  CTA (t, g) takes the antenna rows i of tile t
 // (kGradTile rows) and the layers of group g; thread j walks the baselines
 // (i, j), j > i, of every such row -- contiguous in the upper-triangle order,
@@ -52,13 +75,14 @@ __global__ void k_gain_products(const float2 *__restrict__ gains, int64_t stride
 //   to row i's partial:     gamma(V_ij) g_j conj(M_ij)        (kept per thread,
 //                                                              reduced at the end)
 //   to column j's partial:  conj(gamma(V_ij)) g_i M_ij.
-// Products in FP32, sums in FP64, all in a fixed order.  Partials:
+// Products in FP32, per-thread sums compensated FP32, the reduction of the
+// row partials in FP64, all in a fixed order.  Partials (FP64):
 // pcol[g][t][j] and prow[g][i].
-constexpr int kGradTile = 16;
+constexpr int kGradTile = 8;
 constexpr int kGradThreads = 256;
 constexpr int kGradMaxJ = 4;  // antennas per thread: n_ant <= 1024
 
-__global__ void __launch_bounds__(kGradThreads) k_gain_grad_part(const float2 *__restrict__ dvis,
+__global__ void __launch_bounds__(kGradThreads, 2) k_gain_grad_part(const float2 *__restrict__ dvis,
                                                                  const float2 *__restrict__ model,
                                                                  const float2 *__restrict__ gains,
                                                                  const int64_t *__restrict__ vis_off, int n_layers,
@@ -68,62 +92,71 @@ __global__ void __launch_bounds__(kGradThreads) k_gain_grad_part(const float2 *_
     const int t = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
     const int i0 = t * kGradTile;
     const int l0 = g * layers_per_group, l1 = min(n_layers, l0 + layers_per_group);
-    double2 racc[kGradTile];
-    double2 cacc[kGradMaxJ];
+    KSum racc[kGradTile];
 #pragma unroll
-    for (int k = 0; k < kGradTile; ++k) racc[k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < kGradTile; ++k) racc[k].zero();
+    // the tile's rows: g_i and the position of baseline (i, 0) in a layer
+    float2 gik[kGradTile];
+    int32_t rowoff[kGradTile];
 #pragma unroll
-    for (int q = 0; q < kGradMaxJ; ++q) cacc[q] = make_double2(0.0, 0.0);
-    float2 gjv[kGradMaxJ];
-#pragma unroll
-    for (int q = 0; q < kGradMaxJ; ++q) {
-        const int j = tid + q * kGradThreads;
-        gjv[q] = j < n_ant ? gains[j] : make_float2(0.f, 0.f);
-    }
-    for (int l = l0; l < l1; ++l) {
-        const int64_t o = vis_off[l];
-#pragma unroll
-        for (int k = 0; k < kGradTile; ++k) {
-            const int i = i0 + k;
-            if (i >= n_ant - 1) break;
-            const float2 gi = gains[i];
-            const int64_t rs = o + pair_row_start(i, n_ant) - i - 1;  // baseline (i, j) at rs + j
-#pragma unroll
-            for (int q = 0; q < kGradMaxJ; ++q) {
-                const int j = tid + q * kGradThreads;
-                if (j <= i || j >= n_ant) continue;
-                const float2 gv = dvis[rs + j], m = model[rs + j], gj = gjv[q];
-                const float tr = gj.x * m.x + gj.y * m.y, ti = gj.y * m.x - gj.x * m.y;  // g_j conj(M)
-                racc[k].x += double(gv.x * tr - gv.y * ti);
-                racc[k].y += double(gv.x * ti + gv.y * tr);
-                const float ur = gi.x * m.x - gi.y * m.y, ui = gi.x * m.y + gi.y * m.x;  // g_i M
-                cacc[q].x += double(gv.x * ur + gv.y * ui);                            // conj(gamma) g_i M
-                cacc[q].y += double(gv.x * ui - gv.y * ur);
-            }
-        }
+    for (int k = 0; k < kGradTile; ++k) {
+        const int i = min(i0 + k, n_ant - 1);
+        gik[k] = gains[i];
+        rowoff[k] = int32_t(pair_row_start(i, n_ant) - i - 1);  // baseline (i, j) at rowoff + j
     }
     double2 *pc = pcol + (int64_t(g) * gridDim.x + t) * n_ant;
 #pragma unroll
     for (int q = 0; q < kGradMaxJ; ++q) {
+        if (q * kGradThreads >= n_ant) break;  // CTA-uniform
         const int j = tid + q * kGradThreads;
-        if (j < n_ant) pc[j] = cacc[q];
+        const float2 gj = j < n_ant ? gains[j] : make_float2(0.f, 0.f);
+        KSum cacc;
+        cacc.zero();
+        for (int l = l0; l < l1; ++l) {
+            const int64_t o = vis_off[l];
+            // every row's loads of this layer first (sixteen in flight), then
+            // the sums in the fixed order of the rows
+            float2 gv[kGradTile], mv[kGradTile];
+#pragma unroll
+            for (int k = 0; k < kGradTile; ++k) {
+                const int i = i0 + k;
+                const bool live = i < n_ant - 1 && j > i && j < n_ant;
+                gv[k] = live ? dvis[o + rowoff[k] + j] : make_float2(0.f, 0.f);
+                mv[k] = live ? model[o + rowoff[k] + j] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < kGradTile; ++k) {
+                const int i = i0 + k;
+                if (i < n_ant - 1 && j > i && j < n_ant) {
+                    const float2 v = gv[k], m = mv[k], gi = gik[k];
+                    const float tr = gj.x * m.x + gj.y * m.y, ti = gj.y * m.x - gj.x * m.y;  // g_j conj(M)
+                    racc[k].add(v.x * tr - v.y * ti, v.x * ti + v.y * tr);
+                    const float ur = gi.x * m.x - gi.y * m.y, ui = gi.x * m.y + gi.y * m.x;  // g_i M
+                    cacc.add(v.x * ur + v.y * ui, v.x * ui - v.y * ur);                      // conj(gamma) g_i M
+                }
+            }
+        }
+        if (j < n_ant) pc[j] = cacc.value();
     }
     // row partials: a fixed-order tree over the threads, one row at a time
+    // (unrolled over the rows, so the accumulators stay in registers)
     __shared__ double2 red[kGradThreads];
+#pragma unroll
     for (int k = 0; k < kGradTile; ++k) {
         const int i = i0 + k;
-        if (i >= n_ant) break;  // CTA-uniform
-        red[tid] = racc[k];
-        __syncthreads();
-        for (int s2 = kGradThreads / 2; s2 > 0; s2 >>= 1) {
-            if (tid < s2) {
-                red[tid].x += red[tid + s2].x;
-                red[tid].y += red[tid + s2].y;
+        if (i < n_ant) {  // CTA-uniform
+            red[tid] = racc[k].value();
+            __syncthreads();
+            for (int s2 = kGradThreads / 2; s2 > 0; s2 >>= 1) {
+                if (tid < s2) {
+                    red[tid].x += red[tid + s2].x;
+                    red[tid].y += red[tid + s2].y;
+                }
+                __syncthreads();
             }
+            if (tid == 0) prow[int64_t(g) * n_ant + i] = red[0];
             __syncthreads();
         }
-        if (tid == 0) prow[int64_t(g) * n_ant + i] = red[0];
-        __syncthreads();
     }
 }
 

@@ -124,7 +124,7 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     // layout of the static scratch: the tables blink_image_batch builds (cell
     // codes, weights, the register schedule of sizes <= 256, the row buckets
     // of large sizes), the work queue and status word, then the row-transform
-    // ring of large images.  A schedule or bucket set that does not fit is
+    // ring of large images and, at the end, their compact grids.  A schedule or bucket set that does not fit is
     // left out and the kernels take their atomic fallback for that call.
     const bool want_sched = n_px <= 256;
     const bool want_csr = !blink::image_small_path(n_px, n_px / 2 + 1);
@@ -246,10 +246,26 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
         row_entries = per_row > row_entries ? per_row : row_entries;
     }
     const size_t per_layer = blink::image_scratch_per_layer(n_px, r_alloc);
-    const size_t rows_bytes = kBytes - o_rows;
+    size_t rows_bytes = kBytes - o_rows;
     if (per_layer > rows_bytes)
         return say(err_msg, err_cap, BLINK_ERR_WORKSPACE,
                    "one layer's row-transform buffer does not fit in BLINK_NOALLOC_SCRATCH_BYTES");
+    // compact grids (as blink_image_batch uses them) at the end of the array,
+    // when at least one layer's grid fits beside one layer's row buffer
+    float2 *d_cg = nullptr;
+    int64_t cg_stride = 0;
+    int cg_cap = 0;
+    if (per_layer && d_csr && blink::cg_fits(r_alloc, kmax) && rows_bytes > per_layer + 256) {
+        cg_stride = (blink::cg_cells(r_alloc, kmax) + 1) & ~int64_t(1);
+        const size_t per_cg = size_t(8 * cg_stride);
+        const size_t fit = (rows_bytes - per_layer - 256) / per_cg;  // 256: the alignment below
+        cg_cap = int(fit < size_t(n_layers) ? fit : size_t(n_layers));
+        if (cg_cap >= 1) {
+            const size_t cg_off = (kBytes - size_t(cg_cap) * per_cg) / 256 * 256;
+            d_cg = reinterpret_cast<float2 *>(base + cg_off);
+            rows_bytes = cg_off - o_rows;
+        }
+    }
     blink::ImageArgs a{};
     a.vis = reinterpret_cast<const float2 *>(d_vis);
     a.out = d_images;
@@ -276,6 +292,11 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     a.n_ant = n_ant;
     a.queue = d_queue;
     a.queue_bytes = blink::image_queue_bytes(n_layers);
+    if (d_cg) {
+        a.cg = d_cg;
+        a.cg_stride = cg_stride;
+        a.cg_cap = cg_cap;
+    }
     e = blink::launch_image_group(n_px, a, s);
     if (e.status) return say(err_msg, err_cap, e.status, e.msg.c_str());
     return BLINK_OK;

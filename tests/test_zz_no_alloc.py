@@ -111,7 +111,10 @@ def test_noalloc_matches_image_batch_two_calls_in_a_row(env):
     w2.n_px = np.array([1024])
     w2.delta_u = np.array([synth.max_uv(w2.ant_xyz, w2.freqs_hz[0]) / 511])
     b = workload(env, w2, [0], [0])
-    for (ws, args), flags in (((a_ws, a), 0), ((w2, b), 1), ((a_ws, a), 1)):
+    # call 3: 512^2 station layers, whose support takes the compact gridding
+    c_ws = synth.station_512(seed=23, n_times=2)
+    c = workload(env, c_ws, [0, 1], [0, 5, 10, 15])
+    for (ws, args), flags in (((a_ws, a), 0), ((w2, b), 1), ((c_ws, c), 0), ((a_ws, a), 1)):
         st, msg, got, gws = noalloc(env, *args, flags)
         assert st == 0, msg
         want, wws = reference(env, *args, flags)
