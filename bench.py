@@ -856,7 +856,7 @@ def measure_gains(torch, binding, ctx, n_t, steps, warmup):
         @staticmethod
         def backward(fctx, gout):
             (r,) = fctx.saved_tensors
-            return r.mul_(2.0 * gout), None
+            return r.mul_(2.0 * float(gout)), None  # a host scalar keeps the kernel vectorized
 
     def step():
         g = g0.clone().requires_grad_(True)
