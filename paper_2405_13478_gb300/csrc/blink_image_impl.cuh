@@ -639,7 +639,12 @@ template <int N>
 struct DegridCfg {
     static constexpr int NT = 256;
     static constexpr int P = 8;           // column pairs per CTA: 16 adjacent image columns
-    static constexpr int W = 2 * P + 1;   // strip row stride in floats (odd)
+    // strip row stride in floats: 64-byte rows (16-byte cp.async pieces), and
+    // the pair loads of a half-warp (8 pairs x 2 rows) cover all 32 banks once
+    static constexpr int W = 2 * P;
+    // natural-order result: pair stride N + 2 (2 mod 16 in 8-byte bank pairs),
+    // so the 8 pairs of a half-warp store to distinct banks
+    static constexpr int ZN = N + 2;
     static constexpr int RB = LargeCfg<N>::RB;
     using ZL = ZLayout<N, P>;
     static_assert(P * Plan<N>::N2 <= NT && P * Plan<N>::N1 <= NT, "one four-step task per thread");
@@ -649,7 +654,7 @@ template <int N>
 size_t degrid_cols_smem() {
     using C = DegridCfg<N>;
     return std::max({size_t(N) * C::W * sizeof(float), size_t(C::P) * C::ZL::S * sizeof(float2),
-                     size_t(C::P) * N * sizeof(float2)});
+                     size_t(C::P) * C::ZN * sizeof(float2)});
 }
 
 // Forward column transforms of the image gradient (the first half of the
@@ -671,7 +676,7 @@ __global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, c
     extern __shared__ float2 sm[];
     float *strip = reinterpret_cast<float *>(sm);  // [N][W]: FFT-order row n = image row (n + H) mod N
     float2 *Z = sm;                                // [P][ZL::S] four-step intermediate
-    float2 *zn = sm;                               // [P][N] natural order
+    float2 *zn = sm;                               // [P][ZN] natural order
     const int lw = blockIdx.y;
     const DevLayer L = a.layers[l0 + lw];
     const ChanInfo ci = a.chans[L.chan];
@@ -681,15 +686,15 @@ __global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, c
     const int tid = threadIdx.x;
     const float *img = resid + L.out_off;
     if (nc == 2 * P && (reinterpret_cast<uintptr_t>(img) & 15) == 0 && (N % 4) == 0) {
+        // every 16-byte piece in flight at once, straight into shared memory
         for (int i = tid; i < N * (2 * P / 4); i += NT) {
             const int y = i / (2 * P / 4), q = i % (2 * P / 4);
-            const float4 v = __ldcs(reinterpret_cast<const float4 *>(img + int64_t(y) * N + x0) + q);
-            float *d = strip + ((y + H) % N) * W + 4 * q;
-            d[0] = v.x;
-            d[1] = v.y;
-            d[2] = v.z;
-            d[3] = v.w;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(uint32_t(__cvta_generic_to_shared(
+                             strip + ((y + H) % N) * W + 4 * q))),
+                         "l"(img + int64_t(y) * N + x0 + 4 * q)
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     } else {
         for (int i = tid; i < N * 2 * P; i += NT) {
             const int y = i / (2 * P), c = i % (2 * P);
@@ -703,10 +708,7 @@ __global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, c
     float2 x[N1];
     if (task_a) {
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) {
-            const float *r = strip + (N2 * n1 + n2) * W + 2 * pa;
-            x[n1] = make_float2(r[0], r[1]);
-        }
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = *reinterpret_cast<const float2 *>(strip + (N2 * n1 + n2) * W + 2 * pa);
     }
     __syncthreads();  // the strip is in registers: the buffer becomes Z
     if (task_a) {
@@ -729,8 +731,12 @@ __global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, c
     }
     __syncthreads();  // Z is in registers: the buffer becomes zn
     if (task_b) {
+        // only the frequencies the unpacking below reads: k < R and N - k < R
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) zn[pb * N + k1 + N1 * k2] = y[k2];
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const int k = k1 + N1 * k2;
+            if (k < R || k > N - R) zn[pb * C::ZN + k] = y[k2];
+        }
     }
     __syncthreads();
     // unpack the two real columns of each pair and keep rows k < R; image
@@ -740,7 +746,7 @@ __global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, c
         const int k = i / P, p = i % P;
         const int xa = x0 + 2 * p;
         if (xa >= N) continue;
-        const float2 za = zn[p * N + k], zb = zn[p * N + (N - k) % N];
+        const float2 za = zn[p * C::ZN + k], zb = zn[p * C::ZN + (N - k) % N];
         // C_a = (Z[k] + conj Z[N-k]) / 2, C_b = (Z[k] - conj Z[N-k]) / (2 i)
         out[int64_t(k) * N + (xa + H) % N] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
         if (xa + 1 < N)
