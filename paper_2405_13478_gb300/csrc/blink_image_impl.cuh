@@ -328,11 +328,15 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
         const int km = ci.kmax_u, kc = 2 * km + 1;
         const float2 *cg = a.cg + int64_t(lidx - a.cg_l0) * a.cg_stride + int64_t(r0) * kc;
         prologue();
-        __syncthreads();
+        __syncthreads();  // the band is zero before the copies land in it
         for (int i = tid; i < nrows * kc; i += NT) {
             const int r = i / kc, ku = i % kc - km;
-            sm[r * S + RowLayout<N>::phys(ku < 0 ? ku + N : ku)] = __ldcs(cg + i);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(uint32_t(__cvta_generic_to_shared(
+                             sm + r * S + RowLayout<N>::phys(ku < 0 ? ku + N : ku)))),
+                         "l"(cg + i)
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     } else {
         const LayerGains gl = layer_gains(a, L);
         if (a.csr && ci.csr_off >= 0) {
@@ -352,7 +356,7 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
         }
         weight_and_complete<N, true>(sm, S, r0, r0 + nrows, ci, a.wgt, tid, NT);
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table in place
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table (and compact rows) in place
     __syncthreads();
     rows_fft<N, +1, true>(sm, S, nrows, tid, NT, tw);
     for (int i = tid; i < nrows * N; i += NT) {
@@ -365,7 +369,7 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
 // path: the tensor-core FP16 modes and callers without a work queue).
 // Grid: (bands, layers in wave).
 template <int N>
-__global__ void __launch_bounds__(RowsCfg<N>::NT, Plan<N>::N1 == 24 ? 2 : 3) k_rows(ImageArgs a, int l0) {
+__global__ void __launch_bounds__(RowsCfg<N>::NT, (Plan<N>::N1 == 24 || N >= 1024) ? 2 : 3) k_rows(ImageArgs a, int l0) {
     extern __shared__ float2 sm[];
     const int lw = blockIdx.y;
     const DevLayer L = a.layers[l0 + lw];
@@ -772,8 +776,14 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_degrid_rows(ImageArgs a, fl
     const float2 *in = a.scratch + (int64_t(lw) * a.r_alloc + r0) * N;
     float2 *tw = sm + tw_offset<N>();
     stage_four_step<N>(tw, tid, NT);
-    for (int i = tid; i < nrows * N; i += NT) sm[(i / N) * S + RowLayout<N>::phys(i % N)] = in[i];
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    // the band's rows: every 8-byte copy in flight at once (the padded row
+    // layout keeps only 8-byte alignment)
+    for (int i = tid; i < nrows * N; i += NT)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(uint32_t(__cvta_generic_to_shared(
+                         sm + (i / N) * S + RowLayout<N>::phys(i % N)))),
+                     "l"(in + i)
+                     : "memory");
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     rows_fft<N, -1, true>(sm, S, nrows, tid, NT, tw);
     const float *w = ci.weighting == 1 ? a.wgt + ci.wgt_off : nullptr;
