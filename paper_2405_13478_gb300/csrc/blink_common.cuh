@@ -67,7 +67,8 @@ struct ChanInfo {
 // each: cell << 12 | conj << 11 | (baseline - q kCgChunk), where the compact
 // cell of row r and column k_u is r (2 kmax + 1) + k_u + kmax (kmax: the
 // channel's largest |k_u|).  cg_ents[q][i], i < cg_cnt[q]; the rest of a
-// chunk's kCgChunk words are 0xFFFFFFFF.
+// chunk's kCgChunk words are 0xFFFFFFFF.  Filled only for channels whose
+// compact grid fits (cg_fits below).
 constexpr int kCsrBlock = 256;        // baselines per block of the bucket sort
 constexpr int kCsrMaxBuckets = 1024 / 2 + 1;  // largest supported n_px / 2 + 1
 constexpr int kCgChunk = 2048;        // baselines per chunk of the compact gridding

@@ -73,9 +73,9 @@ __device__ __forceinline__ void cg_stage(float2 *dst, const float2 *src, int n, 
 }
 
 // Sums of one chunk.  The entries are sorted by cell, so each cell is one run;
-// the thread whose window [8 tid, 8 tid + 8) holds a run's first entry sums
-// the whole run in order -- past the window's end when the run goes on -- and
-// adds it to the cell.  A cell therefore has one writer per chunk and one
+// the thread whose window [8 tid, 8 tid + 8) holds a run's first entry adds
+// the whole run to the cell, entry by entry in order -- past the window's end
+// when the run goes on.  A cell therefore has one writer per chunk and one
 // fixed summation order: no scan, no atomics.  buf holds the chunk's staged
 // visibilities (baselines b0 ..).
 __device__ __forceinline__ void cg_sum_chunk(float2 *G, const CgChunk &c, const uint32_t *__restrict__ e,
@@ -93,37 +93,26 @@ __device__ __forceinline__ void cg_sum_chunk(float2 *G, const CgChunk &c, const 
     float2 v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) v[u] = i0 + u < c.n ? value(c.w[u]) : make_float2(0.f, 0.f);
-    uint32_t cur = kNone;
-    float2 s = make_float2(0.f, 0.f);
+    uint32_t last = kNone;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const uint32_t k = c.w[u] >> 12;
         if (i0 + u < c.n && k != c.kprev) {  // leading entries equal to kprev continue an earlier run
-            if (k == cur) {
-                s.x += v[u].x;
-                s.y += v[u].y;
-            } else {
-                if (cur != kNone) {
-                    G[cur].x += s.x;
-                    G[cur].y += s.y;
-                }
-                cur = k;
-                s = v[u];
-            }
+            float2 *p = G + k;
+            p->x += v[u].x;
+            p->y += v[u].y;
+            last = k;
         }
     }
-    if (cur == kNone) return;
-    if (c.knext == cur) {  // the last run goes on past the window
+    if (last != kNone && c.knext == last) {  // the last run goes on past the window
         for (int j = i0 + U; j < c.n; ++j) {
             const uint32_t w = __ldg(e + j);
-            if ((w >> 12) != cur) break;
+            if ((w >> 12) != last) break;
             const float2 x = value(w);
-            s.x += x.x;
-            s.y += x.y;
+            G[last].x += x.x;
+            G[last].y += x.y;
         }
     }
-    G[cur].x += s.x;
-    G[cur].y += s.y;
 }
 
 // One CTA per layer l0 + blockIdx.x of a.layers; its compact grid goes to

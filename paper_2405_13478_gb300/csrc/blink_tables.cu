@@ -705,7 +705,9 @@ __global__ void __launch_bounds__(256) k_cg_sort(const ChanInfo *__restrict__ in
     __shared__ uint32_t key[kCgChunk];
     __shared__ int s_cnt;
     const ChanInfo ci = info[blockIdx.y];
-    if (ci.csr_off < 0) return;
+    // channels whose compact grid cannot fit the gridding kernel never use
+    // these tables (their group cannot either)
+    if (ci.csr_off < 0 || !cg_fits(max(ci.rows, 1), ci.kmax_u)) return;
     const CsrLayout cl(ci.n_px, nb);
     const int q = blockIdx.x;
     if (q >= cl.n_cg) return;
