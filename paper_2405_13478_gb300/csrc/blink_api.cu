@@ -270,6 +270,26 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         prev_key = k;
     }
     p->n_chan = int(p->geoms.size());
+    // the array's extent, for the compact-support bound of large sizes
+    double span_x = -1.0, span_y = -1.0;
+    bool any_large = false;
+    for (const auto &g : p->geoms) any_large = any_large || g.n_px > kSchedMaxPx;
+    if (any_large && n_ant > 0) {
+        std::vector<double> hx(size_t(3) * size_t(n_ant));
+        if (cudaMemcpyAsync(hx.data(), d_ant_xyz, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost, st) ==
+                cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess) {
+            double x0 = hx[0], x1 = hx[0], y0 = hx[1], y1 = hx[1];
+            for (int a = 1; a < n_ant; ++a) {
+                x0 = std::min(x0, hx[3 * a]);
+                x1 = std::max(x1, hx[3 * a]);
+                y0 = std::min(y0, hx[3 * a + 1]);
+                y1 = std::max(y1, hx[3 * a + 1]);
+            }
+            span_x = x1 - x0;
+            span_y = y1 - y0;
+        }
+    }
     // channel table offsets
     p->infos.assign(size_t(p->n_chan), ChanInfo{});
     int64_t wgt_total = 0;
@@ -289,7 +309,14 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
         } else {
             ci.csr_off = -1;
         }
-        const bool sched = ci.n_px <= kSchedMaxPx;
+        // register-accumulation schedule: sizes <= 256 (the fused kernel), and
+        // larger sizes whose compact support is sure to fit (the compact
+        // gridding kernel)
+        const bool sched_large = ci.n_px > kSchedMaxPx && span_x >= 0.0 &&
+                                 blink::cg_bound_fits(span_x, span_y, p->geoms[size_t(c)].freq_hz,
+                                                      p->geoms[size_t(c)].delta_u, ci.n_px);
+        const bool sched = ci.n_px <= kSchedMaxPx || sched_large;
+        ci.sched_large = sched_large ? 1 : 0;
         if (sched) {
             const int q = int((p->nb + blink::kSchedMaxChunk - 1) / blink::kSchedMaxChunk);
             int k = int((p->nb + q - 1) / q);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 
 // Supported image sizes (N_px): products of small radices whose four-step
@@ -47,7 +48,7 @@ struct ChanInfo {
     int32_t stream_len;  // entries in the schedule stream
     int64_t sched_off;   // byte offset of this channel's schedule block (-1 if none)
     int32_t max_seg;     // longest per-chunk stream segment (entries)
-    int32_t pad2;
+    int32_t sched_large; // 1: the schedule serves the compact gridding of a size > 256
     int64_t csr_off;     // row-bucketed entries of this channel (-1 if none), see CsrLayout
 };
 
@@ -101,6 +102,20 @@ struct CsrLayout {
 constexpr size_t kCgGridBytes = 40 * 1024;
 __host__ __device__ inline int64_t cg_cells(int rows, int kmax) { return int64_t(rows) * (2 * kmax + 1); }
 __host__ __device__ inline bool cg_fits(int rows, int kmax) { return cg_cells(rows, kmax) * 8 <= int64_t(kCgGridBytes); }
+
+// Host bound of a channel's compact support from the array's extent
+// (span_x, span_y: largest coordinate differences in metres): every baseline
+// has |u| <= span_x / lambda, so |k_u| <= span_x / (lambda delta_u) + 1/2; two
+// cells of margin cover the rounding.  Decides, before the tables are built,
+// whether a large-size channel gets a gridding schedule.
+inline bool cg_bound_fits(double span_x, double span_y, double freq_hz, double delta_u, int n_px) {
+    const double lambda = kSpeedOfLight / freq_hz;
+    const double tu = span_x / (lambda * delta_u), tv = span_y / (lambda * delta_u);
+    if (!(tu < 1e6 && tv < 1e6)) return false;
+    const int kmax = std::min(n_px / 2 - 1, int(tu) + 2);
+    const int rows = std::min(n_px / 2, int(tv) + 3);
+    return cg_fits(rows, kmax);
+}
 
 // Register-accumulation gridding schedule (one block per channel).
 //

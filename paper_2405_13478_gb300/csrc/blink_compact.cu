@@ -185,6 +185,109 @@ __global__ void __launch_bounds__(kCgThreads, 3) k_grid_compact(ImageArgs a, int
     for (int i = tid; i < ncell; i += kCgThreads) dst[i] = G[i];
 }
 
+// Scheduled compact gridding: the register-accumulation schedule of the
+// fused small-image kernel, built for the channel's own size (slot positions
+// r (N + 1) + c).  Per chunk of the schedule the visibilities, the entry
+// stream segment and its metadata are staged with cp.async; each thread sums
+// the entries of the <= kSchedSlots cells it owns in registers over all
+// chunks (one add per entry, no per-chunk writes), then writes every owned
+// cell once, weighted, into the compact grid in shared memory (row 0 with its
+// mirror), which goes out coalesced.  The sums follow the schedule's fixed
+// entry order: the same bits on every call.
+__global__ void __launch_bounds__(kSchedThreads, 2) k_grid_compact_sched(ImageArgs a, int l0) {
+    constexpr int NT = kSchedThreads;
+    extern __shared__ float2 sm[];
+    const DevLayer L = a.layers[l0 + blockIdx.x];
+    const ChanInfo ci = a.chans[L.chan];
+    const int N = ci.n_px, S = N + 1, R = ci.rows, km = ci.kmax_u, kc = 2 * km + 1, ncell = R * kc;
+    const int Q = ci.n_chunks, K = ci.chunk, M = ci.m_slots;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SchedLayout lay(N, a.nb, Q);
+    const StageLayout sl(a.max_chunk, a.max_seg, kSchedSlots);
+    const unsigned char *blk = a.sched + ci.sched_off;
+    const uint2 *meta_g = reinterpret_cast<const uint2 *>(blk + lay.meta);
+    const uint16_t *stream_g = reinterpret_cast<const uint16_t *>(blk + lay.stream);
+    char *smc = reinterpret_cast<char *>(sm);
+    float2 *stage = reinterpret_cast<float2 *>(smc + sl.vis);
+    const uint16_t *ent = reinterpret_cast<const uint16_t *>(smc + sl.ent);
+    const uint2 *meta = reinterpret_cast<const uint2 *>(smc + sl.meta);
+    const float2 *vis = a.vis + L.vis_off;
+    const LayerGains gl = layer_gains(a, L);
+    const uint64_t pol_vis = l2_evict_first();
+
+    float2 acc[kSchedSlots];
+#pragma unroll
+    for (int j = 0; j < kSchedSlots; ++j) acc[j] = make_float2(0.f, 0.f);
+    if (tid == 0) stage[K] = make_float2(0.f, 0.f);  // sentinel target
+    const int per_chunk = M * kSchedWarps;
+    auto seg_start = [&](int c) { return c < Q ? int(__ldg(&meta_g[c * per_chunk].x)) : ci.stream_len; };
+    int s_beg = seg_start(0), s_end = seg_start(1);
+    for (int q = 0; q < Q; ++q) {
+        const int64_t rem = a.nb - int64_t(q) * K;
+        const int n_q = int(rem < K ? rem : int64_t(K));
+        const int s0 = s_beg & ~7;
+        stage_async<NT>(stage, vis + int64_t(q) * K, n_q, tid, pol_vis);
+        cp16_async<NT>(smc + sl.ent, stream_g + s0, (s_end - s0 + 7) >> 3, tid);
+        cp16_async<NT>(smc + sl.meta, meta_g + q * per_chunk, per_chunk >> 1, tid);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        const int s_next = seg_start(q + 2);
+        stage_wait();
+        __syncthreads();
+        if (gl) {  // gains on the staged visibilities (fused epilogue)
+            const int64_t b0 = int64_t(q) * K;
+            for (int e = tid; e < n_q; e += NT) stage[e] = apply_gain(stage[e], gl, b0 + e);
+            __syncthreads();
+        }
+        const int shift = -s0;
+#pragma unroll
+        for (int j = 0; j < kSchedSlots; ++j) {
+            if (j < M) {
+                const uint2 m = meta[j * kSchedWarps + warp];
+                const uint16_t *e = ent + int(m.x) + shift + lane;
+                float2 sum = make_float2(0.f, 0.f);
+#pragma unroll 4
+                for (uint32_t k = 0; k < m.y; ++k) {
+                    const uint32_t code = e[32 * k];
+                    const float2 v = stage[code & 0x7FFFu];
+                    sum.x += v.x;
+                    sum.y += (code & 0x8000u) ? -v.y : v.y;
+                }
+                acc[j].x += sum.x;
+                acc[j].y += sum.y;
+            }
+        }
+        s_beg = s_end;
+        s_end = s_next;
+        __syncthreads();
+    }
+    // the staging area becomes the compact grid: zero it, write the slots
+    float2 *G = sm;
+    const uint32_t *slot_pos = reinterpret_cast<const uint32_t *>(blk + lay.slot_pos);
+    const float *slot_w = reinterpret_cast<const float *>(blk + lay.slot_w);
+    for (int i = tid; i < ncell; i += NT) G[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSchedSlots; ++j) {
+        if (j < M) {
+            const uint32_t sp = __ldg(slot_pos + j * NT + tid);
+            if (sp != kSlotEmpty) {
+                const float wv = __ldg(slot_w + j * NT + tid);
+                const int p = int(sp & 0x3FFFFFFFu), r = p / S, c = p % S, ku = c <= N / 2 ? c : c - N;
+                if (sp & kSlotOrigin) {
+                    G[km] = make_float2(2.f * acc[j].x * wv, 0.f);
+                } else {
+                    const float2 g = make_float2(acc[j].x * wv, acc[j].y * wv);
+                    G[r * kc + ku + km] = g;
+                    if (sp & kSlotMirror) G[km - ku] = make_float2(g.x, -g.y);  // row 0
+                }
+            }
+        }
+    }
+    __syncthreads();
+    float2 *dst = a.cg + int64_t(blockIdx.x) * a.cg_stride;
+    for (int i = tid; i < ncell; i += NT) dst[i] = G[i];
+}
+
 }  // namespace
 
 size_t grid_compact_smem(int64_t cg_stride) {
@@ -193,7 +296,22 @@ size_t grid_compact_smem(int64_t cg_stride) {
 
 Error launch_grid_compact(const ImageArgs &a, int l0, int cnt, cudaStream_t st) {
     if (cnt <= 0) return Error{0, ""};
-    if (!a.cg || !a.csr || cnt > a.cg_cap) return Error{-3, "compact gridding without its buffer or tables"};
+    if (!a.cg || cnt > a.cg_cap) return Error{-3, "compact gridding without its buffer"};
+    if (a.sched && a.sched_ok) {  // every channel of the group has its schedule
+        const size_t smem = std::max(size_t(StageLayout(a.max_chunk, a.max_seg, kSchedSlots).bytes),
+                                     size_t(a.cg_stride) * sizeof(float2));
+        BLINK_CUDA_TRY(
+            cudaFuncSetAttribute(k_grid_compact_sched, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        for (int k = 0; k < cnt; k += 1 << 30) {
+            const int c = std::min(cnt - k, 1 << 30);
+            ImageArgs b = a;
+            b.cg = a.cg + int64_t(k) * a.cg_stride;
+            k_grid_compact_sched<<<unsigned(c), kSchedThreads, smem, st>>>(b, l0 + k);
+            BLINK_CUDA_TRY(cudaGetLastError());
+        }
+        return Error{0, ""};
+    }
+    if (!a.csr) return Error{-3, "compact gridding without its tables"};
     const size_t smem = grid_compact_smem(a.cg_stride);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_grid_compact, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     for (int k = 0; k < cnt; k += 1 << 30) {

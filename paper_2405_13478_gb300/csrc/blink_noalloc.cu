@@ -126,7 +126,29 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
     // of large sizes), the work queue and status word, then the row-transform
     // ring of large images and, at the end, their compact grids.  A schedule or bucket set that does not fit is
     // left out and the kernels take their atomic fallback for that call.
-    const bool want_sched = n_px <= 256;
+    // the register schedule: sizes <= 256, and larger sizes whose compact
+    // support is sure to fit (as blink_image_batch decides, from the array's
+    // extent)
+    bool large_sched = false;
+    if (n_px > 256) {
+        double hx[3 * 2048];
+        const bool fits_host = n_ant <= 2048;
+        if (fits_host && cudaMemcpyAsync(hx, d_ant_xyz, sizeof(double) * 3 * size_t(n_ant), cudaMemcpyDeviceToHost,
+                                         static_cast<cudaStream_t>(stream)) == cudaSuccess &&
+            cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) == cudaSuccess) {
+            double x0 = hx[0], x1 = hx[0], y0 = hx[1], y1 = hx[1];
+            for (int a = 1; a < n_ant; ++a) {
+                x0 = std::min(x0, hx[3 * a]);
+                x1 = std::max(x1, hx[3 * a]);
+                y0 = std::min(y0, hx[3 * a + 1]);
+                y1 = std::max(y1, hx[3 * a + 1]);
+            }
+            large_sched = true;
+            for (int c = 0; c < n_chan && large_sched; ++c)
+                large_sched = blink::cg_bound_fits(x1 - x0, y1 - y0, geoms[c].freq_hz, geoms[c].delta_u, n_px);
+        }
+    }
+    const bool want_sched = n_px <= 256 || large_sched;
     const bool want_csr = !blink::image_small_path(n_px, n_px / 2 + 1);
     const int q_chunks = int((nb + blink::kSchedMaxChunk - 1) / blink::kSchedMaxChunk);
     int k_chunk = int((nb + q_chunks - 1) / q_chunks);
@@ -165,6 +187,7 @@ extern "C" BLINK_API int blink_image_batch_noalloc(const double *d_ant_xyz, int 
         ci.sched_off = -1;
         ci.csr_off = -1;
         if (use_sched) {
+            ci.sched_large = n_px > 256 ? 1 : 0;
             ci.n_chunks = q_chunks;
             ci.chunk = k_chunk;
             ci.sched_off = sched_total;

@@ -173,8 +173,10 @@ __global__ void k_finalize(ChanInfo *__restrict__ info, float *__restrict__ wgt)
 // busiest warp of a chunk -- which every chunk waits for -- carries ~5 %
 // more than the mean (~30 % when groups fill the warps in rank order).
 // Falls back (sched = 0) when the cells need more than kSchedSlots slots per
-// thread or the padded stream outgrows its buffer, and skips channels whose
-// support rows do not fit the fused kernels.
+// thread or the padded stream outgrows its buffer, and skips channels of
+// sizes <= 256 whose support rows do not fit the fused kernels.  Channels of
+// larger sizes get a schedule only when flagged (sched_large) for the
+// compact gridding; slot positions are r (N + 1) + c in both cases.
 constexpr int kPeakBins = 64;  // peaks above 63 share the last bucket
 constexpr int kMaxItems = 4096;
 
@@ -184,7 +186,9 @@ __global__ void __launch_bounds__(1024) k_sched_slots(ChanInfo *__restrict__ inf
     ChanInfo ci = info[ch];
     if (ci.sched_off < 0) return;
     const int n = ci.n_px, S = n + 1, R = max(ci.rows, 1), Q = ci.n_chunks;
-    if (!small_path_fits(n, R)) {  // the channel's images take the two-kernel path
+    // channels of sizes <= 256 whose images take the two-kernel path need no
+    // schedule; larger ones have one only for the compact gridding
+    if (!ci.sched_large && !small_path_fits(n, R)) {
         if (threadIdx.x == 0) info[ch].sched = 0;
         return;
     }
