@@ -104,16 +104,35 @@ __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begi
 // the padded layout (PAD) and the table's order every shared access of a
 // warp is conflict-free.
 template <int N, int SIGN = +1, bool PAD = false>
-__device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt, const float2 *tw) {
+__device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt, const float2 *tw,
+                                         int kmax = N) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     auto ph = [](int q) { return PAD ? RowLayout<N>::phys(q) : q; };
+    // rows that are zero outside |k_u| <= kmax < 2 N2: only n1 = 0, 1 and
+    // N1 - 2, N1 - 1 of step A hold data (the other inputs are constant zeros)
+    bool narrow = false;
+    if constexpr (N > 4 * N2 && N1 >= 4) narrow = kmax < 2 * N2;
     // step A: N1-point transforms along stride N2, then twiddle W_N^(n2 k1)
     for (int t = tid; t < nrows * N2; t += nt) {
         const int r = t / N2, n2 = t % N2;
         float2 *row = G + r * S;
         float2 x[N1];
+        if constexpr (N > 4 * N2 && N1 >= 4) {
+            if (narrow) {
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) x[n1] = row[ph(N2 * n1 + n2)];
+                for (int n1 = 0; n1 < N1; ++n1) x[n1] = make_float2(0.f, 0.f);
+                x[0] = row[ph(n2)];
+                x[1] = row[ph(N2 + n2)];
+                x[N1 - 2] = row[ph(N - 2 * N2 + n2)];
+                x[N1 - 1] = row[ph(N - N2 + n2)];
+            } else {
+#pragma unroll
+                for (int n1 = 0; n1 < N1; ++n1) x[n1] = row[ph(N2 * n1 + n2)];
+            }
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) x[n1] = row[ph(N2 * n1 + n2)];
+        }
         dft<N1, SIGN>(x);
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
@@ -168,11 +187,49 @@ struct ZLayout {
 // Pass 2, step A for pairs j0 + jj, jj < P.  `hrow2(k, c)` returns row k (< R)
 // of the pass-1 output at the frequency columns c and c + 1.  Writes the
 // four-step intermediate of pair jj to Z + jj * S.
-template <int N, int P, class ZL, class HRow2>
-__device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow2 hrow2, int tid,
-                                            int nt) {
+template <int N, int P, class ZL, int NT, class HRow2>
+__device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow2 hrow2, int tid) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
-    for (int t = tid; t < P * N2; t += nt) {
+    // (the narrow layout needs 2 N2 < N / 2 and four distinct n1)
+    if constexpr (N > 4 * N2 && N1 >= 4) {
+    if (R <= 2 * N2) {
+        // narrow support (a compact station grid): only n1 = 0, 1 (rows
+        // k < R) and n1 = N1 - 2, N1 - 1 (mirrored rows N - k < R) hold data.
+        // Every task's four loads are issued before any transform, and the
+        // other inputs are constant zeros.
+        constexpr int TPT = (P * N2 + NT - 1) / NT;
+        float4 ld[TPT][4];
+#pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+            const int t = tid + u * NT, jj = t % P, n2 = t / P, q = j0 + jj;
+            const bool ok = t < P * N2 && q < H;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            ld[u][0] = ok && n2 < R ? hrow2(n2, 2 * q) : z4;                    // k = n2
+            ld[u][1] = ok && N2 + n2 < R ? hrow2(N2 + n2, 2 * q) : z4;          // k = N2 + n2
+            ld[u][2] = ok && 2 * N2 - n2 < R ? hrow2(2 * N2 - n2, 2 * q) : z4;  // N - k, n1 = N1 - 2
+            ld[u][3] = ok && N2 - n2 < R ? hrow2(N2 - n2, 2 * q) : z4;          // N - k, n1 = N1 - 1
+        }
+#pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+            const int t = tid + u * NT, jj = t % P, n2 = t / P, q = j0 + jj;
+            if (t >= P * N2 || q >= H) continue;
+            float2 x[N1];
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) x[n1] = make_float2(0.f, 0.f);
+            x[0] = make_float2(ld[u][0].x - ld[u][0].w, ld[u][0].y + ld[u][0].z);            // H_a + i H_b
+            x[1] = make_float2(ld[u][1].x - ld[u][1].w, ld[u][1].y + ld[u][1].z);
+            x[N1 - 2] = make_float2(ld[u][2].x + ld[u][2].w, ld[u][2].z - ld[u][2].y);       // conj(H_a) + i conj(H_b)
+            x[N1 - 1] = make_float2(ld[u][3].x + ld[u][3].w, ld[u][3].z - ld[u][3].y);
+            dft<N1, +1>(x);
+            float2 *zp = Z + jj * ZL::S;
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1)
+                zp[ZL::phys(N2 * k1 + n2)] = k1 == 0 ? x[0] : cmulc(x[k1], four_step_tw<N, +1>(k1, n2));
+        }
+        return;
+    }
+    }
+    for (int t = tid; t < P * N2; t += NT) {
         const int jj = t % P, n2 = t / P;
         const int q = j0 + jj;
         if (q >= H) continue;
@@ -358,7 +415,7 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table (and compact rows) in place
     __syncthreads();
-    rows_fft<N, +1, true>(sm, S, nrows, tid, NT, tw);
+    rows_fft<N, +1, true>(sm, S, nrows, tid, NT, tw, ci.kmax_u);
     for (int i = tid; i < nrows * N; i += NT) {
         const int r = i / N, p = i % N;
         dst[int64_t(r) * N + p] = sm[r * S + RowLayout<N>::phys(pos_after_rows<N>(p))];
@@ -409,23 +466,43 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
     __syncthreads();
     const int jj = tid % P, n2 = tid / P;  // one task per thread
     float2 x[N1];
+    bool narrow = false;
+    if constexpr (N > 4 * N2 && N1 >= 4) {
+    if (R <= 2 * N2) {
+        narrow = true;
+        // narrow support: only n1 = 0, 1 and N1 - 2, N1 - 1 hold data (the
+        // other inputs are constant zeros)
+        auto row = [&](int k) {
+            return k < R ? *reinterpret_cast<const float4 *>(stg + k * 2 * P + 2 * jj) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        const float4 a0 = row(n2), a1 = row(N2 + n2), b2 = row(2 * N2 - n2), b1 = row(N2 - n2);
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) {
-        const int k = N2 * n1 + n2;
-        float2 z = make_float2(0.f, 0.f);
-        if (k < H) {
-            if (k < R) {
-                const float4 ab = *reinterpret_cast<const float4 *>(stg + k * 2 * P + 2 * jj);
-                z = make_float2(ab.x - ab.w, ab.y + ab.z);  // H_a + i H_b
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = make_float2(0.f, 0.f);
+        x[0] = make_float2(a0.x - a0.w, a0.y + a0.z);  // H_a + i H_b
+        x[1] = make_float2(a1.x - a1.w, a1.y + a1.z);
+        x[N1 - 2] = make_float2(b2.x + b2.w, b2.z - b2.y);  // conj(H_a) + i conj(H_b)
+        x[N1 - 1] = make_float2(b1.x + b1.w, b1.z - b1.y);
+    }
+    }
+    if (!narrow) {
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const int k = N2 * n1 + n2;
+            float2 z = make_float2(0.f, 0.f);
+            if (k < H) {
+                if (k < R) {
+                    const float4 ab = *reinterpret_cast<const float4 *>(stg + k * 2 * P + 2 * jj);
+                    z = make_float2(ab.x - ab.w, ab.y + ab.z);  // H_a + i H_b
+                }
+            } else if (k > H) {
+                const int m = N - k;
+                if (m < R) {
+                    const float4 ab = *reinterpret_cast<const float4 *>(stg + m * 2 * P + 2 * jj);
+                    z = make_float2(ab.x + ab.w, ab.z - ab.y);  // conj(H_a) + i conj(H_b)
+                }
             }
-        } else if (k > H) {
-            const int m = N - k;
-            if (m < R) {
-                const float4 ab = *reinterpret_cast<const float4 *>(stg + m * 2 * P + 2 * jj);
-                z = make_float2(ab.x + ab.w, ab.z - ab.y);  // conj(H_a) + i conj(H_b)
-            }
+            x[n1] = z;
         }
-        x[n1] = z;
     }
     __syncthreads();  // every staged value is in registers: the buffer becomes Z
     dft<N1, +1>(x);
@@ -448,7 +525,7 @@ __device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L,
         cols_step_a_staged<N, P, ZL>(sm, R, j0, Hs, tid);
     } else {
         auto hrow2 = [&](int k, int c) { return __ldcg(reinterpret_cast<const float4 *>(Hs + int64_t(k) * N + c)); };
-        cols_step_a<N, P, ZL>(sm, R, j0, hrow2, tid, NT);
+        cols_step_a<N, P, ZL, NT>(sm, R, j0, hrow2, tid);
     }
     __syncthreads();
     consumed();  // every read of Hs has landed in registers or shared memory
@@ -672,7 +749,7 @@ size_t degrid_cols_smem() {
 // j = image column + N/2 mod N), 16 adjacent columns per row.
 // Grid: (N / 16, layers in wave).
 template <int N>
-__global__ void __launch_bounds__(DegridCfg<N>::NT) k_degrid_cols(ImageArgs a, const float *resid, int l0) {
+__global__ void __launch_bounds__(DegridCfg<N>::NT, 3) k_degrid_cols(ImageArgs a, const float *resid, int l0) {
     using C = DegridCfg<N>;
     using ZL = typename C::ZL;
     constexpr int NT = C::NT, P = C::P, W = C::W, H = N / 2;
@@ -830,6 +907,8 @@ Error launch_degrid_n(const ImageArgs &a, const float *resid, float2 *dvis, cuda
     const size_t smem_c = degrid_cols_smem<N>();
     const size_t smem_r = rows_smem<N>();
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_c)));
+    // three CTAs per SM: ask for the largest shared-memory carveout
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_cols<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_r)));
     const unsigned pchunks = unsigned((N + 2 * C::P - 1) / (2 * C::P));
     const unsigned bands = unsigned((a.r_alloc + C::RB - 1) / C::RB);
