@@ -261,3 +261,30 @@ def test_compact_grid_waves_and_paths_agree(torch, ctx):
         err = np.abs(g.astype(np.float64) - w).max()
         assert err <= IMG_TOL * np.abs(w).max(), f"layer {k}: err {err:.3e}"
     plan.close()
+
+
+def test_compact_gridding_without_a_schedule_matches_oracle(torch, ctx):
+    # one antenna 20 km away: every baseline to it lands beyond N/2 - 1 cells
+    # and is dropped, so the kept support stays the station's compact grid,
+    # but the plan's bound from the array's extent no longer promises a fit
+    # and builds no schedule -- the compact gridding then sums the per-chunk
+    # cell-sorted entries instead
+    from paper_2405_13478_gb300 import binding
+    ws = synth.station_512(seed=34, n_times=1)
+    xyz = np.concatenate([ws.ant_xyz, np.array([[20000.0, 15000.0, 0.0]])])
+    n_ant = xyz.shape[0]
+    B = n_ant * (n_ant - 1) // 2
+    rng = np.random.Generator(np.random.PCG64(35))
+    vis = (rng.normal(size=2 * B * 4).astype(np.float32)).view(np.complex64)
+    layers = [dict(n_px=512, weighting=w, freq_hz=float(ws.freqs_hz[c]), delta_u=0.5, vis_offset=k * B)
+              for k, (c, w) in enumerate([(0, 0), (7, 1), (15, 0), (3, 1)])]
+    layers, total = binding.layer_out_offsets(layers)
+    out = torch.full((total,), float("nan"), device="cuda")
+    ctx.image_batch(torch.as_tensor(xyz).cuda(), layers, torch.as_tensor(vis).cuda(), out)
+    torch.cuda.synchronize()
+    want, _ = oracle.image_batch(xyz, layers, vis, "fft")
+    o = out.cpu().numpy()
+    for L, w in zip(layers, want):
+        g = o[L["out_offset"]:L["out_offset"] + 512 * 512].reshape(512, 512)
+        err = np.abs(g.astype(np.float64) - w).max()
+        assert err <= IMG_TOL * np.abs(w).max(), f"err {err:.3e}"
