@@ -103,7 +103,7 @@ __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begi
 // shared memory; lanes run along a row (n2 in step A, k1 in step B), so with
 // the padded layout (PAD) and the table's order every shared access of a
 // warp is conflict-free.
-template <int N, int SIGN = +1, bool PAD = false>
+template <int N, int SIGN = +1, bool PAD = false, bool NARROW = false>
 __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt, const float2 *tw,
                                          int kmax = N) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
@@ -111,13 +111,13 @@ __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, i
     // rows that are zero outside |k_u| <= kmax < 2 N2: only n1 = 0, 1 and
     // N1 - 2, N1 - 1 of step A hold data (the other inputs are constant zeros)
     bool narrow = false;
-    if constexpr (N > 4 * N2 && N1 >= 4) narrow = kmax < 2 * N2;
+    if constexpr (NARROW && N > 4 * N2 && N1 >= 4) narrow = kmax < 2 * N2;
     // step A: N1-point transforms along stride N2, then twiddle W_N^(n2 k1)
     for (int t = tid; t < nrows * N2; t += nt) {
         const int r = t / N2, n2 = t % N2;
         float2 *row = G + r * S;
         float2 x[N1];
-        if constexpr (N > 4 * N2 && N1 >= 4) {
+        if constexpr (NARROW && N > 4 * N2 && N1 >= 4) {
             if (narrow) {
 #pragma unroll
                 for (int n1 = 0; n1 < N1; ++n1) x[n1] = make_float2(0.f, 0.f);
@@ -187,11 +187,12 @@ struct ZLayout {
 // Pass 2, step A for pairs j0 + jj, jj < P.  `hrow2(k, c)` returns row k (< R)
 // of the pass-1 output at the frequency columns c and c + 1.  Writes the
 // four-step intermediate of pair jj to Z + jj * S.
-template <int N, int P, class ZL, int NT, class HRow2>
+template <int N, int P, class ZL, int NT, bool NARROW, class HRow2>
 __device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow2 hrow2, int tid) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
-    // (the narrow layout needs 2 N2 < N / 2 and four distinct n1)
-    if constexpr (N > 4 * N2 && N1 >= 4) {
+    // (the narrow layout needs 2 N2 < N / 2 and four distinct n1; kernels
+    // that never see a narrow support leave it out of their code)
+    if constexpr (NARROW && N > 4 * N2 && N1 >= 4) {
     if (R <= 2 * N2) {
         // narrow support (a compact station grid): only n1 = 0, 1 (rows
         // k < R) and n1 = N1 - 2, N1 - 1 (mirrored rows N - k < R) hold data.
@@ -368,7 +369,7 @@ struct RowsCfg {
 // Pass 1 for the band of canonical rows [r0, r0 + RB) of one layer (r0 below
 // the channel's support R): gridding, weights, Hermitian completion of row 0,
 // the row transforms, written in natural column order to dst[r - r0][p].
-template <int N>
+template <int N, bool NARROW = true>
 __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L, const ChanInfo &ci, int lidx,
                                           int r0, int nrows, float2 *__restrict__ dst, float2 *sm, int tid) {
     using C = RowsCfg<N>;
@@ -415,7 +416,7 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table (and compact rows) in place
     __syncthreads();
-    rows_fft<N, +1, true>(sm, S, nrows, tid, NT, tw, ci.kmax_u);
+    rows_fft<N, +1, true, NARROW>(sm, S, nrows, tid, NT, tw, ci.kmax_u);
     for (int i = tid; i < nrows * N; i += NT) {
         const int r = i / N, p = i % N;
         dst[int64_t(r) * N + p] = sm[r * S + RowLayout<N>::phys(pos_after_rows<N>(p))];
@@ -450,7 +451,7 @@ struct ColsStaged {
 // once into the buffer Z later holds; each thread reads its N1 inputs into
 // registers (one 16-byte load per pair and row), the CTA synchronises, then
 // the intermediate overwrites the buffer.
-template <int N, int P, class ZL>
+template <int N, int P, class ZL, bool NARROW>
 __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, const float2 *Hs, int tid) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2, NT = LargeCfg<N>::NT;
     float2 *stg = Z;  // [R][2P]: frequency columns 2 j0 ..
@@ -467,7 +468,7 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
     const int jj = tid % P, n2 = tid / P;  // one task per thread
     float2 x[N1];
     bool narrow = false;
-    if constexpr (N > 4 * N2 && N1 >= 4) {
+    if constexpr (NARROW && N > 4 * N2 && N1 >= 4) {
     if (R <= 2 * N2) {
         narrow = true;
         // narrow support: only n1 = 0, 1 and N1 - 2, N1 - 1 hold data (the
@@ -514,7 +515,7 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
 
 // Pass 2 for the P column pairs j0.. of one layer from its pass-1 rows Hs
 // (scratch written by other CTAs: read through L2, never a stale L1 line).
-template <int N, bool EPI, class Consumed>
+template <int N, bool EPI, bool NARROW, class Consumed>
 __device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L, const ChanInfo &ci, int j0,
                                           const float2 *Hs, float *__restrict__ out, const float *__restrict__ ref,
                                           float2 *sm, int tid, Consumed &&consumed) {
@@ -522,10 +523,10 @@ __device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L,
     using ZL = ZLayout<N, P>;
     const int R = ci.rows;
     if constexpr (ColsStaged<N>::value) {
-        cols_step_a_staged<N, P, ZL>(sm, R, j0, Hs, tid);
+        cols_step_a_staged<N, P, ZL, NARROW>(sm, R, j0, Hs, tid);
     } else {
         auto hrow2 = [&](int k, int c) { return __ldcg(reinterpret_cast<const float4 *>(Hs + int64_t(k) * N + c)); };
-        cols_step_a<N, P, ZL, NT>(sm, R, j0, hrow2, tid);
+        cols_step_a<N, P, ZL, NT, NARROW>(sm, R, j0, hrow2, tid);
     }
     __syncthreads();
     consumed();  // every read of Hs has landed in registers or shared memory
@@ -550,7 +551,7 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT, EPI ? 1 : 3) k_cols(ImageArgs
     const int lw = blockIdx.y;
     const DevLayer L = a.layers[l0 + lw];
     const ChanInfo ci = a.chans[L.chan];
-    cols_item<N, EPI>(a, L, ci, blockIdx.x * LargeCfg<N>::P, a.scratch + int64_t(lw) * a.r_alloc * N, out, ref, sm,
+    cols_item<N, EPI, true>(a, L, ci, blockIdx.x * LargeCfg<N>::P, a.scratch + int64_t(lw) * a.r_alloc * N, out, ref, sm,
                       threadIdx.x, [] {});
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
 }
@@ -696,7 +697,7 @@ __global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
                 }
                 const int r0 = sub * q.rb;
                 const int nrows = min(RowsCfg<N>::RB, min(q.rb, ci.rows - r0));
-                if (r0 < ci.rows) rows_item<N>(a, L, ci, layer, r0, nrows, Hs + int64_t(r0) * N, sm, tid);
+                if (r0 < ci.rows) rows_item<N, false>(a, L, ci, layer, r0, nrows, Hs + int64_t(r0) * N, sm, tid);
                 __syncthreads();  // every thread's scratch stores precede the release below
                 if (tid == 0) {
                     __threadfence();
@@ -705,7 +706,7 @@ __global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
             } else {
                 // the slot is released as soon as its rows are read: the image
                 // stores do not gate its reuse
-                cols_item<N, EPI>(a, L, ci, sub * LargeCfg<N>::P, Hs, out, ref, sm, tid, [&] {
+                cols_item<N, EPI, false>(a, L, ci, sub * LargeCfg<N>::P, Hs, out, ref, sm, tid, [&] {
                     if (tid == 0) atomicAdd(Q.cols_done + layer, 1);
                 });
                 if (sub == 0 && tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
