@@ -846,33 +846,34 @@ def measure_gains(torch, binding, ctx, n_t, steps, warmup):
     g0 = torch.as_tensor(ws.gains.astype(np.complex64)).cuda()
     box = {}
 
-    class SquaredError(torch.autograd.Function):
-        """sum (image - model image)^2 with one residual pass, a dot product
-        and one in-place scaling for the gradient 2 (image - model image)."""
+    class SquaredNorm(torch.autograd.Function):
+        """sum r^2 as a dot product; its gradient 2 r scaled in place."""
 
         @staticmethod
-        def forward(fctx, x, y):
-            r = x - y
+        def forward(fctx, r):
             fctx.save_for_backward(r)
             return torch.dot(r, r)
 
         @staticmethod
         def backward(fctx, gout):
             (r,) = fctx.saved_tensors
-            return r.mul_(2.0 * float(gout)), None  # a host scalar keeps the kernel vectorized
+            return r.mul_(2.0 * float(gout))  # a host scalar keeps the kernel vectorized
 
     def step():
         g = g0.clone().requires_grad_(True)
         vis = autograd.apply_gains(g, model, ctx, n_ant, layers)
-        img = autograd.dirty_images(vis, plan, total)
-        loss = SquaredError.apply(img, target)
+        # residual image - model image straight from the imaging kernels (the
+        # library's reference-subtraction epilogue)
+        r = autograd.dirty_images(vis, plan, total, ref=target)
+        loss = SquaredNorm.apply(r)
         loss.backward()
-        box["vis"], box["img"] = vis, img
+        box["vis"] = vis
         return g.grad
 
     ms, clk = _time_steps(torch, step, steps, warmup)
     L = len(layers)
-    err = _sample_error(torch, ws, layers, box["vis"].detach(), box["img"].detach(), [0, L - 1])
+    img = autograd.dirty_images(box["vis"].detach(), plan, total)  # the forward images, for the error check
+    err = _sample_error(torch, ws, layers, box["vis"].detach(), img.detach(), [0, L - 1])
     n2 = 1024 * 1024
     per_image = 8 * B + 4 * n2 + 4 * n2 + 8 * B   # vis in, image out, dL/dI in, dL/dV out
     plan.close()

@@ -18,12 +18,15 @@ from . import binding
 
 class _DirtyImages(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, vis, plan, n_out, flags):
+    def forward(ctx, vis, plan, n_out, flags, ref):
         if vis.dtype != torch.complex64 or not vis.is_cuda:
             raise ValueError("vis must be a complex64 CUDA tensor")
         vis = vis.contiguous()
         out = torch.empty(n_out, dtype=torch.float32, device=vis.device)
-        plan.image(vis, out, None, flags)
+        if ref is None:
+            plan.image(vis, out, None, flags)
+        else:  # the fused epilogue subtracts the constant reference at the store
+            plan.image(vis, out, None, flags, ref=ref.detach().contiguous())
         ctx.plan = plan
         ctx.flags = flags
         ctx.vis_shape = vis.shape
@@ -34,12 +37,16 @@ class _DirtyImages(torch.autograd.Function):
         grad_out = grad_out.contiguous()
         dvis = torch.zeros(ctx.vis_shape, dtype=torch.complex64, device=grad_out.device)
         ctx.plan.degrid(grad_out, dvis, ctx.flags)
-        return dvis, None, None, None
+        return dvis, None, None, None, None
 
 
-def dirty_images(vis: torch.Tensor, plan: "binding.Plan", n_out: int, flags: int = 0):
-    """Float32 images (packed at the plan's out_offsets, ``n_out`` floats)."""
-    return _DirtyImages.apply(vis, plan, n_out, flags)
+def dirty_images(vis: torch.Tensor, plan: "binding.Plan", n_out: int, flags: int = 0,
+                 ref: torch.Tensor | None = None):
+    """Float32 images (packed at the plan's out_offsets, ``n_out`` floats).
+    With ``ref`` (float32, laid out like the images, no gradient) the result
+    is image - ref, subtracted by the fused epilogue as the images are
+    stored; the gradient with respect to the visibilities is the same."""
+    return _DirtyImages.apply(vis, plan, n_out, flags, ref)
 
 
 class _ApplyGains(torch.autograd.Function):

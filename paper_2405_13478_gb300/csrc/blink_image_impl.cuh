@@ -274,34 +274,42 @@ __device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img,
         if (q >= H) continue;
         const int xa = (2 * q + H) % N;  // image column of the pair's first column; the second is xa + 1
         const float2 *zp = Z + jj * ZL::S;
-        float2 rf[N2];  // fused epilogue: reference values requested before the transform
-        if (ref) {
-#pragma unroll
-            for (int k2 = 0; k2 < N2; ++k2) {
-                const int qq = k1 + N1 * k2;
-                const float *rp = ref + (qq < H ? qq + H : qq - H) * N + xa;  // 32-bit: N * N < 2^31
-                rf[k2] = pair_store ? __ldcs(reinterpret_cast<const float2 *>(rp)) : make_float2(__ldcs(rp), __ldcs(rp + 1));
-            }
-        }
         float2 y[N2];
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[ZL::phys(N2 * k1 + n2)];
         dft<N2, +1>(y);
+        // stores in batches of KB rows; with the fused epilogue each batch's
+        // reference values are requested together before its stores
+        constexpr int KB = N2 % 4 == 0 ? 4 : 1;
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-            const int qq = k1 + N1 * k2;              // FFT-order row
-            const int row = qq < H ? qq + H : qq - H; // fftshift
-            float *o = img + row * N + xa;            // offsets inside one image fit 32 bits
-            float2 v = make_float2(y[k2].x * scale, y[k2].y * scale);
+        for (int kb = 0; kb < N2; kb += KB) {
+            float2 rf[KB];
             if (ref) {
-                v.x -= rf[k2].x;
-                v.y -= rf[k2].y;
+#pragma unroll
+                for (int u = 0; u < KB; ++u) {
+                    const int qq = k1 + N1 * (kb + u);
+                    const float *rp = ref + (qq < H ? qq + H : qq - H) * N + xa;  // 32-bit: N * N < 2^31
+                    rf[u] = pair_store ? __ldcs(reinterpret_cast<const float2 *>(rp))
+                                       : make_float2(__ldcs(rp), __ldcs(rp + 1));
+                }
             }
-            if (pair_store) {
-                __stcs(reinterpret_cast<float2 *>(o), v);
-            } else {
-                __stcs(o, v.x);
-                __stcs(o + 1, v.y);
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+                const int k2 = kb + u;
+                const int qq = k1 + N1 * k2;              // FFT-order row
+                const int row = qq < H ? qq + H : qq - H; // fftshift
+                float *o = img + row * N + xa;            // offsets inside one image fit 32 bits
+                float2 v = make_float2(y[k2].x * scale, y[k2].y * scale);
+                if (ref) {
+                    v.x -= rf[u].x;
+                    v.y -= rf[u].y;
+                }
+                if (pair_store) {
+                    __stcs(reinterpret_cast<float2 *>(o), v);
+                } else {
+                    __stcs(o, v.x);
+                    __stcs(o + 1, v.y);
+                }
             }
         }
     }
@@ -545,7 +553,7 @@ constexpr size_t cols_smem(int r_alloc) {
 
 // Pass 2 of a wave of layers.  Grid: (ceil(N/2 / P), layers in wave).
 template <int N, bool EPI>
-__global__ void __launch_bounds__(LargeCfg<N>::NT, EPI ? 1 : 3) k_cols(ImageArgs a, int l0, float *__restrict__ out,
+__global__ void __launch_bounds__(LargeCfg<N>::NT, 3) k_cols(ImageArgs a, int l0, float *__restrict__ out,
                                                           const float *__restrict__ ref) {
     extern __shared__ float2 sm[];
     const int lw = blockIdx.y;
@@ -647,7 +655,7 @@ template <int N>
 constexpr size_t large_smem(int r_alloc) { return std::max(RowsCfg<N>::smem, cols_smem<N>(r_alloc)); }
 
 template <int N, bool EPI>
-__global__ void __launch_bounds__(256, EPI ? 1 : (Plan<N>::N1 == 24 ? 2 : 3))
+__global__ void __launch_bounds__(256, (EPI || Plan<N>::N1 == 24) ? 2 : 3)
     k_large(ImageArgs a, LargeSched q, float *__restrict__ out, const float *__restrict__ ref) {
     static_assert(RowsCfg<N>::NT == 256 && LargeCfg<N>::NT == 256, "one block shape for both item kinds");
     extern __shared__ float2 sm[];

@@ -199,3 +199,34 @@ def test_degrid_unaligned_image_gradient(torch, ctx, n_px):
     want = oracle.degrid(ku, kv, resid.astype(np.float32).astype(np.float64), 0, "fft")
     got = dvis.cpu().numpy()
     assert np.abs(got - want).max() <= TOL * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n_px", [512, 1024])
+def test_autograd_images_with_reference(torch, ctx, n_px):
+    """dirty_images(vis, plan, n, ref=t) is image - t, subtracted by the fused
+    epilogue at the store; the loss sum r^2 and its gradient with respect to
+    the visibilities agree with the plain images minus t in torch."""
+    from paper_2405_13478_gb300 import autograd, binding
+    ws = synth.station_gains(seed=12, n_times=1)
+    B = ws.n_baselines
+    layers = [dict(n_px=n_px, weighting=w, freq_hz=float(ws.freqs_hz[c]), delta_u=0.5, vis_offset=k * B)
+              for k, (c, w) in enumerate([(1, 0), (6, 1)])]
+    layers, total = binding.layer_out_offsets(layers)
+    plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
+    v0 = ws.vis("cuda", times=[0])[:, [1, 6], :].reshape(-1).contiguous()
+    t = (0.5 * autograd.dirty_images(v0, plan, total)).detach()
+    a = v0.clone().requires_grad_(True)
+    img = autograd.dirty_images(a, plan, total)
+    la = ((img - t) ** 2).sum()
+    la.backward()
+    b = v0.clone().requires_grad_(True)
+    r = autograd.dirty_images(b, plan, total, ref=t)
+    lb = (r * r).sum()
+    lb.backward()
+    torch.cuda.synchronize()
+    peak = float(img.detach().abs().max())
+    assert float((r.detach() - (img.detach() - t)).abs().max()) <= 1e-6 * peak
+    assert abs(float(la.detach()) - float(lb.detach())) <= 1e-5 * float(la.detach())
+    ga, gb = a.grad, b.grad
+    assert float((ga - gb).abs().max()) <= 1e-5 * float(ga.abs().max())
+    plan.close()
