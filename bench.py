@@ -846,26 +846,14 @@ def measure_gains(torch, binding, ctx, n_t, steps, warmup):
     g0 = torch.as_tensor(ws.gains.astype(np.complex64)).cuda()
     box = {}
 
-    class SquaredNorm(torch.autograd.Function):
-        """sum r^2 as a dot product; its gradient 2 r scaled in place."""
-
-        @staticmethod
-        def forward(fctx, r):
-            fctx.save_for_backward(r)
-            return torch.dot(r, r)
-
-        @staticmethod
-        def backward(fctx, gout):
-            (r,) = fctx.saved_tensors
-            return r.mul_(2.0 * float(gout))  # a host scalar keeps the kernel vectorized
-
     def step():
         g = g0.clone().requires_grad_(True)
         vis = autograd.apply_gains(g, model, ctx, n_ant, layers)
-        # residual image - model image straight from the imaging kernels (the
-        # library's reference-subtraction epilogue)
-        r = autograd.dirty_images(vis, plan, total, ref=target)
-        loss = SquaredNorm.apply(r)
+        # per-layer |image - model image|^2 from the imaging kernels (the
+        # library's reference-subtraction epilogue sums the squares as it
+        # stores the residual); the backward hands the stored residual and a
+        # per-layer factor to the adjoint, so no image-sized torch op runs
+        loss = autograd.image_sqnorm(vis, plan, total, ref=target).sum()
         loss.backward()
         box["vis"] = vis
         return g.grad

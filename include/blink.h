@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define BLINK_ABI_VERSION 1
+#define BLINK_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define BLINK_API __attribute__((visibility("default")))
@@ -170,6 +170,14 @@ BLINK_API int blink_degrid(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, c
                            int n_layers, const float *d_dimage, float *d_dvis, uint32_t flags, void *stream);
 BLINK_API int blink_plan_degrid(blink_plan *plan, const float *d_dimage, float *d_dvis, uint32_t flags,
                                 void *stream);
+/* blink_plan_degrid with the gradient of layer l (index into the plan's
+ * layer array) multiplied by d_layer_scale[l] (float32 [n_layers], device
+ * memory; NULL = 1).  For a loss f(s) of the per-layer sums of squares s_l of
+ * blink_epilogue.d_sqnorm, dL/dI_l = 2 (df/ds_l) r_l with r_l the stored
+ * output: pass the stored images as d_dimage and 2 df/ds_l as the scale, and
+ * no image-sized gradient is formed. */
+BLINK_API int blink_plan_degrid_scaled(blink_plan *plan, const float *d_dimage, const float *d_layer_scale,
+                                       float *d_dvis, uint32_t flags, void *stream);
 
 /* Per-antenna complex gains g (complex64 [n_ant]) on model visibilities
  * (antenna-level calibration, Sec. 4.2): d_vis[b] = g_i conj(g_j) d_model[b]
@@ -236,12 +244,25 @@ BLINK_API int blink_plan_image(blink_plan *plan, const float *d_vis, float *d_im
  *                transient search removed by subtracting a reference image of
  *                the same field).  With BLINK_NORMALIZE the dirty image is
  *                normalised first.  d_ref must not overlap the output
- *                extent (BLINK_ERR_INVALID). */
+ *                extent (BLINK_ERR_INVALID).
+ *   d_sqnorm     float64 [n_layers] in device memory, or NULL: layer l (index
+ *                into the plan's layer array) gets the sum over its N x N
+ *                output pixels of out^2, the output being what is stored
+ *                (with d_ref, the squared norm of the residual image, a
+ *                least-squares image loss).  Summed as the pixels are stored:
+ *                each transform task's 2 N2 squares in FP32 (N = N1 N2 the
+ *                four-step split), those sums in FP64, all in a fixed order
+ *                (the same bits on every call).  Needs the FFT transform: with
+ *                a tensor-core mode flag the call returns
+ *                BLINK_ERR_UNSUPPORTED.  The first call allocates 8 bytes per
+ *                layer and column item of the largest size (64 at 1024^2)
+ *                from the context's pool. */
 typedef struct {
     const float *d_gains;
     int64_t gain_stride;
     int64_t gain_period;
     const float *d_ref;
+    double *d_sqnorm;
 } blink_epilogue;
 
 BLINK_API int blink_plan_image_ex(blink_plan *plan, const float *d_vis, float *d_images, float *d_wsum,
@@ -265,7 +286,10 @@ BLINK_API int blink_plan_tuning(const blink_plan *plan, int group, int *n_px, in
  * 4 waves of two kernels (3 and 4: any size); wave_bytes = row-transform
  * scratch in use (the ring of path 3, a wave of path 4), 0 = default.
  * BLINK_ERR_INVALID for a path the group cannot take; the plan is unchanged
- * then. */
+ * then.  Path 2, and paths 3 and 4 on sizes whose full support always fits
+ * the fused kernels (their channels get no row buckets), grid with
+ * shared-memory atomics: equal within FP32 rounding, not the same bits from
+ * call to call (the autotuner may keep such a choice). */
 BLINK_API int blink_plan_set_tuning(blink_plan *plan, int group, int path, int64_t wave_bytes);
 
 /* CUDA graph of the plan's image launches: blink_plan_capture runs

@@ -30,6 +30,7 @@ EXPORTS = (
     "blink_apply_gains", "blink_gain_grad", "blink_plan_check", "blink_plan_autotune",
     "blink_plan_tuning", "blink_plan_set_tuning", "blink_plan_capture", "blink_plan_replay",
     "blink_plan_image_ex", "blink_ctx_set_wait_limit", "blink_probe_fma_peak",
+    "blink_plan_degrid_scaled",
 )
 
 
@@ -46,27 +47,36 @@ class Layer(ctypes.Structure):
 
 
 class Epilogue(ctypes.Structure):
-    """blink_epilogue: gains applied at gridding, reference image subtracted."""
+    """blink_epilogue: gains applied at gridding, reference image subtracted,
+    per-layer sums of squares of the output."""
     _fields_ = [("d_gains", ctypes.c_void_p), ("gain_stride", ctypes.c_int64),
-                ("gain_period", ctypes.c_int64), ("d_ref", ctypes.c_void_p)]
+                ("gain_period", ctypes.c_int64), ("d_ref", ctypes.c_void_p),
+                ("d_sqnorm", ctypes.c_void_p)]
 
 
-def _epilogue(gains, gain_stride, ref, gain_period=0):
-    """A blink_epilogue for the optional tensors (None when both are absent)."""
-    if gains is None and ref is None:
+def _epilogue(gains, gain_stride, ref, gain_period=0, sqnorm=None):
+    """A blink_epilogue for the optional tensors (None when all are absent)."""
+    if gains is None and ref is None and sqnorm is None:
         return None
-    _check_dev(gains, ref)
+    _check_dev(gains, ref, sqnorm)
     if gains is not None and gains.dtype != _complex64():
         raise ValueError("gains must be complex64")
     if ref is not None and ref.dtype != _float32():
         raise ValueError("reference images must be float32")
+    if sqnorm is not None and sqnorm.dtype != _float64():
+        raise ValueError("sqnorm must be float64")
     return Epilogue(0 if gains is None else gains.data_ptr(), int(gain_stride), int(gain_period),
-                    0 if ref is None else ref.data_ptr())
+                    0 if ref is None else ref.data_ptr(), 0 if sqnorm is None else sqnorm.data_ptr())
 
 
 def _complex64():
     import torch
     return torch.complex64
+
+
+def _float64():
+    import torch
+    return torch.float64
 
 
 def _float32():
@@ -120,6 +130,8 @@ def lib(path: str = LIB_PATH):
     L.blink_degrid.argtypes = [P, P, I, LP, I, P, P, ctypes.c_uint32, P]
     L.blink_plan_degrid.restype = I
     L.blink_plan_degrid.argtypes = [P, P, P, ctypes.c_uint32, P]
+    L.blink_plan_degrid_scaled.restype = I
+    L.blink_plan_degrid_scaled.argtypes = [P, P, P, P, ctypes.c_uint32, P]
     L.blink_apply_gains.restype = I
     L.blink_apply_gains.argtypes = [P, I, LP, I, P, P, P, P]
     L.blink_gain_grad.restype = I
@@ -344,13 +356,15 @@ class Plan:
         self.handle = h
 
     def image(self, vis, images_out, wsum_out=None, flags=0, stream=None, gains=None,
-              gain_stride=0, ref=None, gain_period=0):
+              gain_stride=0, ref=None, gain_period=0, sqnorm=None):
         """Dirty images of the plan's layers.  Optional fused epilogue: ``gains``
         (complex64, layer l uses the row at r * gain_stride, r = l mod
         gain_period or l) applied to the visibilities, ``ref`` (float32, laid
-        out like ``images_out``) subtracted from the images."""
+        out like ``images_out``) subtracted from the images, ``sqnorm``
+        (float64 [layers]) receiving each layer's sum of squares of the
+        stored output."""
         _check_dev(vis, images_out, wsum_out)
-        epi = _epilogue(gains, gain_stride, ref, gain_period)
+        epi = _epilogue(gains, gain_stride, ref, gain_period, sqnorm)
         if epi is None:
             st = self.ctx._lib.blink_plan_image(self.handle, _ptr(vis), _ptr(images_out),
                                                 _ptr(wsum_out), int(flags), _stream(stream))
@@ -360,10 +374,20 @@ class Plan:
                                                    _stream(stream))
         self.ctx._raise(st)
 
-    def degrid(self, dimage, dvis_out, flags=0, stream=None):
-        _check_dev(dimage, dvis_out)
-        self.ctx._raise(self.ctx._lib.blink_plan_degrid(self.handle, _ptr(dimage), _ptr(dvis_out),
-                                                        int(flags), _stream(stream)))
+    def degrid(self, dimage, dvis_out, flags=0, stream=None, layer_scale=None):
+        """Visibility gradient of the image gradient ``dimage``; with
+        ``layer_scale`` (float32 [layers]) layer l's result is multiplied by
+        layer_scale[l]."""
+        _check_dev(dimage, dvis_out, layer_scale)
+        if layer_scale is None:
+            st = self.ctx._lib.blink_plan_degrid(self.handle, _ptr(dimage), _ptr(dvis_out), int(flags),
+                                                 _stream(stream))
+        else:
+            if layer_scale.dtype != _float32():
+                raise ValueError("layer_scale must be float32")
+            st = self.ctx._lib.blink_plan_degrid_scaled(self.handle, _ptr(dimage), _ptr(layer_scale),
+                                                        _ptr(dvis_out), int(flags), _stream(stream))
+        self.ctx._raise(st)
 
     def autotune(self, vis, images_out, stream=None):
         """Time the candidate kernel configurations per image size, keep the fastest."""
@@ -388,11 +412,11 @@ class Plan:
                                                             int(wave_bytes)))
 
     def capture(self, vis, images_out, wsum_out=None, flags=0, stream=None, gains=None,
-                gain_stride=0, ref=None, gain_period=0):
+                gain_stride=0, ref=None, gain_period=0, sqnorm=None):
         """Record the batch's launches (with the optional epilogue) into a CUDA
         graph bound to these buffers."""
         _check_dev(vis, images_out, wsum_out)
-        epi = _epilogue(gains, gain_stride, ref, gain_period)
+        epi = _epilogue(gains, gain_stride, ref, gain_period, sqnorm)
         self.ctx._raise(self.ctx._lib.blink_plan_capture(
             self.handle, _ptr(vis), _ptr(images_out), _ptr(wsum_out), int(flags),
             None if epi is None else ctypes.byref(epi), _stream(stream)))

@@ -108,6 +108,8 @@ struct blink_plan {
     size_t cg_bytes = 0;
     float2 *d_gprod = nullptr;     // gain-product table of the fused epilogue (on first use)
     size_t gprod_bytes = 0;
+    double *d_sqpart = nullptr;    // per-layer partial sums of squares (on first use)
+    int sq_stride = 0;             // slots per layer: the most column items of any group
     cudaStream_t last_stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaGraphExec_t graph = nullptr;     // captured image launches (blink_plan_capture)
@@ -214,6 +216,8 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     p->d_gscratch = nullptr;
     if (p->d_gprod) cudaFreeAsync(p->d_gprod, st);
     p->d_gprod = nullptr;
+    if (p->d_sqpart) cudaFreeAsync(p->d_sqpart, st);
+    p->d_sqpart = nullptr;
     if (p->d_queue) cudaFreeAsync(p->d_queue, st);
     p->d_queue = nullptr;
     p->queue_bytes = 0;
@@ -646,6 +650,7 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
         return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
     const float *d_gains = epi ? epi->d_gains : nullptr;
     const float *d_ref = epi ? epi->d_ref : nullptr;
+    double *d_sqnorm = epi ? epi->d_sqnorm : nullptr;
     if (epi && (epi->gain_stride < 0 || epi->gain_period < 0))
         return fail(ctx, BLINK_ERR_INVALID, "gain_stride and gain_period must be >= 0");
     if (d_gains && p->n_ant >= 65536) return fail(ctx, BLINK_ERR_UNSUPPORTED, "gains need fewer than 65536 antennas");
@@ -657,9 +662,22 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
         if (r0 < i0 + ext && i0 < r0 + ext)
             return fail(ctx, BLINK_ERR_INVALID, "reference images overlap the output");
     }
+    if (d_sqnorm && mode)
+        return fail(ctx, BLINK_ERR_UNSUPPORTED, "per-layer sums of squares need the FFT transform (no tensor-core mode)");
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     p->last_stream = st;
+    if (d_sqnorm && !p->d_sqpart && p->n_layers) {
+        int stride = 1;
+        for (const auto &grp : p->groups) stride = std::max(stride, blink::sq_slots(grp.n_px));
+        void *ptr = nullptr;
+        const cudaError_t e =
+            cudaMallocFromPoolAsync(&ptr, size_t(p->n_layers) * size_t(stride) * sizeof(double), ctx->pool, st);
+        if (e != cudaSuccess)
+            return fail(ctx, BLINK_ERR_WORKSPACE, std::string("partial sums of squares: ") + cudaGetErrorString(e));
+        p->d_sqpart = static_cast<double *>(ptr);
+        p->sq_stride = stride;
+    }
     // gain products g_i conj(g_j) once per distinct gain row, when they fit
     const float2 *gprod = nullptr;
     if (d_gains && p->nb > 0) {
@@ -724,6 +742,10 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
         a.gain_period = epi ? epi->gain_period : 0;
         a.gprod = gprod;
         a.ref = d_ref;
+        if (d_sqnorm) {
+            a.sq_part = p->d_sqpart;
+            a.sq_stride = p->sq_stride;
+        }
         Error e;
         if (gemm_ok(grp)) {
             a.scratch = p->d_gscratch;
@@ -733,6 +755,10 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
         } else {
             e = blink::launch_image_group(grp.n_px, a, st);
         }
+        if (e.status) return fail(ctx, e);
+    }
+    if (d_sqnorm) {
+        Error e = blink::launch_sq_totals(p->d_sqpart, p->sq_stride, p->n_layers, d_sqnorm, st);
         if (e.status) return fail(ctx, e);
     }
     return BLINK_OK;
@@ -896,6 +922,11 @@ int blink_plan_replay(blink_plan *p, void *stream) {
 }
 
 int blink_plan_degrid(blink_plan *p, const float *d_dimage, float *d_dvis, uint32_t flags, void *stream) {
+    return blink_plan_degrid_scaled(p, d_dimage, nullptr, d_dvis, flags, stream);
+}
+
+int blink_plan_degrid_scaled(blink_plan *p, const float *d_dimage, const float *d_layer_scale, float *d_dvis,
+                             uint32_t flags, void *stream) {
     if (!p) return BLINK_ERR_INVALID;
     blink_ctx *ctx = p->ctx;
     if (p->n_layers && (!d_dimage || !d_dvis)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
@@ -920,6 +951,7 @@ int blink_plan_degrid(blink_plan *p, const float *d_dimage, float *d_dvis, uint3
         blink::ImageArgs a = group_args(p, grp, nullptr, nullptr, nullptr, flags);
         a.scratch = p->d_dscratch;
         a.scratch_bytes = p->dscratch_bytes;
+        a.lscale = d_layer_scale;
         Error e = blink::launch_degrid_group(grp.n_px, a, d_dimage, reinterpret_cast<float2 *>(d_dvis), st);
         if (e.status) return fail(ctx, e);
     }

@@ -78,6 +78,24 @@ __global__ void __launch_bounds__(kGridNT) k_grid_full(ImageArgs a, int n) {
     if (blockIdx.x == 0 && tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
 }
 
+// ------------------------------------------- per-layer sums of squares
+// One warp per layer: lane i adds slots i, i + 32, ... in order, then a fixed
+// shuffle tree; the same bits on every run.
+constexpr int kSqWarps = 8;
+
+__global__ void __launch_bounds__(32 * kSqWarps) k_sq_totals(const double *part, int stride, int n_layers,
+                                                             double *out) {
+    const int lane = threadIdx.x & 31;
+    const int l = blockIdx.x * kSqWarps + (threadIdx.x >> 5);
+    if (l >= n_layers) return;  // whole warps leave together
+    const double *row = part + int64_t(l) * stride;
+    double s = 0.0;
+    for (int i = lane; i < stride; i += 32) s += row[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[l] = s;
+}
+
 // ------------------------------------------------------------ adjoint
 // Gradient of a real image loss with respect to the visibilities:
 // gamma_b = 2 w_b H[k_b], H = forward 2-D DFT (exp(-2 pi i k.(p - N/2)/N)) of
@@ -147,6 +165,21 @@ Error launch_degrid_group(int n_px, const ImageArgs &a, const float *resid, floa
     BLINK_FOR_EACH_SIZE(X)
 #undef X
     return Error{-2, "unsupported image size " + std::to_string(n_px)};
+}
+
+int sq_slots(int n_px) {
+#define X(N_) if (n_px == N_) return SizeOps<N_>::sq_slots();
+    BLINK_FOR_EACH_SIZE(X)
+#undef X
+    return 0;
+}
+
+Error launch_sq_totals(const double *part, int stride, int n_layers, double *out, cudaStream_t st) {
+    if (n_layers <= 0) return Error{0, ""};
+    const unsigned blocks = unsigned((n_layers + kSqWarps - 1) / kSqWarps);
+    k_sq_totals<<<blocks, 32 * kSqWarps, 0, st>>>(part, stride, n_layers, out);
+    BLINK_CUDA_TRY(cudaGetLastError());
+    return Error{0, ""};
 }
 
 Error launch_grid_group(int n_px, const ImageArgs &a, cudaStream_t st) {

@@ -262,13 +262,17 @@ __device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow2 hrow
 }
 
 // Pass 2, step B: N2-point transforms, then the two real image columns of
-// each pair (adjacent) with the fftshift folded into the addresses.
-template <int N, int P, class ZL>
-__device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img, float scale,
-                                            int tid, int nt, const float *ref) {
+// each pair (adjacent) with the fftshift folded into the addresses.  With
+// want_sq the sum of the squares of the stored values is returned (valid in
+// thread 0; each task's 2 N2 squares in FP32, the tasks' sums in FP64, in a
+// fixed order).
+template <int N, int P, class ZL, int NT>
+__device__ __forceinline__ double cols_step_b(const float2 *Z, int j0, float *img, float scale,
+                                              int tid, const float *ref, bool want_sq = false) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
     const bool pair_store = ((reinterpret_cast<uintptr_t>(img) | reinterpret_cast<uintptr_t>(ref)) & 7) == 0;
-    for (int t = tid; t < P * N1; t += nt) {
+    double acc = 0.0;
+    for (int t = tid; t < P * N1; t += NT) {
         const int jj = t % P, k1 = t / P;
         const int q = j0 + jj;
         if (q >= H) continue;
@@ -278,6 +282,7 @@ __device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img,
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[ZL::phys(N2 * k1 + n2)];
         dft<N2, +1>(y);
+        float sq = 0.f;
         // stores in batches of KB rows; with the fused epilogue each batch's
         // reference values are requested together before its stores
         constexpr int KB = N2 % 4 == 0 ? 4 : 1;
@@ -310,9 +315,12 @@ __device__ __forceinline__ void cols_step_b(const float2 *Z, int j0, float *img,
                     __stcs(o, v.x);
                     __stcs(o + 1, v.y);
                 }
+                if (want_sq) sq = fmaf(v.x, v.x, fmaf(v.y, v.y, sq));
             }
         }
+        if (want_sq) acc += double(sq);
     }
+    return want_sq ? block_sum_f64<NT>(acc, tid) : 0.0;
 }
 
 // Grid the canonical rows [r0, r0 + nrows) of one layer into G (stride S).
@@ -539,7 +547,12 @@ __device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L,
     __syncthreads();
     consumed();  // every read of Hs has landed in registers or shared memory
     const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
-    cols_step_b<N, P, ZL>(sm, j0, out + L.out_off, scale, tid, NT, EPI && ref ? ref + L.out_off : nullptr);
+    const bool want_sq = EPI && a.sq_part;
+    const double sq = cols_step_b<N, P, ZL, NT>(sm, j0, out + L.out_off, scale, tid,
+                                                EPI && ref ? ref + L.out_off : nullptr, want_sq);
+    if (want_sq)  // one slot per column item
+        store_sq_slot<NT>(a.sq_part + int64_t(L.layer) * a.sq_stride, j0 / P, (N / 2 + P - 1) / P, a.sq_stride,
+                          sq, tid);
 }
 
 template <int N>
@@ -873,7 +886,8 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT) k_degrid_rows(ImageArgs a, fl
     __syncthreads();
     rows_fft<N, -1, true>(sm, S, nrows, tid, NT, tw);
     const float *w = ci.weighting == 1 ? a.wgt + ci.wgt_off : nullptr;
-    const float scale = 2.f * (((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f);
+    const float scale = 2.f * (((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f) *
+                        (a.lscale ? __ldg(a.lscale + L.layer) : 1.f);
     if (a.csr && ci.csr_off >= 0) {
         const CsrLayout cl(N, a.nb);
         const int32_t *ptr = reinterpret_cast<const int32_t *>(a.csr + ci.csr_off + cl.row_ptr);
@@ -981,7 +995,7 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     const size_t ring = a.wave_budget ? std::min(a.scratch_bytes, std::max(a.wave_budget, per_layer)) : a.scratch_bytes;
     q.slots = int(std::max<size_t>(1, std::min<size_t>(ring / per_layer, size_t(q.n))));
     const size_t smem = large_smem<N>(a.r_alloc);
-    auto kern = a.ref ? k_large<N, true> : k_large<N, false>;
+    auto kern = (a.ref || a.sq_part) ? k_large<N, true> : k_large<N, false>;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int dev = 0, sms = 0, per_sm = 0;
     BLINK_CUDA_TRY(cudaGetDevice(&dev));
@@ -1023,7 +1037,7 @@ Error launch_large_body(const ImageArgs &a, cudaStream_t st) {
     const size_t smem_cols = cols_smem<N>(a.r_alloc);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         int(smem_rows)));
-    auto cols = a.ref ? k_cols<N, true> : k_cols<N, false>;
+    auto cols = (a.ref || a.sq_part) ? k_cols<N, true> : k_cols<N, false>;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_cols)));
     const unsigned bands = unsigned((a.r_alloc + RowsCfg<N>::RB - 1) / RowsCfg<N>::RB);
     const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
@@ -1095,5 +1109,8 @@ bool SizeOps<N>::small(int r_alloc) { return use_small<N>(r_alloc); }
 
 template <int N>
 size_t SizeOps<N>::scratch_per_layer(int r_alloc) { return scratch_per_layer_n<N>(r_alloc); }
+
+template <int N>
+int SizeOps<N>::sq_slots() { return (N / 2 + LargeCfg<N>::P - 1) / LargeCfg<N>::P; }
 
 }  // namespace blink

@@ -140,9 +140,41 @@ __device__ __forceinline__ void grid_layer_vec(float2 *G, int S, const uint32_t 
 // Both passes of the transform for one layer whose canonical rows [0, R) are
 // in G (stride N + 1), Hermitian-complete in row 0.  Rows >= 1 are multiplied
 // by w_rows (uniform weights, [N/2][N]) on the way in when it is not null.
+// Sum of one double per thread over the CTA, in a fixed order (a shuffle
+// tree per warp, then the warps' sums in warp order), so the result has the
+// same bits on every run; valid in thread 0.  Every thread calls it.
+template <int NT>
+__device__ __forceinline__ double block_sum_f64(double v, int tid) {
+    __shared__ double red[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();  // the previous call's reads of red are done
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < NT / 32; ++w) s += red[w];
+    return s;
+}
+
+// Sum of squares of a layer's output (the fused epilogue's per-layer norm):
+// slot `slot` of the layer's row of partial sums gets `s`; with slot 0 the
+// caller also zeroes slots [used, stride), which its size never writes, so
+// that the per-layer total can add a fixed number of slots.
+template <int NT>
+__device__ __forceinline__ void store_sq_slot(double *row, int slot, int used, int stride, double s, int tid) {
+    if (tid == 0) row[slot] = s;
+    if (slot == 0)
+        for (int i = used + tid; i < stride; i += NT) row[i] = 0.0;
+}
+
+// With want_sq, the sum of the squares of the stored values is returned
+// (valid in thread 0): each task's squares (2 N2 values) added in FP32, the
+// tasks' sums in FP64, in a fixed order.
 template <int N>
-__device__ __forceinline__ void small_transform(float2 *G, float2 *Z, int R, const float *w_rows,
-                                                float *img, float scale, int tid, const float *ref) {
+__device__ __forceinline__ double small_transform(float2 *G, float2 *Z, int R, const float *w_rows,
+                                                  float *img, float scale, int tid, const float *ref,
+                                                  bool want_sq = false) {
     constexpr int NT = SmallCfg<N>::NT, GR = SmallCfg<N>::GROUPS, P = SmallCfg<N>::P;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, S = N + 1, H = N / 2;
     const int ln = tid & 15, grp = tid >> 4;
@@ -155,6 +187,7 @@ __device__ __forceinline__ void small_transform(float2 *G, float2 *Z, int R, con
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) tw[k1] = four_step_tw<N, +1>(k1, n2c);
     }
+    double acc = 0.0;  // squares of the stored values (want_sq)
 
     // pass 1, step A
     for (int r = grp; r < R; r += GR) {
@@ -245,6 +278,7 @@ __device__ __forceinline__ void small_transform(float2 *G, float2 *Z, int R, con
 #pragma unroll
                     for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[n2];
                     dft<N2, +1>(y);
+                    float sq = 0.f;
 #pragma unroll
                     for (int k2 = 0; k2 < N2; ++k2) {
                         const int q = k1 + N1 * k2;
@@ -257,12 +291,15 @@ __device__ __forceinline__ void small_transform(float2 *G, float2 *Z, int R, con
                         }
                         __stcs(img + o + ja + H, va);
                         __stcs(img + o + ja, vb);
+                        if (want_sq) sq = fmaf(va, va, fmaf(vb, vb, sq));
                     }
+                    if (want_sq) acc += double(sq);
                 }
             }
         }
         __syncthreads();
     }
+    return want_sq ? block_sum_f64<NT>(acc, tid) : 0.0;
 }
 
 // L2 eviction policies (createpolicy): visibilities are read once, so they
@@ -347,7 +384,10 @@ __global__ void __launch_bounds__(SmallCfg<N>::NT, 2) k_image_small(ImageArgs a,
     }
     __syncthreads();
     const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
-    small_transform<N>(G, Z, R, w, out + L.out_off, scale, tid, EPI && ref ? ref + L.out_off : nullptr);
+    const bool want_sq = EPI && a.sq_part;
+    const double sq = small_transform<N>(G, Z, R, w, out + L.out_off, scale, tid,
+                                         EPI && ref ? ref + L.out_off : nullptr, want_sq);
+    if (want_sq) store_sq_slot<NT>(a.sq_part + int64_t(L.layer) * a.sq_stride, 0, 1, a.sq_stride, sq, tid);
     if (tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
 }
 
@@ -543,7 +583,10 @@ __global__ void __launch_bounds__(SmallCfg<N>::NT, 2) k_image_sched(ImageArgs a,
     }
     __syncthreads();
     const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
-    small_transform<N>(G, Z, R, nullptr, out + L.out_off, scale, tid, EPI && ref ? ref + L.out_off : nullptr);
+    const bool want_sq = EPI && a.sq_part;
+    const double sq = small_transform<N>(G, Z, R, nullptr, out + L.out_off, scale, tid,
+                                         EPI && ref ? ref + L.out_off : nullptr, want_sq);
+    if (want_sq) store_sq_slot<NT>(a.sq_part + int64_t(L.layer) * a.sq_stride, 0, 1, a.sq_stride, sq, tid);
     if (tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
 }
 
@@ -564,7 +607,7 @@ bool launch_fused_n(const ImageArgs &a, cudaStream_t st, Error &err) {
         size_t smem = small_smem<N>(a.r_alloc);
         const bool sched = a.sched && a.sched_ok && a.force_path != 2;
         if (sched) smem = std::max(smem, size_t(StageLayout(a.max_chunk, a.max_seg, kSchedSlots).bytes));
-        const bool epi = a.gains || a.ref;
+        const bool epi = a.gains || a.ref || a.sq_part;
         auto kern = sched ? (epi ? k_image_sched<N, true> : k_image_sched<N, false>)
                           : (epi ? k_image_small<N, true> : k_image_small<N, false>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -71,6 +71,14 @@ struct ImageArgs {
     int64_t cg_stride = 0;
     int cg_cap = 0;
     int cg_l0 = 0;
+    // fused epilogue's per-layer sum of squares of the output: the kernels
+    // write partial sums to sq_part[caller layer * sq_stride + slot] (slot =
+    // column item; slots a size does not use are zeroed), launch_sq_totals
+    // adds each row in slot order.  Null: not computed.
+    double *sq_part = nullptr;
+    int sq_stride = 0;
+    // adjoint: per caller layer factor on the visibility gradient (or null)
+    const float *lscale = nullptr;
 };
 
 // Compact gridding (blink_compact.cu) of layers [l0, l0 + cnt) of a.layers
@@ -92,6 +100,7 @@ struct SizeOps {
     static Error degrid(const ImageArgs &a, const float *resid, float2 *dvis, cudaStream_t st);
     static bool small(int r_alloc);
     static size_t scratch_per_layer(int r_alloc);
+    static int sq_slots();
 };
 
 bool image_size_supported(int n_px);
@@ -118,6 +127,11 @@ size_t dftgemm_scratch_per_layer(int n_px, int r_alloc);
 // Layer-independent part of that scratch (DFT tables of both passes).
 size_t dftgemm_scratch_fixed(int n_px, int r_alloc, int kmax);
 Error launch_dftgemm_group(int n_px, int mode, const ImageArgs &a, cudaStream_t st);
+
+// Slots of sq_part one layer of size n_px can use (its column items).
+int sq_slots(int n_px);
+// out[l] = sum over s < stride of part[l * stride + s], in slot order.
+Error launch_sq_totals(const double *part, int stride, int n_layers, double *out, cudaStream_t st);
 
 // Adjoint of the image path: resid (float [N][N] at out_off) -> dvis
 // (complex64 at vis_off).  Needs degrid_scratch_per_layer() bytes per layer.

@@ -40,7 +40,7 @@ def test_binding_lists_every_declared_symbol():
 
 def test_abi_version_and_sizes(lib):
     from paper_2405_13478_gb300 import binding
-    assert lib.blink_abi_version() == 1
+    assert lib.blink_abi_version() == 2
     sizes = binding.supported_sizes()
     for n in (128, 180, 256, 512, 1024):
         assert n in sizes
