@@ -863,14 +863,22 @@ def measure_gains(torch, binding, ctx, n_t, steps, warmup):
     img = autograd.dirty_images(box["vis"].detach(), plan, total)  # the forward images, for the error check
     err = _sample_error(torch, ws, layers, box["vis"].detach(), img.detach(), [0, L - 1])
     n2 = 1024 * 1024
-    per_image = 8 * B + 4 * n2 + 4 * n2 + 8 * B   # vis in, image out, dL/dI in, dL/dV out
+    # what the step has to move: the model visibilities and the model image in
+    # (the visibilities, the residual image, its gradient and the visibility
+    # gradient are intermediates: the residual is summed and column-transformed
+    # where it is formed); an unfused step also writes and re-reads the image
+    # and its gradient and the visibility gradient
+    per_image = 8 * B + 4 * n2
+    unfused = 8 * B + 4 * n2 + 4 * n2 + 8 * B   # vis in, image out, dL/dI in, dL/dV out
     plan.close()
     return {"workload": f"station: 256 antennas, {n_t} steps x 8 channels, 1024^2 images, gains on a "
                         "20-source model, loss = sum (image - model image)^2, forward + backward",
             "layers": L, "images_per_s": L / (ms / 1e3), "ms_per_step": ms, "clocks": clk,
             "err_vs_oracle": err, "err_what": "forward images vs the oracle (gradients: GPU tests)",
             "l2": f"inputs larger than L2 ({2 * total * 4 / 1e9:.2f} GB of images and image gradients)",
-            "roofline": _hbm_roofline(L * per_image, ms, "whole forward + backward step", per_image)}
+            "roofline": dict(_hbm_roofline(L * per_image, ms, "whole forward + backward step", per_image),
+                             unfused_bytes_per_image=unfused,
+                             frac_of_unfused_bytes=L * unfused / (ms / 1e3) / 1e9 / measured_peaks()[0])}
 
 
 def _standalone(args, fn, n_default, **kw):

@@ -178,6 +178,14 @@ BLINK_API int blink_plan_degrid(blink_plan *plan, const float *d_dimage, float *
  * no image-sized gradient is formed. */
 BLINK_API int blink_plan_degrid_scaled(blink_plan *plan, const float *d_dimage, const float *d_layer_scale,
                                        float *d_dvis, uint32_t flags, void *stream);
+/* Bytes of the d_adjoint buffer of blink_epilogue for this plan. */
+BLINK_API int blink_plan_adjoint_bytes(const blink_plan *plan, int64_t *bytes);
+/* blink_plan_degrid_scaled(plan, images, d_layer_scale, ...) for the images
+ * a blink_plan_image_ex call stored while it filled d_adjoint: the second
+ * half of the adjoint (DFT along u of the kept rows, gather at each
+ * baseline's cell) only.  Same results as that call, bit for bit. */
+BLINK_API int blink_plan_degrid_adjoint(blink_plan *plan, const float *d_adjoint, const float *d_layer_scale,
+                                        float *d_dvis, uint32_t flags, void *stream);
 
 /* Per-antenna complex gains g (complex64 [n_ant]) on model visibilities
  * (antenna-level calibration, Sec. 4.2): d_vis[b] = g_i conj(g_j) d_model[b]
@@ -256,13 +264,30 @@ BLINK_API int blink_plan_image(blink_plan *plan, const float *d_vis, float *d_im
  *                a tensor-core mode flag the call returns
  *                BLINK_ERR_UNSUPPORTED.  The first call allocates 8 bytes per
  *                layer and column item of the largest size (64 at 1024^2)
- *                from the context's pool. */
+ *                from the context's pool.
+ *   d_adjoint    device buffer of blink_plan_adjoint_bytes bytes (8-byte
+ *                aligned), or NULL: receives the first half of blink_degrid
+ *                applied to the stored output -- the forward DFT along v of
+ *                every image column, rows k < R of the support -- so that
+ *                blink_plan_degrid_adjoint can later finish the adjoint
+ *                without reading the images again.  Where the column pass
+ *                holds exactly one 16-column strip of the image per CTA
+ *                (1024^2 on the FFT path) the strip is transformed in shared
+ *                memory as it is stored; other sizes and the tensor-core
+ *                modes transform the stored images after their launch.
+ *                Layout: per size group in plan order, per layer of the
+ *                group, r_alloc rows of N complex64 (FFT-order columns).
+ *                With d_adjoint set, d_images may be NULL: no image is
+ *                stored (sizes whose columns come from stored images image
+ *                into a temporary array of the plan's output extent from the
+ *                context's pool, freed in stream order). */
 typedef struct {
     const float *d_gains;
     int64_t gain_stride;
     int64_t gain_period;
     const float *d_ref;
     double *d_sqnorm;
+    float *d_adjoint;
 } blink_epilogue;
 
 BLINK_API int blink_plan_image_ex(blink_plan *plan, const float *d_vis, float *d_images, float *d_wsum,

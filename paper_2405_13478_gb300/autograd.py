@@ -5,9 +5,10 @@ kernels; its backward runs the library's adjoint kernels (forward FFT of the
 image gradient + degridding, ``blink_plan_degrid``), recomputing from the
 plan instead of storing grids.  ``image_sqnorm(vis, plan, ...)`` returns
 each layer's sum of squares of the (residual) image, formed by the fused
-epilogue as the image is stored; its backward passes the stored image and a
-per-layer factor to ``blink_plan_degrid_scaled``, so no image-sized gradient
-is ever formed.  ``apply_gains(gains, model, ...)`` forms
+epilogue as the image is stored, and keeps the adjoint's column transforms
+of the stored image (``blink_epilogue.d_adjoint``); its backward finishes the
+adjoint from those with a per-layer factor (``blink_plan_degrid_adjoint``),
+so no image-sized gradient is formed and the images are not read again.  ``apply_gains(gains, model, ...)`` forms
 V_ij = g_i conj(g_j) M_ij with ``blink_apply_gains``; its backward is
 ``blink_gain_grad``.  Gradients follow torch's complex convention
 dL/dRe + i dL/dIm.  No image-sized computation happens in torch: it
@@ -59,18 +60,22 @@ class _ImageSqNorm(torch.autograd.Function):
         if vis.dtype != torch.complex64 or not vis.is_cuda:
             raise ValueError("vis must be a complex64 CUDA tensor")
         vis = vis.contiguous()
-        out = torch.empty(n_out, dtype=torch.float32, device=vis.device)
         sq = torch.empty(plan.n_layers, dtype=torch.float64, device=vis.device)
-        plan.image(vis, out, None, flags, ref=None if ref is None else ref.detach().contiguous(), sqnorm=sq)
+        adj = torch.empty(plan.adjoint_bytes() // 4, dtype=torch.float32, device=vis.device)
+        # no image array: the residual is summed and column-transformed as it
+        # is formed, never stored
+        plan.image(vis, None, None, flags, ref=None if ref is None else ref.detach().contiguous(), sqnorm=sq,
+                   adjoint=adj)
         ctx.plan, ctx.flags, ctx.vis_shape = plan, flags, vis.shape
-        ctx.resid = out  # the stored (residual) images: dL/dI_l = 2 dL/ds_l * resid_l
+        # the residual's column transforms: dL/dI_l = 2 dL/ds_l * resid_l
+        ctx.adj = adj
         return sq
 
     @staticmethod
     def backward(ctx, grad_sq):
         scale = (2.0 * grad_sq).to(torch.float32).contiguous()
         dvis = torch.zeros(ctx.vis_shape, dtype=torch.complex64, device=grad_sq.device)
-        ctx.plan.degrid(ctx.resid, dvis, ctx.flags, layer_scale=scale)
+        ctx.plan.degrid_adjoint(ctx.adj, dvis, ctx.flags, layer_scale=scale)
         return dvis, None, None, None, None
 
 
@@ -78,8 +83,9 @@ def image_sqnorm(vis: torch.Tensor, plan: "binding.Plan", n_out: int, flags: int
                  ref: torch.Tensor | None = None):
     """Float64 [layers]: layer l's sum over its pixels of (image - ref)^2
     (of the image alone without ``ref``), summed by the fused epilogue as the
-    image is stored (``n_out`` floats of image storage are kept for the
-    backward).  A least-squares image loss is ``image_sqnorm(...).sum()``."""
+    image is formed (no image is stored: the backward starts from the
+    adjoint's column transforms of the residual, r_alloc x N complex values
+    per layer; ``n_out`` is accepted for symmetry with dirty_images).  A least-squares image loss is ``image_sqnorm(...).sum()``."""
     return _ImageSqNorm.apply(vis, plan, n_out, flags, ref)
 
 

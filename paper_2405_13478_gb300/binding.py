@@ -30,7 +30,7 @@ EXPORTS = (
     "blink_apply_gains", "blink_gain_grad", "blink_plan_check", "blink_plan_autotune",
     "blink_plan_tuning", "blink_plan_set_tuning", "blink_plan_capture", "blink_plan_replay",
     "blink_plan_image_ex", "blink_ctx_set_wait_limit", "blink_probe_fma_peak",
-    "blink_plan_degrid_scaled",
+    "blink_plan_degrid_scaled", "blink_plan_adjoint_bytes", "blink_plan_degrid_adjoint",
 )
 
 
@@ -51,14 +51,14 @@ class Epilogue(ctypes.Structure):
     per-layer sums of squares of the output."""
     _fields_ = [("d_gains", ctypes.c_void_p), ("gain_stride", ctypes.c_int64),
                 ("gain_period", ctypes.c_int64), ("d_ref", ctypes.c_void_p),
-                ("d_sqnorm", ctypes.c_void_p)]
+                ("d_sqnorm", ctypes.c_void_p), ("d_adjoint", ctypes.c_void_p)]
 
 
-def _epilogue(gains, gain_stride, ref, gain_period=0, sqnorm=None):
+def _epilogue(gains, gain_stride, ref, gain_period=0, sqnorm=None, adjoint=None):
     """A blink_epilogue for the optional tensors (None when all are absent)."""
-    if gains is None and ref is None and sqnorm is None:
+    if gains is None and ref is None and sqnorm is None and adjoint is None:
         return None
-    _check_dev(gains, ref, sqnorm)
+    _check_dev(gains, ref, sqnorm, adjoint)
     if gains is not None and gains.dtype != _complex64():
         raise ValueError("gains must be complex64")
     if ref is not None and ref.dtype != _float32():
@@ -66,7 +66,8 @@ def _epilogue(gains, gain_stride, ref, gain_period=0, sqnorm=None):
     if sqnorm is not None and sqnorm.dtype != _float64():
         raise ValueError("sqnorm must be float64")
     return Epilogue(0 if gains is None else gains.data_ptr(), int(gain_stride), int(gain_period),
-                    0 if ref is None else ref.data_ptr(), 0 if sqnorm is None else sqnorm.data_ptr())
+                    0 if ref is None else ref.data_ptr(), 0 if sqnorm is None else sqnorm.data_ptr(),
+                    0 if adjoint is None else adjoint.data_ptr())
 
 
 def _complex64():
@@ -132,6 +133,10 @@ def lib(path: str = LIB_PATH):
     L.blink_plan_degrid.argtypes = [P, P, P, ctypes.c_uint32, P]
     L.blink_plan_degrid_scaled.restype = I
     L.blink_plan_degrid_scaled.argtypes = [P, P, P, P, ctypes.c_uint32, P]
+    L.blink_plan_adjoint_bytes.restype = I
+    L.blink_plan_adjoint_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    L.blink_plan_degrid_adjoint.restype = I
+    L.blink_plan_degrid_adjoint.argtypes = [P, P, P, P, ctypes.c_uint32, P]
     L.blink_apply_gains.restype = I
     L.blink_apply_gains.argtypes = [P, I, LP, I, P, P, P, P]
     L.blink_gain_grad.restype = I
@@ -356,15 +361,17 @@ class Plan:
         self.handle = h
 
     def image(self, vis, images_out, wsum_out=None, flags=0, stream=None, gains=None,
-              gain_stride=0, ref=None, gain_period=0, sqnorm=None):
+              gain_stride=0, ref=None, gain_period=0, sqnorm=None, adjoint=None):
         """Dirty images of the plan's layers.  Optional fused epilogue: ``gains``
         (complex64, layer l uses the row at r * gain_stride, r = l mod
         gain_period or l) applied to the visibilities, ``ref`` (float32, laid
         out like ``images_out``) subtracted from the images, ``sqnorm``
         (float64 [layers]) receiving each layer's sum of squares of the
-        stored output."""
+        stored output, ``adjoint`` (float32, adjoint_bytes() / 4 elements)
+        receiving the adjoint's column transforms of the stored output for
+        degrid_adjoint()."""
         _check_dev(vis, images_out, wsum_out)
-        epi = _epilogue(gains, gain_stride, ref, gain_period, sqnorm)
+        epi = _epilogue(gains, gain_stride, ref, gain_period, sqnorm, adjoint)
         if epi is None:
             st = self.ctx._lib.blink_plan_image(self.handle, _ptr(vis), _ptr(images_out),
                                                 _ptr(wsum_out), int(flags), _stream(stream))
@@ -388,6 +395,20 @@ class Plan:
             st = self.ctx._lib.blink_plan_degrid_scaled(self.handle, _ptr(dimage), _ptr(layer_scale),
                                                         _ptr(dvis_out), int(flags), _stream(stream))
         self.ctx._raise(st)
+
+    def adjoint_bytes(self) -> int:
+        n = ctypes.c_int64()
+        self.ctx._raise(self.ctx._lib.blink_plan_adjoint_bytes(self.handle, ctypes.byref(n)))
+        return int(n.value)
+
+    def degrid_adjoint(self, adjoint, dvis_out, flags=0, stream=None, layer_scale=None):
+        """degrid(images, ...) for the images whose column transforms an
+        image(..., adjoint=) call kept in ``adjoint``."""
+        _check_dev(adjoint, dvis_out, layer_scale)
+        if layer_scale is not None and layer_scale.dtype != _float32():
+            raise ValueError("layer_scale must be float32")
+        self.ctx._raise(self.ctx._lib.blink_plan_degrid_adjoint(self.handle, _ptr(adjoint), _ptr(layer_scale),
+                                                                _ptr(dvis_out), int(flags), _stream(stream)))
 
     def autotune(self, vis, images_out, stream=None):
         """Time the candidate kernel configurations per image size, keep the fastest."""

@@ -498,6 +498,15 @@ int build_plan(blink_ctx *ctx, const double *d_ant_xyz, int n_ant, const blink_l
     return BLINK_OK;
 }
 
+// Complex elements of the kept adjoint columns before group g (slots of
+// r_alloc rows of N per layer, groups in plan order); g == groups: the total.
+static int64_t adjoint_offset(const blink_plan *p, size_t g) {
+    int64_t off = 0;
+    for (size_t k = 0; k < g && k < p->groups.size(); ++k)
+        off += int64_t(p->groups[k].count) * p->groups[k].r_alloc * p->groups[k].n_px;
+    return off;
+}
+
 blink::ImageArgs group_args(const blink_plan *p, const blink_plan::Group &g, const float *d_vis,
                             void *out, float *d_wsum, uint32_t flags) {
     blink::ImageArgs a{};
@@ -644,17 +653,21 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
                         const blink_epilogue *epi, void *stream) {
     if (!p) return BLINK_ERR_INVALID;
     blink_ctx *ctx = p->ctx;
-    if (p->n_layers && (!d_vis || !d_images)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    if (p->n_layers && (!d_vis || (!d_images && !(epi && epi->d_adjoint))))
+        return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
     const uint32_t mode = (flags & BLINK_TRANSFORM_MASK) >> 4;
     if ((flags & ~uint32_t(BLINK_NORMALIZE | BLINK_TRANSFORM_MASK)) || mode > 4)
         return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
     const float *d_gains = epi ? epi->d_gains : nullptr;
     const float *d_ref = epi ? epi->d_ref : nullptr;
     double *d_sqnorm = epi ? epi->d_sqnorm : nullptr;
+    float *d_adjoint = epi ? epi->d_adjoint : nullptr;
+    if (d_adjoint && (reinterpret_cast<uintptr_t>(d_adjoint) & 7))
+        return fail(ctx, BLINK_ERR_INVALID, "adjoint buffer must be 8-byte aligned");
     if (epi && (epi->gain_stride < 0 || epi->gain_period < 0))
         return fail(ctx, BLINK_ERR_INVALID, "gain_stride and gain_period must be >= 0");
     if (d_gains && p->n_ant >= 65536) return fail(ctx, BLINK_ERR_UNSUPPORTED, "gains need fewer than 65536 antennas");
-    if (d_ref) {
+    if (d_ref && d_images) {
         // the kernels read the reference and write the output through
         // non-aliasing (restrict) pointers: the two extents must not overlap
         const uintptr_t r0 = reinterpret_cast<uintptr_t>(d_ref), i0 = reinterpret_cast<uintptr_t>(d_images);
@@ -735,8 +748,26 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
             if (rc) return rc;
             break;
         }
-    for (const auto &grp : p->groups) {
-        blink::ImageArgs a = group_args(p, grp, d_vis, d_images, d_wsum, flags & BLINK_NORMALIZE);
+    // without an output array (d_adjoint set), groups whose adjoint columns
+    // come from stored images image into a temporary array from the pool
+    float *d_tmp = nullptr;
+    if (!d_images && p->n_layers) {
+        bool need = false;
+        for (const auto &grp : p->groups) need = need || gemm_ok(grp) || !blink::adjoint_fusable(grp.n_px);
+        if (need) {
+            void *ptr = nullptr;
+            const cudaError_t e = cudaMallocFromPoolAsync(&ptr, size_t(p->out_extent) * sizeof(float), ctx->pool, st);
+            if (e != cudaSuccess)
+                return fail(ctx, BLINK_ERR_WORKSPACE, std::string("temporary images: ") + cudaGetErrorString(e));
+            d_tmp = static_cast<float *>(ptr);
+        }
+    }
+    for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+        const auto &grp = p->groups[gi];
+        float *img = d_images;
+        if (!img && (gemm_ok(grp) || !blink::adjoint_fusable(grp.n_px))) img = d_tmp;
+        blink::ImageArgs a = group_args(p, grp, d_vis, img, d_wsum, flags & BLINK_NORMALIZE);
+        float2 *adj = d_adjoint ? reinterpret_cast<float2 *>(d_adjoint) + adjoint_offset(p, gi) : nullptr;
         a.gains = reinterpret_cast<const float2 *>(d_gains);
         a.gain_stride = epi ? epi->gain_stride : 0;
         a.gain_period = epi ? epi->gain_period : 0;
@@ -752,11 +783,18 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
             a.scratch_bytes = p->gscratch_bytes;
             e = blink::launch_dftgemm_group(grp.n_px, int(mode), a, st);
             if (!e.status && d_wsum) e = blink::launch_wsum_copy(a, st);
+            // the adjoint's columns from the stored images
+            if (!e.status && adj) e = blink::launch_degrid_cols_group(grp.n_px, a, img, adj, st);
         } else {
+            a.adj = adj;
             e = blink::launch_image_group(grp.n_px, a, st);
         }
-        if (e.status) return fail(ctx, e);
+        if (e.status) {
+            if (d_tmp) cudaFreeAsync(d_tmp, st);
+            return fail(ctx, e);
+        }
     }
+    if (d_tmp) cudaFreeAsync(d_tmp, st);
     if (d_sqnorm) {
         Error e = blink::launch_sq_totals(p->d_sqpart, p->sq_stride, p->n_layers, d_sqnorm, st);
         if (e.status) return fail(ctx, e);
@@ -953,6 +991,34 @@ int blink_plan_degrid_scaled(blink_plan *p, const float *d_dimage, const float *
         a.scratch_bytes = p->dscratch_bytes;
         a.lscale = d_layer_scale;
         Error e = blink::launch_degrid_group(grp.n_px, a, d_dimage, reinterpret_cast<float2 *>(d_dvis), st);
+        if (e.status) return fail(ctx, e);
+    }
+    return BLINK_OK;
+}
+
+int blink_plan_adjoint_bytes(const blink_plan *p, int64_t *bytes) {
+    if (!p || !bytes) return BLINK_ERR_INVALID;
+    *bytes = adjoint_offset(p, p->groups.size()) * int64_t(sizeof(float2));
+    return BLINK_OK;
+}
+
+int blink_plan_degrid_adjoint(blink_plan *p, const float *d_adjoint, const float *d_layer_scale, float *d_dvis,
+                              uint32_t flags, void *stream) {
+    if (!p) return BLINK_ERR_INVALID;
+    blink_ctx *ctx = p->ctx;
+    if (p->n_layers && (!d_adjoint || !d_dvis)) return fail(ctx, BLINK_ERR_INVALID, "null data pointer");
+    if (reinterpret_cast<uintptr_t>(d_adjoint) & 7)
+        return fail(ctx, BLINK_ERR_INVALID, "adjoint buffer must be 8-byte aligned");
+    if (flags & ~uint32_t(BLINK_NORMALIZE)) return fail(ctx, BLINK_ERR_INVALID, "unknown flags");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    p->last_stream = st;
+    for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+        const auto &grp = p->groups[gi];
+        blink::ImageArgs a = group_args(p, grp, nullptr, nullptr, nullptr, flags);
+        a.lscale = d_layer_scale;
+        const float2 *in = reinterpret_cast<const float2 *>(d_adjoint) + adjoint_offset(p, gi);
+        Error e = blink::launch_degrid_rows_group(grp.n_px, a, in, reinterpret_cast<float2 *>(d_dvis), st);
         if (e.status) return fail(ctx, e);
     }
     return BLINK_OK;

@@ -167,6 +167,13 @@ Error launch_degrid_group(int n_px, const ImageArgs &a, const float *resid, floa
     return Error{-2, "unsupported image size " + std::to_string(n_px)};
 }
 
+bool adjoint_fusable(int n_px) {
+#define X(N_) if (n_px == N_) return SizeOps<N_>::adj_fusable();
+    BLINK_FOR_EACH_SIZE(X)
+#undef X
+    return false;
+}
+
 int sq_slots(int n_px) {
 #define X(N_) if (n_px == N_) return SizeOps<N_>::sq_slots();
     BLINK_FOR_EACH_SIZE(X)
@@ -180,6 +187,20 @@ Error launch_sq_totals(const double *part, int stride, int n_layers, double *out
     k_sq_totals<<<blocks, 32 * kSqWarps, 0, st>>>(part, stride, n_layers, out);
     BLINK_CUDA_TRY(cudaGetLastError());
     return Error{0, ""};
+}
+
+Error launch_degrid_cols_group(int n_px, const ImageArgs &a, const float *resid, float2 *out, cudaStream_t st) {
+#define X(N_) if (n_px == N_) return SizeOps<N_>::degrid_cols(a, resid, out, st);
+    BLINK_FOR_EACH_SIZE(X)
+#undef X
+    return Error{-2, "unsupported image size " + std::to_string(n_px)};
+}
+
+Error launch_degrid_rows_group(int n_px, const ImageArgs &a, const float2 *in, float2 *dvis, cudaStream_t st) {
+#define X(N_) if (n_px == N_) return SizeOps<N_>::degrid_rows(a, in, dvis, st);
+    BLINK_FOR_EACH_SIZE(X)
+#undef X
+    return Error{-2, "unsupported image size " + std::to_string(n_px)};
 }
 
 Error launch_grid_group(int n_px, const ImageArgs &a, cudaStream_t st) {

@@ -261,17 +261,100 @@ __device__ __forceinline__ void cols_step_a(float2 *Z, int R, int j0, HRow2 hrow
     }
 }
 
+template <int N>
+struct DegridCfg;
+template <int N>
+struct AdjFusable;
+template <int N>
+__device__ __forceinline__ void degrid_cols_strip(float2 *sm, int R, int x0, float2 *__restrict__ out, int tid);
+
+// The N2 results y of one pass-2 step-B task (pair jj, FFT-order rows
+// k1 + N1 k2) as image values: scaled, the reference subtracted, stored at
+// image column xa and xa + 1 (when img is set) and at strip[row][2 jj] (when
+// strip is set: FFT-order rows of 16 floats).  Returns the sum of their
+// squares in FP32 when want_sq.
+template <int N>
+__device__ __forceinline__ float store_task(const float2 (&y)[Plan<N>::N2], int k1, int xa, int jj, float *img,
+                                            float scale, const float *ref, bool pair_store, bool want_sq,
+                                            float *strip) {
+    constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
+    float sq = 0.f;
+    // stores in batches of KB rows; with the fused epilogue each batch's
+    // reference values are requested together before its stores
+    constexpr int KB = N2 % 4 == 0 ? 4 : 1;
+#pragma unroll
+    for (int kb = 0; kb < N2; kb += KB) {
+        float2 rf[KB];
+        if (ref) {
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+                const int qq = k1 + N1 * (kb + u);
+                const float *rp = ref + (qq < H ? qq + H : qq - H) * N + xa;  // 32-bit: N * N < 2^31
+                rf[u] = pair_store ? __ldcs(reinterpret_cast<const float2 *>(rp))
+                                   : make_float2(__ldcs(rp), __ldcs(rp + 1));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int k2 = kb + u;
+            const int qq = k1 + N1 * k2;              // FFT-order row
+            const int row = qq < H ? qq + H : qq - H; // fftshift
+            float2 v = make_float2(y[k2].x * scale, y[k2].y * scale);
+            if (ref) {
+                v.x -= rf[u].x;
+                v.y -= rf[u].y;
+            }
+            if (img) {
+                float *o = img + row * N + xa;        // offsets inside one image fit 32 bits
+                if (pair_store) {
+                    __stcs(reinterpret_cast<float2 *>(o), v);
+                } else {
+                    __stcs(o, v.x);
+                    __stcs(o + 1, v.y);
+                }
+            }
+            if (strip) *reinterpret_cast<float2 *>(strip + qq * 16 + 2 * jj) = v;
+            if (want_sq) sq = fmaf(v.x, v.x, fmaf(v.y, v.y, sq));
+        }
+    }
+    return sq;
+}
+
 // Pass 2, step B: N2-point transforms, then the two real image columns of
 // each pair (adjacent) with the fftshift folded into the addresses.  With
 // want_sq the sum of the squares of the stored values is returned (valid in
 // thread 0; each task's 2 N2 squares in FP32, the tasks' sums in FP64, in a
-// fixed order).
+// fixed order).  With adj (sizes whose column item is one 16-column strip of
+// the image: AdjFusable), the CTA's values also go to a strip in Z's buffer
+// and the adjoint's column transforms of that strip (rows k < R) go to adj.
 template <int N, int P, class ZL, int NT>
-__device__ __forceinline__ double cols_step_b(const float2 *Z, int j0, float *img, float scale,
-                                              int tid, const float *ref, bool want_sq = false) {
+__device__ __forceinline__ double cols_step_b(float2 *Z, int j0, float *img, float scale, int tid,
+                                              const float *ref, bool want_sq = false, float2 *adj = nullptr,
+                                              int R = 0) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
     const bool pair_store = ((reinterpret_cast<uintptr_t>(img) | reinterpret_cast<uintptr_t>(ref)) & 7) == 0;
     double acc = 0.0;
+    if constexpr (AdjFusable<N>::value) {
+        if (adj) {
+            // one task per thread, every pair inside the image: all reads of
+            // Z land in registers before the barrier that hands its buffer to
+            // the strip
+            const int jj = tid % P, k1 = tid / P;
+            const int xa = (2 * (j0 + jj) + H) % N;
+            const float2 *zp = Z + jj * ZL::S;
+            float2 y[N2];
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[ZL::phys(N2 * k1 + n2)];
+            dft<N2, +1>(y);
+            __syncthreads();
+            const float sq = store_task<N>(y, k1, xa, jj, img, scale, ref, pair_store, want_sq,
+                                           reinterpret_cast<float *>(Z));
+            if (want_sq) acc = double(sq);
+            __syncthreads();  // the strip is complete
+            degrid_cols_strip<N>(Z, R, (2 * j0 + H) % N, adj, tid);
+            return want_sq ? block_sum_f64<NT>(acc, tid) : 0.0;
+        }
+    }
     for (int t = tid; t < P * N1; t += NT) {
         const int jj = t % P, k1 = t / P;
         const int q = j0 + jj;
@@ -282,42 +365,7 @@ __device__ __forceinline__ double cols_step_b(const float2 *Z, int j0, float *im
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[ZL::phys(N2 * k1 + n2)];
         dft<N2, +1>(y);
-        float sq = 0.f;
-        // stores in batches of KB rows; with the fused epilogue each batch's
-        // reference values are requested together before its stores
-        constexpr int KB = N2 % 4 == 0 ? 4 : 1;
-#pragma unroll
-        for (int kb = 0; kb < N2; kb += KB) {
-            float2 rf[KB];
-            if (ref) {
-#pragma unroll
-                for (int u = 0; u < KB; ++u) {
-                    const int qq = k1 + N1 * (kb + u);
-                    const float *rp = ref + (qq < H ? qq + H : qq - H) * N + xa;  // 32-bit: N * N < 2^31
-                    rf[u] = pair_store ? __ldcs(reinterpret_cast<const float2 *>(rp))
-                                       : make_float2(__ldcs(rp), __ldcs(rp + 1));
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < KB; ++u) {
-                const int k2 = kb + u;
-                const int qq = k1 + N1 * k2;              // FFT-order row
-                const int row = qq < H ? qq + H : qq - H; // fftshift
-                float *o = img + row * N + xa;            // offsets inside one image fit 32 bits
-                float2 v = make_float2(y[k2].x * scale, y[k2].y * scale);
-                if (ref) {
-                    v.x -= rf[u].x;
-                    v.y -= rf[u].y;
-                }
-                if (pair_store) {
-                    __stcs(reinterpret_cast<float2 *>(o), v);
-                } else {
-                    __stcs(o, v.x);
-                    __stcs(o + 1, v.y);
-                }
-                if (want_sq) sq = fmaf(v.x, v.x, fmaf(v.y, v.y, sq));
-            }
-        }
+        const float sq = store_task<N>(y, k1, xa, jj, img, scale, ref, pair_store, want_sq, nullptr);
         if (want_sq) acc += double(sq);
     }
     return want_sq ? block_sum_f64<NT>(acc, tid) : 0.0;
@@ -534,7 +582,7 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
 template <int N, bool EPI, bool NARROW, class Consumed>
 __device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L, const ChanInfo &ci, int j0,
                                           const float2 *Hs, float *__restrict__ out, const float *__restrict__ ref,
-                                          float2 *sm, int tid, Consumed &&consumed) {
+                                          float2 *sm, int tid, Consumed &&consumed, int lidx = 0) {
     constexpr int NT = LargeCfg<N>::NT, P = LargeCfg<N>::P;
     using ZL = ZLayout<N, P>;
     const int R = ci.rows;
@@ -548,8 +596,11 @@ __device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L,
     consumed();  // every read of Hs has landed in registers or shared memory
     const float scale = ((a.flags & kNormalize) && ci.wsum > 0.f) ? 1.f / ci.wsum : 1.f;
     const bool want_sq = EPI && a.sq_part;
-    const double sq = cols_step_b<N, P, ZL, NT>(sm, j0, out + L.out_off, scale, tid,
-                                                EPI && ref ? ref + L.out_off : nullptr, want_sq);
+    // fused adjoint columns: layer lidx of the group's slots (r_alloc rows of N)
+    float2 *adj = EPI && a.adj ? a.adj + int64_t(lidx) * a.r_alloc * N : nullptr;
+    // (no output array: the fused adjoint keeps the columns, no image is stored)
+    const double sq = cols_step_b<N, P, ZL, NT>(sm, j0, out ? out + L.out_off : nullptr, scale, tid,
+                                                EPI && ref ? ref + L.out_off : nullptr, want_sq, adj, R);
     if (want_sq)  // one slot per column item
         store_sq_slot<NT>(a.sq_part + int64_t(L.layer) * a.sq_stride, j0 / P, (N / 2 + P - 1) / P, a.sq_stride,
                           sq, tid);
@@ -573,7 +624,7 @@ __global__ void __launch_bounds__(LargeCfg<N>::NT, 3) k_cols(ImageArgs a, int l0
     const DevLayer L = a.layers[l0 + lw];
     const ChanInfo ci = a.chans[L.chan];
     cols_item<N, EPI, true>(a, L, ci, blockIdx.x * LargeCfg<N>::P, a.scratch + int64_t(lw) * a.r_alloc * N, out, ref, sm,
-                      threadIdx.x, [] {});
+                            threadIdx.x, [] {}, l0 + lw);
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
 }
 
@@ -729,7 +780,7 @@ __global__ void __launch_bounds__(256, (EPI || Plan<N>::N1 == 24) ? 2 : 3)
                 // stores do not gate its reuse
                 cols_item<N, EPI, false>(a, L, ci, sub * LargeCfg<N>::P, Hs, out, ref, sm, tid, [&] {
                     if (tid == 0) atomicAdd(Q.cols_done + layer, 1);
-                });
+                }, layer);
                 if (sub == 0 && tid == 0 && a.wsum_out) a.wsum_out[L.layer] = ci.wsum;
             }
         }
@@ -753,6 +804,14 @@ struct DegridCfg {
     static_assert(P * Plan<N>::N2 <= NT && P * Plan<N>::N1 <= NT, "one four-step task per thread");
 };
 
+// The column item of the forward pass is exactly one strip of the adjoint's
+// column kernel (16 adjacent image columns, one task per thread in both).
+template <int N>
+struct AdjFusable {
+    static constexpr bool value = LargeCfg<N>::P == DegridCfg<N>::P && LargeCfg<N>::NT == DegridCfg<N>::NT &&
+                                  LargeCfg<N>::P * Plan<N>::N1 == LargeCfg<N>::NT && (N / 2) % LargeCfg<N>::P == 0;
+};
+
 template <int N>
 size_t degrid_cols_smem() {
     using C = DegridCfg<N>;
@@ -770,41 +829,21 @@ size_t degrid_cols_smem() {
 // the two real columns' transforms go to scratch[lw][k][j] (FFT-order column
 // j = image column + N/2 mod N), 16 adjacent columns per row.
 // Grid: (N / 16, layers in wave).
+// The column transforms of one 16-column strip already in shared memory
+// (strip[n][c], FFT-order row n = image row (n + N/2) mod N, c < 16, 64-byte
+// rows): rows k < R of the two real columns of every pair go to
+// out[k][(x0 + c + N/2) mod N] (row stride N).  The strip's buffer is reused:
+// it must hold max(N * 16 floats, P * ZL::S, P * ZN complex).  Every thread
+// of the CTA calls it (NT = DegridCfg<N>::NT).
 template <int N>
-__global__ void __launch_bounds__(DegridCfg<N>::NT, 3) k_degrid_cols(ImageArgs a, const float *resid, int l0) {
+__device__ __forceinline__ void degrid_cols_strip(float2 *sm, int R, int x0, float2 *__restrict__ out, int tid) {
     using C = DegridCfg<N>;
     using ZL = typename C::ZL;
-    constexpr int NT = C::NT, P = C::P, W = C::W, H = N / 2;
+    constexpr int P = C::P, W = C::W, H = N / 2;
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
-    extern __shared__ float2 sm[];
-    float *strip = reinterpret_cast<float *>(sm);  // [N][W]: FFT-order row n = image row (n + H) mod N
-    float2 *Z = sm;                                // [P][ZL::S] four-step intermediate
-    float2 *zn = sm;                               // [P][ZN] natural order
-    const int lw = blockIdx.y;
-    const DevLayer L = a.layers[l0 + lw];
-    const ChanInfo ci = a.chans[L.chan];
-    const int R = ci.rows;
-    const int x0 = blockIdx.x * 2 * P;             // first image column
-    const int nc = min(2 * P, N - x0);             // columns of this CTA (the last may be partial)
-    const int tid = threadIdx.x;
-    const float *img = resid + L.out_off;
-    if (nc == 2 * P && (reinterpret_cast<uintptr_t>(img) & 15) == 0 && (N % 4) == 0) {
-        // every 16-byte piece in flight at once, straight into shared memory
-        for (int i = tid; i < N * (2 * P / 4); i += NT) {
-            const int y = i / (2 * P / 4), q = i % (2 * P / 4);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(uint32_t(__cvta_generic_to_shared(
-                             strip + ((y + H) % N) * W + 4 * q))),
-                         "l"(img + int64_t(y) * N + x0 + 4 * q)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-    } else {
-        for (int i = tid; i < N * 2 * P; i += NT) {
-            const int y = i / (2 * P), c = i % (2 * P);
-            strip[((y + H) % N) * W + c] = c < nc ? __ldcs(img + int64_t(y) * N + x0 + c) : 0.f;
-        }
-    }
-    __syncthreads();
+    const float *strip = reinterpret_cast<const float *>(sm);
+    float2 *Z = sm;   // [P][ZL::S] four-step intermediate
+    float2 *zn = sm;  // [P][ZN] natural order
     // step A: pair p, n2; z = R_a + i R_b along stride N2, forward twiddles
     const int pa = tid % P, n2 = tid / P;
     const bool task_a = n2 < N2;
@@ -844,8 +883,7 @@ __global__ void __launch_bounds__(DegridCfg<N>::NT, 3) k_degrid_cols(ImageArgs a
     __syncthreads();
     // unpack the two real columns of each pair and keep rows k < R; image
     // column x goes to FFT-order column (x + N/2) mod N
-    float2 *out = a.scratch + int64_t(lw) * a.r_alloc * N;
-    for (int i = tid; i < R * P; i += NT) {
+    for (int i = tid; i < R * P; i += C::NT) {
         const int k = i / P, p = i % P;
         const int xa = x0 + 2 * p;
         if (xa >= N) continue;
@@ -855,6 +893,49 @@ __global__ void __launch_bounds__(DegridCfg<N>::NT, 3) k_degrid_cols(ImageArgs a
         if (xa + 1 < N)
             out[int64_t(k) * N + (xa + 1 + H) % N] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
     }
+}
+
+// Forward column transforms of the image gradient (the first half of the
+// adjoint's forward 2-D FFT).  CTA x of a layer takes the 16 adjacent image
+// columns [16 x, 16 x + 16) -- one 64-byte piece of every image row, read
+// once -- as 8 pairs of real columns, each pair one complex N-point transform
+// (z = R_a + i R_b).  The strip, the four-step intermediate and the
+// natural-order result share one buffer: every task holds its inputs in
+// registers across a barrier before the buffer is overwritten.  Rows k < R of
+// the two real columns' transforms go to scratch[lw][k][j] (FFT-order column
+// j = image column + N/2 mod N), 16 adjacent columns per row.
+// Grid: (N / 16, layers in wave).
+template <int N>
+__global__ void __launch_bounds__(DegridCfg<N>::NT, 3) k_degrid_cols(ImageArgs a, const float *resid, int l0) {
+    using C = DegridCfg<N>;
+    constexpr int NT = C::NT, P = C::P, W = C::W, H = N / 2;
+    extern __shared__ float2 sm[];
+    float *strip = reinterpret_cast<float *>(sm);  // [N][W]: FFT-order row n = image row (n + H) mod N
+    const int lw = blockIdx.y;
+    const DevLayer L = a.layers[l0 + lw];
+    const ChanInfo ci = a.chans[L.chan];
+    const int x0 = blockIdx.x * 2 * P;             // first image column
+    const int nc = min(2 * P, N - x0);             // columns of this CTA (the last may be partial)
+    const int tid = threadIdx.x;
+    const float *img = resid + L.out_off;
+    if (nc == 2 * P && (reinterpret_cast<uintptr_t>(img) & 15) == 0 && (N % 4) == 0) {
+        // every 16-byte piece in flight at once, straight into shared memory
+        for (int i = tid; i < N * (2 * P / 4); i += NT) {
+            const int y = i / (2 * P / 4), q = i % (2 * P / 4);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(uint32_t(__cvta_generic_to_shared(
+                             strip + ((y + H) % N) * W + 4 * q))),
+                         "l"(img + int64_t(y) * N + x0 + 4 * q)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    } else {
+        for (int i = tid; i < N * 2 * P; i += NT) {
+            const int y = i / (2 * P), c = i % (2 * P);
+            strip[((y + H) % N) * W + c] = c < nc ? __ldcs(img + int64_t(y) * N + x0 + c) : 0.f;
+        }
+    }
+    __syncthreads();
+    degrid_cols_strip<N>(sm, ci.rows, x0, a.scratch + int64_t(lw) * a.r_alloc * N, tid);
 }
 
 // Grid: (bands of RB rows, layers in wave).  gamma goes to dvis at vis_off.
@@ -971,6 +1052,42 @@ Error launch_degrid_n(const ImageArgs &a, const float *resid, float2 *dvis, cuda
     return Error{0, ""};
 }
 
+// The adjoint's column transforms of every layer's image (resid) into the
+// slots out[l][k][p] (r_alloc rows of N per layer, FFT-order columns): the
+// first half of blink_degrid, kept for a later row pass.
+template <int N>
+Error launch_degrid_cols_n(const ImageArgs &a, const float *resid, float2 *out, cudaStream_t st) {
+    using C = DegridCfg<N>;
+    const size_t smem_c = degrid_cols_smem<N>();
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_c)));
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_cols<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    const unsigned pchunks = unsigned((N + 2 * C::P - 1) / (2 * C::P));
+    for (int l0 = 0; l0 < a.n_layers; l0 += 65535) {
+        const int cnt = std::min(65535, a.n_layers - l0);
+        ImageArgs b = a;
+        b.scratch = out + int64_t(l0) * a.r_alloc * N;
+        k_degrid_cols<N><<<dim3(pchunks, unsigned(cnt)), C::NT, smem_c, st>>>(b, resid, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+    }
+    return Error{0, ""};
+}
+
+// The adjoint's row pass from kept column transforms (slots as above).
+template <int N>
+Error launch_degrid_rows_n(const ImageArgs &a, const float2 *in, float2 *dvis, cudaStream_t st) {
+    const size_t smem_r = rows_smem<N>();
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_degrid_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_r)));
+    const unsigned bands = unsigned((a.r_alloc + LargeCfg<N>::RB - 1) / LargeCfg<N>::RB);
+    for (int l0 = 0; l0 < a.n_layers; l0 += 65535) {
+        const int cnt = std::min(65535, a.n_layers - l0);
+        ImageArgs b = a;
+        b.scratch = const_cast<float2 *>(in) + int64_t(l0) * a.r_alloc * N;
+        k_degrid_rows<N><<<dim3(bands, unsigned(cnt)), LargeCfg<N>::NT, smem_r, st>>>(b, dvis, l0);
+        BLINK_CUDA_TRY(cudaGetLastError());
+    }
+    return Error{0, ""};
+}
+
 template <int N>
 bool use_small(int r_alloc) {
     return N <= 256 && small_path_fits(N, r_alloc);
@@ -995,7 +1112,7 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     const size_t ring = a.wave_budget ? std::min(a.scratch_bytes, std::max(a.wave_budget, per_layer)) : a.scratch_bytes;
     q.slots = int(std::max<size_t>(1, std::min<size_t>(ring / per_layer, size_t(q.n))));
     const size_t smem = large_smem<N>(a.r_alloc);
-    auto kern = (a.ref || a.sq_part) ? k_large<N, true> : k_large<N, false>;
+    auto kern = (a.ref || a.sq_part || a.adj) ? k_large<N, true> : k_large<N, false>;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int dev = 0, sms = 0, per_sm = 0;
     BLINK_CUDA_TRY(cudaGetDevice(&dev));
@@ -1037,7 +1154,7 @@ Error launch_large_body(const ImageArgs &a, cudaStream_t st) {
     const size_t smem_cols = cols_smem<N>(a.r_alloc);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         int(smem_rows)));
-    auto cols = (a.ref || a.sq_part) ? k_cols<N, true> : k_cols<N, false>;
+    auto cols = (a.ref || a.sq_part || a.adj) ? k_cols<N, true> : k_cols<N, false>;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_cols)));
     const unsigned bands = unsigned((a.r_alloc + RowsCfg<N>::RB - 1) / RowsCfg<N>::RB);
     const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
@@ -1056,11 +1173,23 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
     if (a.n_layers == 0) return Error{0, ""};
     {
         Error e;
-        if (launch_fused_n<N>(a, st, e)) return e;
+        if (launch_fused_n<N>(a, st, e)) {
+            // the fused small-image kernels keep no column strips: the
+            // adjoint's columns are transformed from the stored images
+            if (!e.status && a.adj) e = launch_degrid_cols_n<N>(a, static_cast<const float *>(a.out), a.adj, st);
+            return e;
+        }
     }
     const size_t per_layer = size_t(a.r_alloc) * N * sizeof(float2);
     if (!a.scratch || a.scratch_bytes < per_layer)
         return Error{-5, "row-transform scratch too small for image size " + std::to_string(N)};
+    if (!AdjFusable<N>::value && a.adj) {
+        ImageArgs b = a;
+        b.adj = nullptr;
+        Error e = launch_image_n<N>(b, st);
+        if (!e.status) e = launch_degrid_cols_n<N>(a, static_cast<const float *>(a.out), a.adj, st);
+        return e;
+    }
     if (!a.cg) return launch_large_body<N>(a, st);
     // compact gridding, one wave of the compact-grid buffer at a time, each
     // wave followed by its rows and columns
@@ -1069,6 +1198,7 @@ Error launch_image_n(const ImageArgs &a, cudaStream_t st) {
         b.layers = a.layers + l0;
         b.n_layers = std::min(a.cg_cap, a.n_layers - l0);
         b.cg_l0 = 0;
+        if (a.adj) b.adj = a.adj + int64_t(l0) * a.r_alloc * N;
         Error e = launch_grid_compact(b, 0, b.n_layers, st);
         if (e.status) return e;
         e = launch_large_body<N>(b, st);
@@ -1105,6 +1235,18 @@ Error SizeOps<N>::degrid(const ImageArgs &a, const float *resid, float2 *dvis, c
 }
 
 template <int N>
+Error SizeOps<N>::degrid_rows(const ImageArgs &a, const float2 *in, float2 *dvis, cudaStream_t st) {
+    if (a.n_layers == 0) return Error{0, ""};
+    return launch_degrid_rows_n<N>(a, in, dvis, st);
+}
+
+template <int N>
+Error SizeOps<N>::degrid_cols(const ImageArgs &a, const float *resid, float2 *out, cudaStream_t st) {
+    if (a.n_layers == 0) return Error{0, ""};
+    return launch_degrid_cols_n<N>(a, resid, out, st);
+}
+
+template <int N>
 bool SizeOps<N>::small(int r_alloc) { return use_small<N>(r_alloc); }
 
 template <int N>
@@ -1112,5 +1254,8 @@ size_t SizeOps<N>::scratch_per_layer(int r_alloc) { return scratch_per_layer_n<N
 
 template <int N>
 int SizeOps<N>::sq_slots() { return (N / 2 + LargeCfg<N>::P - 1) / LargeCfg<N>::P; }
+
+template <int N>
+bool SizeOps<N>::adj_fusable() { return AdjFusable<N>::value; }
 
 }  // namespace blink

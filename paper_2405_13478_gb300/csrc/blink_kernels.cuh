@@ -79,6 +79,9 @@ struct ImageArgs {
     int sq_stride = 0;
     // adjoint: per caller layer factor on the visibility gradient (or null)
     const float *lscale = nullptr;
+    // fused epilogue: the adjoint's column transforms of the stored output,
+    // r_alloc rows of N complex per layer of the group (or null)
+    float2 *adj = nullptr;
 };
 
 // Compact gridding (blink_compact.cu) of layers [l0, l0 + cnt) of a.layers
@@ -98,9 +101,12 @@ struct SizeOps {
     static Error image(const ImageArgs &a, cudaStream_t st);
     static Error rows_wave(const ImageArgs &a, int l0, int cnt, cudaStream_t st);
     static Error degrid(const ImageArgs &a, const float *resid, float2 *dvis, cudaStream_t st);
+    static Error degrid_rows(const ImageArgs &a, const float2 *in, float2 *dvis, cudaStream_t st);
+    static Error degrid_cols(const ImageArgs &a, const float *resid, float2 *out, cudaStream_t st);
     static bool small(int r_alloc);
     static size_t scratch_per_layer(int r_alloc);
     static int sq_slots();
+    static bool adj_fusable();
 };
 
 bool image_size_supported(int n_px);
@@ -128,6 +134,9 @@ size_t dftgemm_scratch_per_layer(int n_px, int r_alloc);
 size_t dftgemm_scratch_fixed(int n_px, int r_alloc, int kmax);
 Error launch_dftgemm_group(int n_px, int mode, const ImageArgs &a, cudaStream_t st);
 
+// Whether the column pass of size n_px (FFT path) transforms the adjoint's
+// columns as it stores them (else they come from the stored images).
+bool adjoint_fusable(int n_px);
 // Slots of sq_part one layer of size n_px can use (its column items).
 int sq_slots(int n_px);
 // out[l] = sum over s < stride of part[l * stride + s], in slot order.
@@ -137,6 +146,10 @@ Error launch_sq_totals(const double *part, int stride, int n_layers, double *out
 // (complex64 at vis_off).  Needs degrid_scratch_per_layer() bytes per layer.
 size_t degrid_scratch_per_layer(int n_px, int r_alloc);
 Error launch_degrid_group(int n_px, const ImageArgs &a, const float *resid, float2 *dvis, cudaStream_t st);
+// The two halves of that adjoint with the column transforms kept in between
+// (slots of r_alloc rows of N complex per layer of the group).
+Error launch_degrid_cols_group(int n_px, const ImageArgs &a, const float *resid, float2 *out, cudaStream_t st);
+Error launch_degrid_rows_group(int n_px, const ImageArgs &a, const float2 *in, float2 *dvis, cudaStream_t st);
 
 // Antenna gains (blink_gains.cu): vis = g_i conj(g_j) model per layer, and
 // the per-antenna gradient accumulated over all layers.

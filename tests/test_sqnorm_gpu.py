@@ -214,3 +214,70 @@ def test_autograd_sqnorm_loss(torch, ctx, n_px):
     ga, gb = a.grad, b.grad
     assert float((ga - gb).abs().max()) <= 1e-5 * float(ga.abs().max())
     plan.close()
+
+
+@pytest.mark.parametrize("case,path,flags", [("mixed", None, 0), ("mixed", 3, 1), ("mixed", 4, 0),
+                                             ("compact1024", None, 0), ("compact1024", 3, 0),
+                                             ("compact512", None, 0x20)])
+def test_kept_adjoint_is_the_adjoint_of_the_stored_images(torch, ctx, case, path, flags):
+    """blink_plan_degrid_adjoint from the columns kept by the forward (fused
+    into the 1024^2 column pass, or from the stored images elsewhere and in
+    the tensor-core modes) gives the bits of blink_plan_degrid_scaled on the
+    stored images."""
+    from paper_2405_13478_gb300 import binding
+    if case == "mixed":
+        ws, layers, vis = mixed_case(29)
+    else:
+        ws, layers, vis = compact_case(6, int(case[len("compact"):]))
+    layers, total = binding.layer_out_offsets(layers)
+    plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
+    force(plan, path)
+    rng = np.random.default_rng(2)
+    d_vis = vis.reshape(-1).cuda()
+    ref = torch.as_tensor(rng.normal(0, 1.0, total).astype(np.float32)).cuda()
+    out = torch.empty(total, device="cuda")
+    adj = torch.full((plan.adjoint_bytes() // 4,), float("nan"), device="cuda")
+    plan.image(d_vis, out, flags=flags, ref=ref, adjoint=adj)
+    plan.check()
+    scale = torch.as_tensor(rng.normal(size=len(layers)).astype(np.float32)).cuda()
+    nb = ws.n_baselines
+    d1 = torch.zeros(len(layers) * nb, dtype=torch.complex64, device="cuda")
+    d2 = torch.zeros_like(d1)
+    nflag = flags & binding.NORMALIZE
+    plan.degrid(out, d1, nflag, layer_scale=scale)
+    plan.degrid_adjoint(adj, d2, nflag, layer_scale=scale)
+    torch.cuda.synchronize()
+    assert torch.isfinite(torch.view_as_real(d1)).all()
+    assert torch.equal(d1, d2)
+    plan.close()
+
+
+@pytest.mark.parametrize("case", ["mixed", "compact1024"])
+def test_no_image_output_with_kept_adjoint(torch, ctx, case):
+    """With the adjoint columns kept, the image array may be omitted: the
+    sums of squares and the kept columns are the bits of a call that stores
+    the images (1024^2 fused; other sizes through a temporary array)."""
+    from paper_2405_13478_gb300 import binding
+    ws, layers, vis = mixed_case(31) if case == "mixed" else compact_case(8, 1024)
+    layers, total = binding.layer_out_offsets(layers)
+    plan = ctx.plan(torch.as_tensor(ws.ant_xyz).cuda(), layers)
+    d_vis = vis.reshape(-1).cuda()
+    ref = torch.as_tensor(np.random.default_rng(4).normal(0, 1.0, total).astype(np.float32)).cuda()
+    out = torch.empty(total, device="cuda")
+    n_adj = plan.adjoint_bytes() // 4
+    a1, a2 = torch.empty(n_adj, device="cuda"), torch.empty(n_adj, device="cuda")
+    s1 = torch.empty(len(layers), dtype=torch.float64, device="cuda")
+    s2 = torch.empty_like(s1)
+    plan.image(d_vis, out, ref=ref, sqnorm=s1, adjoint=a1)
+    plan.image(d_vis, None, ref=ref, sqnorm=s2, adjoint=a2)
+    plan.check()
+    assert torch.equal(s1, s2)
+    d1 = torch.zeros(len(layers) * ws.n_baselines, dtype=torch.complex64, device="cuda")
+    d2 = torch.zeros_like(d1)
+    plan.degrid_adjoint(a1, d1)
+    plan.degrid_adjoint(a2, d2)
+    torch.cuda.synchronize()
+    assert torch.equal(d1, d2)
+    with pytest.raises(binding.BlinkError):
+        plan.image(d_vis, None, ref=ref, sqnorm=s2)  # no images and nothing kept
+    plan.close()
