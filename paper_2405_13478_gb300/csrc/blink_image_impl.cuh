@@ -105,7 +105,7 @@ __device__ __forceinline__ void weight_and_complete(float2 *G, int S, int r_begi
 // warp is conflict-free.
 template <int N, int SIGN = +1, bool PAD = false, bool NARROW = false>
 __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, int nt, const float2 *tw,
-                                         int kmax = N) {
+                                         int kmax = N, float2 *__restrict__ dst = nullptr) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
     auto ph = [](int q) { return PAD ? RowLayout<N>::phys(q) : q; };
     // rows that are zero outside |k_u| <= kmax < 2 N2: only n1 = 0, 1 and
@@ -143,7 +143,9 @@ __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, i
         for (int k1 = 0; k1 < N1; ++k1) row[ph(N2 * k1 + n2)] = x[k1];
     }
     __syncthreads();
-    // step B: N2-point transforms on contiguous runs, result kept in place
+    // step B: N2-point transforms on contiguous runs; the result stays in
+    // place (transposed order), or with dst goes straight to dst[r][p] in
+    // natural order p = k1 + N1 k2 (consecutive k1 of a warp: coalesced)
     for (int t = tid; t < nrows * N1; t += nt) {
         const int r = t / N1, k1 = t % N1;
         float2 *run = G + r * S;
@@ -151,8 +153,14 @@ __device__ __forceinline__ void rows_fft(float2 *G, int S, int nrows, int tid, i
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) y[n2] = run[ph(N2 * k1 + n2)];
         dft<N2, SIGN>(y);
+        if (dst) {
+            float2 *o = dst + int64_t(r) * N + k1;
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) run[ph(N2 * k1 + k2)] = y[k2];
+            for (int k2 = 0; k2 < N2; ++k2) o[N1 * k2] = y[k2];
+        } else {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) run[ph(N2 * k1 + k2)] = y[k2];
+        }
     }
     __syncthreads();
 }
@@ -480,11 +488,7 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // twiddle table (and compact rows) in place
     __syncthreads();
-    rows_fft<N, +1, true, NARROW>(sm, S, nrows, tid, NT, tw, ci.kmax_u);
-    for (int i = tid; i < nrows * N; i += NT) {
-        const int r = i / N, p = i % N;
-        dst[int64_t(r) * N + p] = sm[r * S + RowLayout<N>::phys(pos_after_rows<N>(p))];
-    }
+    rows_fft<N, +1, true, NARROW>(sm, S, nrows, tid, NT, tw, ci.kmax_u, dst);
 }
 
 // Pass 1 of a wave of layers into scratch[layer_in_wave][r][p] (the wave
@@ -531,10 +535,10 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
     __syncthreads();
     const int jj = tid % P, n2 = tid / P;  // one task per thread
     float2 x[N1];
-    bool narrow = false;
+    bool loaded = false;  // x holds the task's inputs
     if constexpr (NARROW && N > 4 * N2 && N1 >= 4) {
     if (R <= 2 * N2) {
-        narrow = true;
+        loaded = true;
         // narrow support: only n1 = 0, 1 and N1 - 2, N1 - 1 hold data (the
         // other inputs are constant zeros)
         auto row = [&](int k) {
@@ -549,7 +553,28 @@ __device__ __forceinline__ void cols_step_a_staged(float2 *Z, int R, int j0, con
         x[N1 - 1] = make_float2(b1.x + b1.w, b1.z - b1.y);
     }
     }
-    if (!narrow) {
+    if constexpr (N1 % 2 == 0) {
+    if (!loaded && R == H) {
+        // full support (rows 0 .. H - 1 all present): n1 < N1 / 2 reads row
+        // k = N2 n1 + n2 < H, n1 > N1 / 2 the mirrored row N - k < H; only
+        // n1 = N1 / 2 can hit k = H (n2 = 0), whose input is zero
+        loaded = true;
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const int k = N2 * n1 + n2;
+            if (n1 < N1 / 2) {
+                const float4 ab = *reinterpret_cast<const float4 *>(stg + k * 2 * P + 2 * jj);
+                x[n1] = make_float2(ab.x - ab.w, ab.y + ab.z);  // H_a + i H_b
+            } else if (n1 > N1 / 2 || n2 > 0) {
+                const float4 ab = *reinterpret_cast<const float4 *>(stg + (N - k) * 2 * P + 2 * jj);
+                x[n1] = make_float2(ab.x + ab.w, ab.z - ab.y);  // conj(H_a) + i conj(H_b)
+            } else {
+                x[n1] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+    }
+    if (!loaded) {
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
             const int k = N2 * n1 + n2;
