@@ -433,7 +433,11 @@ template <int N>
 struct RowsCfg {
     static constexpr int NT = 256;
     static constexpr int S = RowLayout<N>::S;
-    static constexpr int RB = std::max(1, std::min(32, int((kRowsSmemBudget - size_t(N) * 8) / (size_t(S) * 8))));
+    static constexpr int RB0 = std::max(1, std::min(32, int((kRowsSmemBudget - size_t(N) * 8) / (size_t(S) * 8))));
+    // at 1024^2 (N1 = N2 = 32) a band of 8 rows gives every thread one task
+    // in both steps (7 rows left 32 idle) and, at 75.8 KB, still lets three
+    // CTAs share an SM
+    static constexpr int RB = (Plan<N>::N1 == 32 && Plan<N>::N2 == 32) ? 8 : RB0;
     static constexpr int tw = (RB * S + 1) & ~1;  // float2 offset of the twiddles (16-byte aligned)
     static constexpr size_t smem = (size_t(tw) + N) * sizeof(float2);
 };
@@ -450,7 +454,11 @@ __device__ __forceinline__ void rows_item(const ImageArgs &a, const DevLayer &L,
     float2 *tw = sm + C::tw;
     auto prologue = [&]() {
         stage_four_step<N>(tw, tid, NT);
-        for (int i = tid; i < nrows * S; i += NT) sm[i] = make_float2(0.f, 0.f);
+        // zero the band two elements at a time (sm is 16-byte aligned)
+        const int n = nrows * S;
+        float4 *z4 = reinterpret_cast<float4 *>(sm);
+        for (int i = tid; i < n / 2; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((n & 1) && tid == 0) sm[n - 1] = make_float2(0.f, 0.f);
     };
     if (a.cg) {
         // the layer's compact grid (weighted, row 0 complete): expand the
@@ -1139,6 +1147,8 @@ Error launch_large_n(const ImageArgs &a, cudaStream_t st) {
     const size_t smem = large_smem<N>(a.r_alloc);
     auto kern = (a.ref || a.sq_part || a.adj) ? k_large<N, true> : k_large<N, false>;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    // three CTAs per SM need the largest shared-memory carveout
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int dev = 0, sms = 0, per_sm = 0;
     BLINK_CUDA_TRY(cudaGetDevice(&dev));
     BLINK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1179,8 +1189,10 @@ Error launch_large_body(const ImageArgs &a, cudaStream_t st) {
     const size_t smem_cols = cols_smem<N>(a.r_alloc);
     BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         int(smem_rows)));
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(k_rows<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     auto cols = (a.ref || a.sq_part || a.adj) ? k_cols<N, true> : k_cols<N, false>;
     BLINK_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_cols)));
+    BLINK_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     const unsigned bands = unsigned((a.r_alloc + RowsCfg<N>::RB - 1) / RowsCfg<N>::RB);
     const unsigned pchunks = unsigned((N / 2 + C::P - 1) / C::P);
     for (int l0 = 0; l0 < a.n_layers; l0 += wave) {
