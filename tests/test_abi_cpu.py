@@ -83,3 +83,36 @@ def test_layer_array_matches_the_c_struct():
     d = binding.make_layers([dict(n_px=180, weighting=1, freq_hz=1.5e8, delta_u=0.5,
                                   vis_offset=0, out_offset=0)])
     assert bytes(d[0]) == np.asarray(arr[0:1]).tobytes()
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Field offsets and sizes of blink_layer and blink_epilogue as the C
+    compiler lays them out from include/blink.h, against the ctypes mirrors."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+
+    from paper_2405_13478_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    fields = {"blink_layer": [f for f, _ in binding.Layer._fields_],
+              "blink_epilogue": [f for f, _ in binding.Epilogue._fields_]}
+    lines = ["#include <stdio.h>", "#include \"blink.h\"", "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st, cls in (("blink_layer", binding.Layer), ("blink_epilogue", binding.Epilogue)):
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
