@@ -279,8 +279,9 @@ BLINK_API int blink_plan_image(blink_plan *plan, const float *d_vis, float *d_im
  *                group, r_alloc rows of N complex64 (FFT-order columns).
  *                With d_adjoint set, d_images may be NULL: no image is
  *                stored (sizes whose columns come from stored images image
- *                into a temporary array of the plan's output extent from the
- *                context's pool, freed in stream order). */
+ *                into an array of the plan's output extent that the plan
+ *                allocates from the context's pool on first need and keeps
+ *                until it is destroyed). */
 typedef struct {
     const float *d_gains;
     int64_t gain_stride;

@@ -433,11 +433,11 @@ class Plan:
                                                             int(wave_bytes)))
 
     def capture(self, vis, images_out, wsum_out=None, flags=0, stream=None, gains=None,
-                gain_stride=0, ref=None, gain_period=0, sqnorm=None):
+                gain_stride=0, ref=None, gain_period=0, sqnorm=None, adjoint=None):
         """Record the batch's launches (with the optional epilogue) into a CUDA
         graph bound to these buffers."""
         _check_dev(vis, images_out, wsum_out)
-        epi = _epilogue(gains, gain_stride, ref, gain_period, sqnorm)
+        epi = _epilogue(gains, gain_stride, ref, gain_period, sqnorm, adjoint)
         self.ctx._raise(self.ctx._lib.blink_plan_capture(
             self.handle, _ptr(vis), _ptr(images_out), _ptr(wsum_out), int(flags),
             None if epi is None else ctypes.byref(epi), _stream(stream)))

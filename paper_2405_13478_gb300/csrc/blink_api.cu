@@ -109,6 +109,8 @@ struct blink_plan {
     float2 *d_gprod = nullptr;     // gain-product table of the fused epilogue (on first use)
     size_t gprod_bytes = 0;
     double *d_sqpart = nullptr;    // per-layer partial sums of squares (on first use)
+    float *d_imgtmp = nullptr;     // images of sizes without the fused adjoint columns when the
+                                   // caller stores none (on first use; output extent)
     int sq_stride = 0;             // slots per layer: the most column items of any group
     cudaStream_t last_stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
@@ -218,6 +220,8 @@ void free_plan_memory(blink_plan *p, cudaStream_t st) {
     p->d_gprod = nullptr;
     if (p->d_sqpart) cudaFreeAsync(p->d_sqpart, st);
     p->d_sqpart = nullptr;
+    if (p->d_imgtmp) cudaFreeAsync(p->d_imgtmp, st);
+    p->d_imgtmp = nullptr;
     if (p->d_queue) cudaFreeAsync(p->d_queue, st);
     p->d_queue = nullptr;
     p->queue_bytes = 0;
@@ -749,18 +753,20 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
             break;
         }
     // without an output array (d_adjoint set), groups whose adjoint columns
-    // come from stored images image into a temporary array from the pool
+    // come from stored images image into the plan's own image array
+    // (allocated on first need, before any graph capture records this call)
     float *d_tmp = nullptr;
     if (!d_images && p->n_layers) {
         bool need = false;
         for (const auto &grp : p->groups) need = need || gemm_ok(grp) || !blink::adjoint_fusable(grp.n_px);
-        if (need) {
+        if (need && !p->d_imgtmp) {
             void *ptr = nullptr;
             const cudaError_t e = cudaMallocFromPoolAsync(&ptr, size_t(p->out_extent) * sizeof(float), ctx->pool, st);
             if (e != cudaSuccess)
-                return fail(ctx, BLINK_ERR_WORKSPACE, std::string("temporary images: ") + cudaGetErrorString(e));
-            d_tmp = static_cast<float *>(ptr);
+                return fail(ctx, BLINK_ERR_WORKSPACE, std::string("plan images: ") + cudaGetErrorString(e));
+            p->d_imgtmp = static_cast<float *>(ptr);
         }
+        if (need) d_tmp = p->d_imgtmp;
     }
     for (size_t gi = 0; gi < p->groups.size(); ++gi) {
         const auto &grp = p->groups[gi];
@@ -789,12 +795,8 @@ int blink_plan_image_ex(blink_plan *p, const float *d_vis, float *d_images, floa
             a.adj = adj;
             e = blink::launch_image_group(grp.n_px, a, st);
         }
-        if (e.status) {
-            if (d_tmp) cudaFreeAsync(d_tmp, st);
-            return fail(ctx, e);
-        }
+        if (e.status) return fail(ctx, e);
     }
-    if (d_tmp) cudaFreeAsync(d_tmp, st);
     if (d_sqnorm) {
         Error e = blink::launch_sq_totals(p->d_sqpart, p->sq_stride, p->n_layers, d_sqnorm, st);
         if (e.status) return fail(ctx, e);

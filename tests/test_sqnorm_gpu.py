@@ -278,6 +278,18 @@ def test_no_image_output_with_kept_adjoint(torch, ctx, case):
     plan.degrid_adjoint(a2, d2)
     torch.cuda.synchronize()
     assert torch.equal(d1, d2)
+    # the same through a CUDA graph (the plan's own image array, where one is
+    # needed, is allocated by the capture's first run, outside the graph)
+    a3, s3 = torch.empty(n_adj, device="cuda"), torch.empty_like(s1)
+    plan.capture(d_vis, None, ref=ref, sqnorm=s3, adjoint=a3)
+    a3.zero_()
+    s3.zero_()
+    plan.replay()
+    plan.check()
+    d3 = torch.zeros_like(d1)
+    plan.degrid_adjoint(a3, d3)
+    torch.cuda.synchronize()
+    assert torch.equal(s1, s3) and torch.equal(d1, d3)
     with pytest.raises(binding.BlinkError):
         plan.image(d_vis, None, ref=ref, sqnorm=s2)  # no images and nothing kept
     plan.close()
