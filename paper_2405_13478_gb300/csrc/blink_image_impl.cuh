@@ -281,11 +281,19 @@ __device__ __forceinline__ void degrid_cols_strip(float2 *sm, int R, int x0, flo
 // image column xa and xa + 1 (when img is set) and at strip[row][2 jj] (when
 // strip is set: FFT-order rows of 16 floats).  Returns the sum of their
 // squares in FP32 when want_sq.
-template <int N>
+template <int N, bool EPI>
 __device__ __forceinline__ float store_task(const float2 (&y)[Plan<N>::N2], int k1, int xa, int jj, float *img,
                                             float scale, const float *ref, bool pair_store, bool want_sq,
                                             float *strip) {
     constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H = N / 2;
+    // with N2 even, FFT-order row k1 + N1 k2 (k1 < N1) is below H exactly
+    // when k2 < N2 / 2: the fftshift is then fixed per k2 at compile time
+    constexpr bool split = N2 % 2 == 0;
+    auto image_row = [&](int k2) {
+        const int qq = k1 + N1 * k2;
+        if constexpr (split) return k2 < N2 / 2 ? qq + H : qq - H;
+        return qq < H ? qq + H : qq - H;
+    };
     float sq = 0.f;
     // stores in batches of KB rows; with the fused epilogue each batch's
     // reference values are requested together before its stores
@@ -296,8 +304,7 @@ __device__ __forceinline__ float store_task(const float2 (&y)[Plan<N>::N2], int 
         if (ref) {
 #pragma unroll
             for (int u = 0; u < KB; ++u) {
-                const int qq = k1 + N1 * (kb + u);
-                const float *rp = ref + (qq < H ? qq + H : qq - H) * N + xa;  // 32-bit: N * N < 2^31
+                const float *rp = ref + image_row(kb + u) * N + xa;  // 32-bit: N * N < 2^31
                 rf[u] = pair_store ? __ldcs(reinterpret_cast<const float2 *>(rp))
                                    : make_float2(__ldcs(rp), __ldcs(rp + 1));
             }
@@ -306,13 +313,13 @@ __device__ __forceinline__ float store_task(const float2 (&y)[Plan<N>::N2], int 
         for (int u = 0; u < KB; ++u) {
             const int k2 = kb + u;
             const int qq = k1 + N1 * k2;              // FFT-order row
-            const int row = qq < H ? qq + H : qq - H; // fftshift
+            const int row = image_row(k2);            // fftshift
             float2 v = make_float2(y[k2].x * scale, y[k2].y * scale);
             if (ref) {
                 v.x -= rf[u].x;
                 v.y -= rf[u].y;
             }
-            if (img) {
+            if (!EPI || img) {  // (only the epilogue may store no image)
                 float *o = img + row * N + xa;        // offsets inside one image fit 32 bits
                 if (pair_store) {
                     __stcs(reinterpret_cast<float2 *>(o), v);
@@ -335,7 +342,7 @@ __device__ __forceinline__ float store_task(const float2 (&y)[Plan<N>::N2], int 
 // fixed order).  With adj (sizes whose column item is one 16-column strip of
 // the image: AdjFusable), the CTA's values also go to a strip in Z's buffer
 // and the adjoint's column transforms of that strip (rows k < R) go to adj.
-template <int N, int P, class ZL, int NT>
+template <int N, int P, class ZL, int NT, bool EPI>
 __device__ __forceinline__ double cols_step_b(float2 *Z, int j0, float *img, float scale, int tid,
                                               const float *ref, bool want_sq = false, float2 *adj = nullptr,
                                               int R = 0) {
@@ -355,7 +362,7 @@ __device__ __forceinline__ double cols_step_b(float2 *Z, int j0, float *img, flo
             for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[ZL::phys(N2 * k1 + n2)];
             dft<N2, +1>(y);
             __syncthreads();
-            const float sq = store_task<N>(y, k1, xa, jj, img, scale, ref, pair_store, want_sq,
+            const float sq = store_task<N, EPI>(y, k1, xa, jj, img, scale, ref, pair_store, want_sq,
                                            reinterpret_cast<float *>(Z));
             if (want_sq) acc = double(sq);
             __syncthreads();  // the strip is complete
@@ -373,7 +380,7 @@ __device__ __forceinline__ double cols_step_b(float2 *Z, int j0, float *img, flo
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) y[n2] = zp[ZL::phys(N2 * k1 + n2)];
         dft<N2, +1>(y);
-        const float sq = store_task<N>(y, k1, xa, jj, img, scale, ref, pair_store, want_sq, nullptr);
+        const float sq = store_task<N, EPI>(y, k1, xa, jj, img, scale, ref, pair_store, want_sq, nullptr);
         if (want_sq) acc += double(sq);
     }
     return want_sq ? block_sum_f64<NT>(acc, tid) : 0.0;
@@ -632,7 +639,7 @@ __device__ __forceinline__ void cols_item(const ImageArgs &a, const DevLayer &L,
     // fused adjoint columns: layer lidx of the group's slots (r_alloc rows of N)
     float2 *adj = EPI && a.adj ? a.adj + int64_t(lidx) * a.r_alloc * N : nullptr;
     // (no output array: the fused adjoint keeps the columns, no image is stored)
-    const double sq = cols_step_b<N, P, ZL, NT>(sm, j0, out ? out + L.out_off : nullptr, scale, tid,
+    const double sq = cols_step_b<N, P, ZL, NT, EPI>(sm, j0, out ? out + L.out_off : nullptr, scale, tid,
                                                 EPI && ref ? ref + L.out_off : nullptr, want_sq, adj, R);
     if (want_sq)  // one slot per column item
         store_sq_slot<NT>(a.sq_part + int64_t(L.layer) * a.sq_stride, j0 / P, (N / 2 + P - 1) / P, a.sq_stride,
